@@ -1,0 +1,238 @@
+"""Galerkin assembly of the IgA Helmholtz operator (paper Section 2.3, Eq. linearsystem1).
+
+Test infrastructure only (see oracle/__init__.py).
+
+S_ij = int grad Phi_i . grad Phi_j,  M_ij = int Phi_i Phi_j,
+M^{k^2}_ij = int k(x)^2 Phi_i Phi_j, all by (p+1)-point Gauss quadrature per
+knot span (per element in 2D, tensor Gauss rule).  The operator is
+A = S - M^{k^2}: the reading of the paper's sign conflict that matches its
+model problems (-Delta u - k^2 u = f) and the exact solution e^{ikx}.
+Homogeneous Dirichlet conditions are imposed by deleting the first and last
+basis function in each direction (the open knot vector makes them the only
+functions that are non-zero on the boundary).
+
+Index convention: interior coefficient (ix, iy) sits at flat index
+iy * n_x + ix (x fastest), ix = bx - 1 for full basis index bx.
+
+Pins (tests/test_oracle_assembly.py): p=1 textbook element matrices, zero row
+sums of S before Dirichlet elimination, sum(M) = |Omega|, symmetry,
+generalised eigenvalues -> j^2 pi^2 at rate h^{2p}, manufactured-solution
+L2 rates O(h^{p+1}), MP 1-B Green's function, MP 1-A Table 1 rates.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+
+from . import bspline
+
+
+# ---------------------------------------------------------------- k field
+def k_of(kfield, x, y=None):
+    """Piecewise-constant wave number: values[count of lines with a*x+b*y+c >= 0],
+    the sum evaluated as ((a*x) + (b*y)) + c."""
+    x = np.asarray(x, dtype=np.float64)
+    if len(kfield.lines) == 0:
+        return np.full(x.shape, float(kfield.values[0]))
+    y = np.asarray(y, dtype=np.float64)
+    count = np.zeros(x.shape, dtype=np.int64)
+    for ln in kfield.lines:
+        s = (ln.a * x + ln.b * y) + ln.c
+        count += (s >= 0.0)
+    return np.asarray(kfield.values, dtype=np.float64)[count]
+
+
+# ---------------------------------------------------------------- 1D tables
+def local_tables(n_el: int, p: int):
+    """Per element e and Gauss point q: values B[e,q,a] and derivatives
+    D[e,q,a] of the p+1 functions a = 0..p that are active on span e
+    (full basis index e + a), Gauss points xq[e,q] and weights wq[e,q]."""
+    t = bspline.open_uniform_knots(n_el, p)
+    xq, wq, spans = bspline.element_quadrature(t, p)
+    assert len(spans) == n_el
+    pts = xq.reshape(-1)
+    phi = bspline.basis_all(t, p, pts)
+    dphi = bspline.basis_deriv_all(t, p, pts)
+    nq = p + 1
+    B = np.zeros((n_el, nq, p + 1))
+    D = np.zeros((n_el, nq, p + 1))
+    for e in range(n_el):
+        cols = slice(e * nq, (e + 1) * nq)
+        # every function outside e..e+p must vanish on span e
+        mask = np.ones(phi.shape[0], bool)
+        mask[e:e + p + 1] = False
+        assert np.all(phi[mask, cols] == 0.0)
+        B[e] = phi[e:e + p + 1, cols].T
+        D[e] = dphi[e:e + p + 1, cols].T
+    return B, D, xq, wq
+
+
+def assemble_1d(n_el: int, p: int, k2_fn=None):
+    """Full (boundary functions included) 1D stiffness K, mass M and, if
+    k2_fn is given, the weighted mass int k^2 phi_i phi_j, as CSR matrices."""
+    B, D, xq, wq = local_tables(n_el, p)
+    nb = n_el + p
+    rows, cols, kv, mv, mkv = [], [], [], [], []
+    k2 = k2_fn(xq) if k2_fn is not None else None
+    for e in range(n_el):
+        for a in range(p + 1):
+            for c in range(p + 1):
+                rows.append(e + a)
+                cols.append(e + c)
+                kv.append(np.sum(wq[e] * D[e, :, a] * D[e, :, c]))
+                mv.append(np.sum(wq[e] * B[e, :, a] * B[e, :, c]))
+                if k2 is not None:
+                    mkv.append(np.sum(wq[e] * k2[e] * B[e, :, a] * B[e, :, c]))
+    K = sp.csr_matrix((kv, (rows, cols)), shape=(nb, nb))
+    M = sp.csr_matrix((mv, (rows, cols)), shape=(nb, nb))
+    Mk = sp.csr_matrix((mkv, (rows, cols)), shape=(nb, nb)) if k2 is not None else None
+    return K, M, Mk
+
+
+def interior_1d(mat):
+    """Delete the first and last row/column (homogeneous Dirichlet)."""
+    n = mat.shape[0]
+    return mat[1:n - 1, :][:, 1:n - 1].tocsr()
+
+
+def assemble_2d(n_el: int, p: int, kfield, chunk: int = 32):
+    """Full 2D stiffness S, plain mass M and weighted mass M^{k^2} on the unit
+    square by tensor Gauss quadrature on each element (ex, ey).  k^2 is
+    evaluated at every Gauss point.  Returns CSR matrices over the full
+    (n_el+p)^2 basis, flat index by * nb + bx."""
+    B, D, xq, wq = local_tables(n_el, p)
+    nb = n_el + p
+    q1 = p + 1
+    S_parts, M_parts, Mk_parts = [], [], []
+    a_idx = np.arange(q1)
+    for ey0 in range(0, n_el, chunk):
+        ey1 = min(n_el, ey0 + chunk)
+        ey = np.arange(ey0, ey1)
+        ex = np.arange(n_el)
+        # Gauss points of elements (ex, ey): X[ex,qx], Y[ey,qy]
+        Xg = xq[ex][:, None, :, None]             # ex, 1, qx, 1
+        Yg = xq[ey][None, :, None, :]             # 1, ey, 1, qy
+        Xb, Yb = np.broadcast_arrays(Xg, Yg)
+        k = k_of(kfield, Xb, Yb)                  # ex, ey, qx, qy
+        W = wq[ex][:, None, :, None] * wq[ey][None, :, None, :]
+        Bx, Dx = B[ex], D[ex]                     # ex, qx, a
+        By, Dy = B[ey], D[ey]                     # ey, qy, b
+        # local matrices [ex, ey, a, b, c, d]: row (a,b), column (c,d)
+        Ml = np.einsum('xyqr,xqa,xqc,yrb,yrd->xyabcd', W, Bx, Bx, By, By, optimize=True)
+        Mkl = np.einsum('xyqr,xqa,xqc,yrb,yrd->xyabcd', W * k * k, Bx, Bx, By, By, optimize=True)
+        Sl = (np.einsum('xyqr,xqa,xqc,yrb,yrd->xyabcd', W, Dx, Dx, By, By, optimize=True)
+              + np.einsum('xyqr,xqa,xqc,yrb,yrd->xyabcd', W, Bx, Bx, Dy, Dy, optimize=True))
+        gx = ex[:, None, None, None, None, None] + a_idx[None, None, :, None, None, None]
+        gy = ey[None, :, None, None, None, None] + a_idx[None, None, None, :, None, None]
+        hx = ex[:, None, None, None, None, None] + a_idx[None, None, None, None, :, None]
+        hy = ey[None, :, None, None, None, None] + a_idx[None, None, None, None, None, :]
+        shape = Ml.shape
+        r = np.broadcast_to(gy * nb + gx, shape).reshape(-1)
+        c = np.broadcast_to(hy * nb + hx, shape).reshape(-1)
+        S_parts.append(sp.coo_matrix((Sl.reshape(-1), (r, c)), shape=(nb * nb, nb * nb)).tocsr())
+        M_parts.append(sp.coo_matrix((Ml.reshape(-1), (r, c)), shape=(nb * nb, nb * nb)).tocsr())
+        Mk_parts.append(sp.coo_matrix((Mkl.reshape(-1), (r, c)), shape=(nb * nb, nb * nb)).tocsr())
+    S = S_parts[0]
+    M = M_parts[0]
+    Mk = Mk_parts[0]
+    for i in range(1, len(S_parts)):
+        S = S + S_parts[i]
+        M = M + M_parts[i]
+        Mk = Mk + Mk_parts[i]
+    return S.tocsr(), M.tocsr(), Mk.tocsr()
+
+
+def interior_index_2d(nb: int) -> np.ndarray:
+    """Flat full indices of the interior functions, in interior lexicographic
+    order (x fastest)."""
+    i = np.arange(1, nb - 1)
+    return (i[:, None] * nb + i[None, :]).reshape(-1)
+
+
+def interior_2d(mat, nb: int):
+    idx = interior_index_2d(nb)
+    return mat[idx, :][:, idx].tocsr()
+
+
+# ---------------------------------------------------------------- operators
+class Discretization:
+    """Interior (Dirichlet-eliminated) S, M, M^{k^2} and A = S - M^{k^2} for one
+    problem description (dim, p, n_el, kfield)."""
+
+    def __init__(self, dim: int, p: int, n_el: int, kfield):
+        self.dim, self.p, self.n_el, self.kfield = dim, p, n_el, kfield
+        self.nb = n_el + p
+        self.n_x = n_el + p - 2
+        if dim == 1:
+            k2 = (lambda x: k_of(kfield, x) ** 2)
+            K, M, Mk = assemble_1d(n_el, p, k2)
+            self.S = interior_1d(K)
+            self.M = interior_1d(M)
+            self.Mk = interior_1d(Mk)
+        else:
+            S, M, Mk = assemble_2d(n_el, p, kfield)
+            self.S = interior_2d(S, self.nb)
+            self.M = interior_2d(M, self.nb)
+            self.Mk = interior_2d(Mk, self.nb)
+        self.A = (self.S - self.Mk).astype(np.complex128).tocsr()
+
+    @property
+    def n(self) -> int:
+        return self.S.shape[0]
+
+    def shifted(self, beta1: float, beta2: float):
+        """CSLP operator M_beta = S - (beta1 - i beta2) M^{k^2} (Section 3, CSLP
+        equation, read with the mass matrix in place of I)."""
+        return (self.S - (beta1 - 1j * beta2) * self.Mk).astype(np.complex128).tocsr()
+
+
+def point_source(dim: int, p: int, n_el: int, pos) -> np.ndarray:
+    """Load vector of a unit point source: f_i = Phi_i(pos), interior functions."""
+    t = bspline.open_uniform_knots(n_el, p)
+    vx = bspline.basis_all(t, p, [pos[0]])[:, 0][1:-1]
+    if dim == 1:
+        return vx.astype(np.complex128)
+    vy = bspline.basis_all(t, p, [pos[1]])[:, 0][1:-1]
+    return np.outer(vy, vx).reshape(-1).astype(np.complex128)
+
+
+def l2_load_1d(n_el: int, p: int, f_fn, nq: int | None = None) -> np.ndarray:
+    """f_i = int f phi_i by Gauss quadrature with nq points per span (interior i)."""
+    t = bspline.open_uniform_knots(n_el, p)
+    nq = nq or (p + 4)
+    xq, wq, _ = bspline.element_quadrature(t, p, nq)
+    pts = xq.reshape(-1)
+    phi = bspline.basis_all(t, p, pts)
+    vals = f_fn(pts) * wq.reshape(-1)
+    return (phi @ vals)[1:-1]
+
+
+def eval_spline_1d(n_el: int, p: int, coef_full: np.ndarray, x) -> np.ndarray:
+    t = bspline.open_uniform_knots(n_el, p)
+    return coef_full @ bspline.basis_all(t, p, x)
+
+
+def l2_error_1d(n_el: int, p: int, coef_full: np.ndarray, u_exact, nq: int = 10) -> float:
+    """Continuous L2 error of a spline (full coefficient vector) vs u_exact by
+    nq-point Gauss quadrature per span."""
+    t = bspline.open_uniform_knots(n_el, p)
+    xq, wq, _ = bspline.element_quadrature(t, p, nq)
+    pts = xq.reshape(-1)
+    uh = coef_full @ bspline.basis_all(t, p, pts)
+    d = uh - u_exact(pts)
+    return float(np.sqrt(np.sum(wq.reshape(-1) * np.abs(d) ** 2)))
+
+
+def mp1a_solve(n_el: int, p: int, k: float):
+    """MP 1-A (Section 2.1): -u'' - k^2 u = 0 on [0, 1], u(0) = 1,
+    u'(1) - i k u(1) = 0.  Weak form gives A = K - k^2 M - i k N with the
+    boundary mass N = phi_last(1)^2 at x = 1; the Dirichlet value enters as the
+    first (interpolatory) coefficient.  Returns the full coefficient vector."""
+    K, M, _ = assemble_1d(n_el, p)
+    nb = n_el + p
+    Nb = sp.csr_matrix(([1.0], ([nb - 1], [nb - 1])), shape=(nb, nb))
+    A = (K - k * k * M - 1j * k * Nb).tocsc().astype(np.complex128)
+    import scipy.sparse.linalg as spla
+    rhs = -np.asarray(A[1:, 0].toarray()).reshape(-1)
+    c = spla.spsolve(A[1:, 1:].tocsc(), rhs)
+    return np.concatenate([[1.0 + 0j], c])

@@ -1,0 +1,80 @@
+"""End-to-end deflated, MG-preconditioned GMRES solve (paper Section 3,
+deflated preconditioned system; Section 4.3 settings), plus the direct solve.
+
+Test infrastructure only (see oracle/__init__.py).
+
+Operator ordering (reading of the paper's P^T M^{-1} A u = P^T M^{-1} f, which
+taken literally is singular and gives no recovery formula):
+
+* 'def1' (default): GMRES on M~^{-1} P A x^ = M~^{-1} P f from x^ = 0, then
+  u = Q f + P^T x^, with P = I - A Q, Q = Z E^{-1} Z^T, P^T = I - Q A.
+* 'literal': GMRES on P^T M~^{-1} A u = P^T M~^{-1} f from u = 0; the iterate is
+  used as u directly (reported for comparison only).
+* flexible=True: right-preconditioned FGMRES on P A (M~^{-1} y) = P f, stopping
+  on ||P (f - A x^)|| / ||P f||, recovery as for 'def1'.
+
+M~^{-1} is n_vcycles V-cycles of the CSLP hierarchy (oracle.multigrid).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse.linalg as spla
+
+from .assembly import Discretization, point_source
+from .multigrid import MGHierarchy
+from .deflation import Deflation, z_matrix
+from .krylov import gmres, fgmres
+
+
+class Solver:
+    def __init__(self, problem, disc: Discretization | None = None):
+        pr = problem
+        self.problem = pr
+        self.disc = disc or Discretization(pr.dim, pr.p, pr.n_el, pr.kfield)
+        b1, b2 = pr.shift
+        self.mg = MGHierarchy(pr.dim, pr.p, pr.n_el, pr.kfield, b1, b2, omega=pr.omega,
+                              nu_pre=pr.nu_pre, nu_post=pr.nu_post, fine_disc=self.disc)
+        self.Z = z_matrix(pr.dim, self.disc.n_x, pr.eps)
+        self.defl = Deflation(self.disc.A, self.Z)
+
+    @property
+    def A(self):
+        return self.disc.A
+
+    def precond(self, v):
+        return self.mg.apply(v, self.problem.n_vcycles)
+
+    def op_def1(self, v):
+        return self.precond(self.defl.P(self.A @ v))
+
+    def load(self, k: int = 0) -> np.ndarray:
+        pr = self.problem
+        return point_source(pr.dim, pr.p, pr.n_el, pr.sources[k])
+
+    def solve(self, f, tol=1e-7, maxit=100, variant='def1', flexible=False, x_at=None):
+        f = np.asarray(f, dtype=np.complex128)
+        if flexible:
+            res = fgmres(lambda z: self.defl.P(self.A @ z), self.precond, self.defl.P(f), tol, maxit)
+            u = self.defl.Q(f) + self.defl.PT(res.x)
+        elif variant == 'def1':
+            res = gmres(self.op_def1, self.precond(self.defl.P(f)), tol, maxit, x_at=x_at)
+            u = self.defl.Q(f) + self.defl.PT(res.x)
+            if x_at is not None and res.x_at is not None:
+                res.u_at = self.defl.Q(f) + self.defl.PT(res.x_at)
+        elif variant == 'literal':
+            res = gmres(lambda v: self.defl.PT(self.precond(self.A @ v)),
+                        self.defl.PT(self.precond(f)), tol, maxit)
+            u = res.x
+        else:
+            raise ValueError(variant)
+        res.u = u
+        res.true_res = float(np.linalg.norm(f - self.A @ u) / np.linalg.norm(f))
+        return res
+
+    def direct(self, f):
+        """u* = A^{-1} f by sparse LU (the plain definition of the result)."""
+        return spla.splu(self.A.tocsc()).solve(np.asarray(f, dtype=np.complex128))
+
+
+def rel_err(a, b) -> float:
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))

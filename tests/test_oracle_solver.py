@@ -1,0 +1,204 @@
+"""Pins for oracle.multigrid, oracle.deflation, oracle.krylov and oracle.solver."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import workloads as W
+from oracle import bspline
+from oracle import assembly as asm
+from oracle import multigrid as mg
+from oracle import deflation as dfl
+from oracle.krylov import gmres, fgmres
+from oracle.solver import Solver, rel_err
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ------------------------------------------------------------------ multigrid
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5])
+def test_knot_insertion_reproduces_spline(p):
+    nc = 6
+    P = mg.prolongation_1d(nc, p)
+    tc = bspline.open_uniform_knots(nc, p)
+    tf = bspline.open_uniform_knots(2 * nc, p)
+    c = np.random.default_rng(1).standard_normal(nc + p)
+    x = np.random.default_rng(2).uniform(0, 1, 200)
+    coarse = c @ bspline.basis_all(tc, p, x)
+    fine = (P @ c) @ bspline.basis_all(tf, p, x)
+    np.testing.assert_allclose(fine, coarse, atol=1e-13)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_interior_subdivision_mask(p):
+    P = mg.prolongation_1d(16, p)
+    col = P[:, 8]
+    nz = col[np.abs(col) > 0]
+    mask = np.array([math.comb(p + 1, j) for j in range(p + 2)]) / 2 ** p
+    np.testing.assert_allclose(nz, mask, atol=1e-15)
+    if p == 1:
+        np.testing.assert_allclose(mask, [0.5, 1.0, 0.5])    # linear interpolation (Section 4.2)
+
+
+def test_levels():
+    assert mg.level_sizes(320) == [320, 160, 80, 40, 20, 10, 5]
+    assert mg.level_sizes(48) == [48, 24, 12, 6]
+    assert mg.level_sizes(80) == [80, 40, 20, 10, 5]
+
+
+@pytest.mark.parametrize("dim,p", [(1, 2), (2, 1), (2, 3)])
+def test_rediscretised_equals_galerkin_constant_k(dim, p):
+    h = mg.MGHierarchy(dim, p, 16, W.constant_k(4.0), 1.0, 0.5)
+    for li in range(len(h.levels) - 1):
+        gal = (h.P[li].T @ h.levels[li].Mb @ h.P[li]).toarray()
+        np.testing.assert_allclose(gal, h.levels[li + 1].Mb.toarray(), atol=1e-10 * np.abs(gal).max())
+
+
+def test_vcycle_iteration_converges_to_inverse():
+    pr = W.small_2d(n_el=16, p=2, k=6.0)
+    h = mg.MGHierarchy(2, 2, 16, pr.kfield, 1.0, 0.5)
+    b = W.seeded_complex_vector(h.levels[0].Mb.shape[0], 7)
+    exact = np.linalg.solve(h.levels[0].Mb.toarray(), b)
+    errs = [rel_err(h.apply(b, j), exact) for j in (1, 2, 4, 8, 16, 32)]
+    assert all(e1 < e0 for e0, e1 in zip(errs, errs[1:])), errs
+    assert errs[-1] < 1e-6
+
+
+def test_two_level_vcycle_matrix():
+    """On a two-level hierarchy the V-cycle is the linear map
+    S_post (I - P Mc^{-1} P^T M) S_pre-form applied to b: check against the
+    composition of explicit dense factors."""
+    h = mg.MGHierarchy(1, 2, 8, W.constant_k(3.0), 1.0, 0.5)
+    assert h.sizes == [8, 4]
+    Mf = h.levels[0].Mb.toarray()
+    Mc = h.levels[1].Mb.toarray()
+    P = h.P[0].toarray()
+    n = Mf.shape[0]
+    Dinv = np.diag(0.6 / np.diag(Mf))
+    I = np.eye(n)
+    S = I - Dinv @ Mf                          # Jacobi error propagation
+    CG = I - P @ np.linalg.solve(Mc, P.T @ Mf)
+    E = S @ CG @ S                             # two-grid error propagation
+    V = (I - E) @ np.linalg.inv(Mf)            # the V-cycle as a matrix
+    cols = np.stack([h.vcycle(I[:, j].astype(complex)) for j in range(n)], axis=1)
+    np.testing.assert_allclose(cols, V, atol=1e-12 * np.abs(V).max())
+
+
+# ------------------------------------------------------------------ deflation
+def test_z_constants_and_linears():
+    n_x = 21
+    Z = dfl.z_matrix_1d(n_x).toarray()
+    m = n_x // 2
+    one = Z @ np.ones(m)
+    np.testing.assert_allclose(one[2:-2], 1.0)               # interior rows
+    jc = np.arange(1, m + 1, dtype=float)                     # coarse i at fine 2i
+    lin = Z @ (2 * jc)
+    np.testing.assert_allclose(lin[2:-2], np.arange(1, n_x + 1, dtype=float)[2:-2])
+    # Z^T row = (1, 4, 6, 4, 1)/8 on 2i-2..2i+2
+    np.testing.assert_allclose(Z[:, 4][7:12] * 8, [1, 4, 6, 4, 1])
+    Ze = dfl.z_matrix_1d(n_x, eps=0.3).toarray()
+    assert abs(Ze[9, 4] * 8 - 5.7) < 1e-15
+
+
+def test_deflation_projector_properties():
+    pr = W.small_2d(n_el=12, p=2, k=9.0)
+    s = Solver(pr)
+    A = s.A.toarray()
+    Z = s.Z.toarray()
+    E = s.defl.E.toarray()
+    np.testing.assert_allclose(E, E.T, atol=1e-12 * np.abs(E).max())   # complex symmetric
+    n = A.shape[0]
+    Pm = np.stack([s.defl.P(np.eye(n)[:, j].astype(complex)) for j in range(n)], axis=1)
+    np.testing.assert_allclose(Pm @ Pm, Pm, atol=1e-10)
+    np.testing.assert_allclose(Pm @ A @ Z, 0, atol=1e-9 * np.abs(A).max())
+    # M~^{-1} P A has exactly m zero eigenvalues (Section 4.2: "half")
+    Bm = np.stack([s.op_def1(np.eye(n)[:, j].astype(complex)) for j in range(n)], axis=1)
+    ev = np.abs(np.linalg.eigvals(Bm))
+    m = s.defl.m
+    assert np.sum(ev < 1e-9) == m
+    assert np.sort(ev)[m] > 1e-6
+
+
+def test_recovery_gives_solution():
+    pr = W.small_2d(n_el=16, p=3, k=12.0)
+    s = Solver(pr)
+    f = s.load()
+    r = s.solve(f, tol=1e-12, maxit=200)
+    assert r.converged
+    assert r.true_res < 1e-9
+    assert rel_err(r.u, s.direct(f)) < 1e-8
+
+
+# ------------------------------------------------------------------ krylov
+def test_gmres_iterate_is_krylov_minimiser():
+    rng = np.random.default_rng(0)
+    n = 30
+    B = np.eye(n) * 3 + rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    for j in (1, 3, 7):
+        r = gmres(lambda v: B @ v, b, tol=0.0, maxit=j, x_at=j)
+        K = np.stack([np.linalg.matrix_power(B, i) @ b for i in range(j)], axis=1)
+        c, *_ = np.linalg.lstsq(B @ K, b, rcond=None)
+        np.testing.assert_allclose(r.x, K @ c, rtol=1e-9, atol=1e-12)
+        np.testing.assert_allclose(r.x_at, r.x, atol=1e-14)
+        h = np.array(r.hist)
+        assert np.all(np.diff(h) <= 1e-15)
+        np.testing.assert_allclose(h[-1], np.linalg.norm(b - B @ r.x) / np.linalg.norm(b), rtol=1e-9)
+
+
+def test_fgmres_fixed_preconditioner_matches_right_preconditioned_gmres():
+    rng = np.random.default_rng(1)
+    n = 25
+    B = np.eye(n) * 4 + rng.standard_normal((n, n))
+    Mi = np.eye(n) + 0.1 * rng.standard_normal((n, n))
+    b = rng.standard_normal(n) + 0j
+    r1 = fgmres(lambda z: B @ z, lambda v: Mi @ v, b, tol=0.0, maxit=6)
+    r2 = gmres(lambda v: B @ (Mi @ v), b, tol=0.0, maxit=6)
+    np.testing.assert_allclose(r1.x, Mi @ r2.x, rtol=1e-10, atol=1e-13)
+
+
+# ------------------------------------------------------------------ soft pins
+def test_table5_soft_pin():
+    """MP 2-A, k = 50, DC^1_MG with beta_2 = 1 (Section 4.3.2, Table 5):
+    iteration counts within a few of the paper's (level count, coarse
+    operator and smoothing count are unstated in the paper)."""
+    g = json.load(open(os.path.join(GOLD, "table5_iterations.json")))
+    for p in (1, 2, 3):
+        pr = W.config2(k=50.0, p=p)
+        pr.shift = (1.0, 1.0)
+        s = Solver(pr)
+        r = s.solve(s.load())
+        assert r.converged
+        paper = g["dc1"][str(p)]
+        assert abs(r.iters - paper) <= max(3, 0.35 * paper), (p, r.iters, paper)
+
+
+def test_table4_soft_pin_1d():
+    """MP 1-B, k = 100, p = 2, DC^1_MG, beta_2 = 1: the paper reports 5
+    (Section 4.3.1, Table 4)."""
+    pr = W.Problem(dim=1, p=2, n_el=160, kfield=W.constant_k(100.0), shift=(1.0, 1.0), sources=[(0.5,)])
+    s = Solver(pr)
+    r = s.solve(s.load())
+    assert r.converged and abs(r.iters - 5) <= 2, r.iters
+
+
+def test_config1_solves():
+    pr = W.config1()[0]
+    s = Solver(pr)
+    for f in (s.load(), W.seeded_normal_rhs(s.disc.n, 0).astype(complex)):
+        r = s.solve(f)
+        assert r.converged and r.true_res < 1e-6
+        assert rel_err(r.u, s.direct(f)) < 1e-6
+
+
+def test_planted_mistake_is_caught():
+    """A sign error planted in the oracle's deflation (P = I + A Q) must break
+    the projector identity P A Z = 0 that the parity tests rely on."""
+    pr = W.small_2d(n_el=8, p=2, k=5.0)
+    s = Solver(pr)
+    good = s.defl.P(s.A @ s.Z[:, 3].toarray().ravel().astype(complex))
+    bad = s.A @ s.Z[:, 3].toarray().ravel() + s.A @ s.defl.Q(s.A @ s.Z[:, 3].toarray().ravel())
+    assert np.linalg.norm(good) < 1e-9 * np.linalg.norm(bad)

@@ -1,0 +1,180 @@
+/*
+ * iga_helmholtz.h — C ABI of the GB300 (sm_103a) IgA Helmholtz solver.
+ *
+ * Method: arXiv 2010.10232 (Dwarka, Tielen, Moller, Vuik).  GMRES on the
+ * B-spline Galerkin system A u = f with A = S - M^{k^2} (Section 2.3, Eq.
+ * linearsystem1, read with the sign of the model problems), preconditioned by
+ * multigrid V-cycles of the complex shifted Laplacian (Section 3, CSLP
+ * equation; damped Jacobi omega = 0.6) and deflated with P = I - A Q,
+ * Q = Z E^{-1} Z^T, E = Z^T A Z (Section 3, Eq. adef1, quadratic Bezier Z).
+ *
+ * Conventions (all entry points):
+ *  - Vectors hold the interior (Dirichlet-eliminated) B-spline coefficients,
+ *    lexicographic with x fastest: entry (ix, iy) at iy * n_x + ix, n_x =
+ *    n_el + p - 2.  Complex values are interleaved (re, im) pairs.
+ *  - Unless stated otherwise every pointer argument is a DEVICE pointer,
+ *    allocated and owned by the caller, 16-byte aligned (8-byte for
+ *    iga_c64), on the device that was current at iga_setup.  A misaligned or
+ *    NULL pointer returns IGA_E_INVALID and launches nothing.
+ *  - Work is enqueued on params.stream (NULL = the legacy default stream) and
+ *    is asynchronous with respect to the host, except where a function says it
+ *    synchronises.
+ *  - No exception crosses the ABI.  Errors are returned; the most recent
+ *    error text of a context is available from iga_last_error().
+ *  - The context owns its device workspace (allocated in iga_setup and
+ *    iga_solve, released in iga_destroy).
+ */
+#ifndef IGA_HELMHOLTZ_H
+#define IGA_HELMHOLTZ_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct { double re, im; } iga_c128;
+typedef struct { float re, im; } iga_c64;
+
+typedef enum {
+  IGA_OK = 0,
+  IGA_NOT_CONVERGED = 1,   /* solve reached maxit; outputs are still valid          */
+  IGA_E_INVALID = -1,      /* bad argument (NULL, misaligned, out of range)          */
+  IGA_E_CUDA = -2,         /* a CUDA runtime call failed                              */
+  IGA_E_OOM = -3,          /* device allocation failed                                */
+  IGA_E_BREAKDOWN = -4,    /* Arnoldi produced an unusable basis vector               */
+  IGA_E_NONFINITE = -5,    /* NaN or Inf met in the iteration                         */
+  IGA_E_TIMEOUT = -6,      /* a bounded device wait gave up                           */
+  IGA_E_UNSUPPORTED = -7   /* valid request that this build does not implement       */
+} iga_status;
+
+#define IGA_MAX_LINES 8
+
+/* Problem and solver parameters.  Fill with iga_default_params() first. */
+typedef struct {
+  int dim;                 /* 1 or 2 (unit interval / unit square)                        */
+  int p;                   /* B-spline degree, 1..5 (Section 2.3.1)                       */
+  int n_el;                /* elements per direction; open uniform knots i/n_el           */
+  /* wave number: k(x,y) = k_values[#lines with a*x + b*y + c >= 0]; n_lines = 0 is
+     the constant k_values[0].  Lines must not cross inside the domain.        */
+  int n_lines;             /* 0..IGA_MAX_LINES (2D only when > 0)                         */
+  double lines[IGA_MAX_LINES][3];
+  double k_values[IGA_MAX_LINES + 1];
+  double beta1, beta2;     /* CSLP M = S - (beta1 - i beta2) M^{k^2}                       */
+  double eps;              /* ADP weight epsilon (Section 3, weighted stencil)            */
+  int nu_pre, nu_post;     /* damped-Jacobi sweeps before / after coarse correction        */
+  double omega;            /* Jacobi damping, 0.6 in the paper                            */
+  int n_vcycles;           /* V-cycles per preconditioner application                     */
+  int precision;           /* 0: FP64 throughout, GMRES left-preconditioned
+                              1: FP32 V-cycle (FP32 storage and accumulation) inside
+                                 FP64 flexible GMRES                                      */
+  int flexible;            /* 1: right-preconditioned FGMRES even in FP64 (precision 1
+                              implies it)                                                 */
+  void* stream;            /* cudaStream_t for all work of this context                   */
+} iga_params;
+
+typedef struct iga_ctx iga_ctx;
+
+/* Fill *prm with the defaults: dim 2, p 3, n_el 32, k 10, beta (1, 0.5), eps 0,
+   nu 1/1, omega 0.6, one V-cycle, FP64, stream NULL. Host pointer. */
+void iga_default_params(iga_params* prm);
+
+/* Build everything the solve needs on the device (Sections 2.3, 3): knots,
+   Gauss tables, 1D band matrices and transfer operators per multigrid level,
+   the coarsest-level inverse, Z and the factorised E.  Synchronises.
+   prm is a host pointer; *out receives a context to release with iga_destroy.
+   Errors: IGA_E_INVALID for out-of-range parameters, IGA_E_OOM, IGA_E_CUDA. */
+iga_status iga_setup(const iga_params* prm, iga_ctx** out);
+void iga_destroy(iga_ctx* ctx);
+
+/* Sizes.  n = n_x^dim fine dofs, m = floor(n_x/2)^dim deflation dofs. */
+size_t iga_ndof(const iga_ctx* ctx);
+size_t iga_coarse_ndof(const iga_ctx* ctx);
+int iga_num_levels(const iga_ctx* ctx);
+int iga_level_nx(const iga_ctx* ctx, int level);       /* interior functions per direction */
+int iga_level_nel(const iga_ctx* ctx, int level);
+const char* iga_status_str(iga_status s);
+const char* iga_last_error(const iga_ctx* ctx);
+
+/* Copy the open knot vector of multigrid level `level` (n_el_l + 2p + 1 doubles,
+   computed on the device as i/n_el_l) to the HOST buffer out (capacity cap).
+   Synchronises. */
+iga_status iga_get_knots(iga_ctx* ctx, int level, double* out, int cap);
+/* Copy the 1D interior band matrix of level `level` to the HOST buffer out:
+   which = 0 stiffness K, 1 mass M; layout [n_x][2p+1], out[i*(2p+1)+d+p] =
+   Mat[i][i+d] (zero outside the matrix). Synchronises. */
+iga_status iga_get_band(iga_ctx* ctx, int level, int which, double* out, size_t cap);
+/* Copy the knot-insertion prolongation of level l -> l+1 as a dense HOST
+   matrix [n_x(l)][n_x(l+1)] (interior rows and columns). Synchronises. */
+iga_status iga_get_prolongation(iga_ctx* ctx, int level, double* out, size_t cap);
+
+/* y = A x, A = S - M^{k^2} (Section 2.3), matrix-free: constant k by banded
+   1D passes (K_x, M_x then M_y, K_y), variable k by per-element sum-factorised
+   quadrature with k evaluated at the Gauss points.  x, y: n complex128, must
+   not alias. */
+iga_status iga_apply_A(iga_ctx* ctx, const iga_c128* x, iga_c128* y);
+
+/* y = M_beta x on multigrid level `level` (0 = finest), M_beta =
+   S_l - (beta1 - i beta2) M^{k^2}_l by rediscretisation (Section 3, CSLP
+   equation).  FP64. */
+iga_status iga_apply_Mshift(iga_ctx* ctx, int level, const iga_c128* x, iga_c128* y);
+
+/* x_out = x_in + omega D^{-1} (b - M_beta x_in), D = diag(M_beta), `sweeps`
+   times on level `level` (Section 3: damped Jacobi).  x_out receives the
+   result; x_in is used as scratch and overwritten when sweeps > 1. FP64. */
+iga_status iga_jacobi(iga_ctx* ctx, int level, const iga_c128* b, iga_c128* x_in,
+                      iga_c128* x_out, int sweeps);
+
+/* Multigrid transfers between level l (fine) and l+1 (coarse): knot-insertion
+   prolongation P_l (Section 4.2: linear interpolation is the p = 1 case).
+   restrict: coarse = P_l^T fine.  prolong_add: fine += P_l coarse.  FP64. */
+iga_status iga_restrict(iga_ctx* ctx, int level, const iga_c128* fine, iga_c128* coarse);
+iga_status iga_prolong_add(iga_ctx* ctx, int level, const iga_c128* coarse, iga_c128* fine);
+
+/* Coarsest-level solve x = M_beta^{-1} b with the dense inverse built at setup. */
+iga_status iga_coarse_solve(iga_ctx* ctx, const iga_c128* b, iga_c128* x);
+
+/* z ~ M_beta^{-1} r by n_vcycles V-cycles (Section 3; Section 4.2). r, z: n
+   complex128.  In precision 1 the cycle runs in FP32 and r, z are converted. */
+iga_status iga_vcycle_cslp(iga_ctx* ctx, const iga_c128* r, iga_c128* z);
+
+/* Deflation pieces (Section 3, Eq. adef1 and the Z / Z^T stencils):
+   zt: c = Z^T x (n -> m);  z: x = Z c (m -> n);  esolve: s = E^{-1} t (m);
+   deflate: y = P x = x - A Z E^{-1} Z^T x (n). */
+iga_status iga_zt(iga_ctx* ctx, const iga_c128* x, iga_c128* c);
+iga_status iga_z(iga_ctx* ctx, const iga_c128* c, iga_c128* x);
+iga_status iga_esolve(iga_ctx* ctx, const iga_c128* t, iga_c128* s);
+iga_status iga_deflate(iga_ctx* ctx, const iga_c128* x, iga_c128* y);
+
+/* Unit load vector of a point source at (x0, y0): f_i = Phi_i(x0, y0)
+   (y0 ignored in 1D).  f: n complex128. */
+iga_status iga_load_point_source(iga_ctx* ctx, double x0, double y0, iga_c128* f);
+
+/* One modified Gram-Schmidt sweep (Arnoldi, Section 3 GMRES): for i = 0..j,
+   h[i] = v_i^H w, w -= h[i] v_i; then h[j+1] = ||w||.  V: column-major,
+   column i at V + i*ldv, n entries each.  w (n) is updated in place; h
+   (j+2 entries) is written in DEVICE memory.  Uses context scratch. */
+iga_status iga_mgs(iga_ctx* ctx, const iga_c128* V, size_t ldv, int j, iga_c128* w,
+                   iga_c128* h);
+
+/* Deflated, preconditioned GMRES (DEF1 reading of Section 3's deflated
+   system): GMRES on M~^{-1} P A x^ = M~^{-1} P f from x^ = 0 (or FGMRES on
+   P A M~^{-1} y = P f), then u = Q f + P^T x^.  Stops when the residual
+   GMRES minimises has dropped by `tol` (1e-7 in Section 4.3) or after maxit.
+   rhs, x: device, n complex128.  iters, res_hist (maxit+1 doubles, relative
+   residual estimate per iteration, entry 0 = 1) and true_res
+   (||f - A u|| / ||f||) are HOST pointers; res_hist and true_res may be NULL.
+   Synchronises.  Returns IGA_OK or IGA_NOT_CONVERGED, or an error. */
+iga_status iga_solve(iga_ctx* ctx, const iga_c128* rhs, iga_c128* x, double tol, int maxit,
+                     int* iters, double* res_hist, double* true_res);
+
+/* Same as iga_solve, but rhs and x are HOST pointers: the host->device and
+   device->host copies are part of the call. */
+iga_status iga_solve_host(iga_ctx* ctx, const iga_c128* rhs_host, iga_c128* x_host, double tol,
+                          int maxit, int* iters, double* res_hist, double* true_res);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IGA_HELMHOLTZ_H */

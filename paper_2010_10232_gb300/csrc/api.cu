@@ -1,0 +1,337 @@
+// C ABI of the IgA Helmholtz library (declared in include/iga_helmholtz.h).
+// Argument checking, context construction and dispatch to the kernels.
+#include "common.cuh"
+#include "bspline.cuh"
+#include <cmath>
+#include <new>
+
+static bool aligned16(const void* p) { return p && (((uintptr_t)p) & 15u) == 0; }
+
+extern "C" {
+
+void iga_default_params(iga_params* prm) {
+  if (!prm) return;
+  iga_params d{};
+  d.dim = 2;
+  d.p = 3;
+  d.n_el = 32;
+  d.n_lines = 0;
+  d.k_values[0] = 10.0;
+  d.beta1 = 1.0;
+  d.beta2 = 0.5;
+  d.eps = 0.0;
+  d.nu_pre = 1;
+  d.nu_post = 1;
+  d.omega = 0.6;
+  d.n_vcycles = 1;
+  d.precision = 0;
+  d.flexible = 0;
+  d.stream = nullptr;
+  *prm = d;
+}
+
+const char* iga_status_str(iga_status s) {
+  switch (s) {
+    case IGA_OK: return "IGA_OK";
+    case IGA_NOT_CONVERGED: return "IGA_NOT_CONVERGED";
+    case IGA_E_INVALID: return "IGA_E_INVALID";
+    case IGA_E_CUDA: return "IGA_E_CUDA";
+    case IGA_E_OOM: return "IGA_E_OOM";
+    case IGA_E_BREAKDOWN: return "IGA_E_BREAKDOWN";
+    case IGA_E_NONFINITE: return "IGA_E_NONFINITE";
+    case IGA_E_TIMEOUT: return "IGA_E_TIMEOUT";
+    case IGA_E_UNSUPPORTED: return "IGA_E_UNSUPPORTED";
+  }
+  return "unknown";
+}
+
+const char* iga_last_error(const iga_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+static iga_status alloc_level_vectors(iga_ctx* ctx) {
+  for (int l = 0; l < ctx->L; ++l) {
+    LevelData& L = ctx->lv[l];
+    L.vb = dalloc<double2>(ctx, L.n);
+    L.vx = dalloc<double2>(ctx, L.n);
+    L.vy = dalloc<double2>(ctx, L.n);
+    L.vr = dalloc<double2>(ctx, L.n);
+    L.fb = dalloc<float2>(ctx, L.n);
+    L.fx = dalloc<float2>(ctx, L.n);
+    L.fy = dalloc<float2>(ctx, L.n);
+    L.fr = dalloc<float2>(ctx, L.n);
+    if (!L.vb || !L.vx || !L.vy || !L.vr || !L.fb || !L.fx || !L.fy || !L.fr)
+      return set_err(ctx, IGA_E_OOM, "level vectors");
+  }
+  return IGA_OK;
+}
+
+iga_status iga_setup(const iga_params* prm, iga_ctx** out) {
+  if (!prm || !out) return IGA_E_INVALID;
+  *out = nullptr;
+  const iga_params& P = *prm;
+  if (P.dim != 1 && P.dim != 2) return IGA_E_INVALID;
+  if (P.p < 1 || P.p > IGA_MAXP) return IGA_E_INVALID;
+  if (P.n_el < 2 || P.n_el + P.p - 2 < 2) return IGA_E_INVALID;
+  if (P.n_lines < 0 || P.n_lines > IGA_MAX_LINES || (P.n_lines > 0 && P.dim != 2)) return IGA_E_INVALID;
+  if (!(P.omega > 0.0) || P.nu_pre < 0 || P.nu_post < 0 || P.n_vcycles < 1) return IGA_E_INVALID;
+  if (P.precision < 0 || P.precision > 1) return IGA_E_INVALID;
+  for (int l = 0; l <= P.n_lines; ++l)
+    if (!std::isfinite(P.k_values[l]) || P.k_values[l] < 0.0) return IGA_E_INVALID;
+  iga_ctx* ctx = new (std::nothrow) iga_ctx();
+  if (!ctx) return IGA_E_OOM;
+  ctx->prm = P;
+  ctx->dim = P.dim;
+  ctx->p = P.p;
+  ctx->Q = P.p + 1;
+  ctx->st = (cudaStream_t)P.stream;
+  ctx->vark = P.n_lines > 0;
+  ctx->kf.n_lines = P.n_lines;
+  for (int l = 0; l < IGA_MAX_LINES; ++l)
+    for (int c = 0; c < 3; ++c) ctx->kf.lines[l][c] = l < P.n_lines ? P.lines[l][c] : 0.0;
+  for (int l = 0; l <= IGA_MAX_LINES; ++l) ctx->kf.k2[l] = l <= P.n_lines ? P.k_values[l] * P.k_values[l] : 0.0;
+  ctx->k2const = P.k_values[0] * P.k_values[0];
+  ctx->sig = make_double2(P.beta1, -P.beta2);
+  iga_status s = IGA_OK;
+  do {
+    if (cudaGetDevice(&ctx->device) != cudaSuccess) { s = set_err(ctx, IGA_E_CUDA, "no CUDA device"); break; }
+    cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    if ((s = setup_levels(ctx)) != IGA_OK) break;
+    if (ctx->vark && ctx->dim == 2)
+      for (int l = 0; l < ctx->L && s == IGA_OK; ++l) s = setup_vark_diag(ctx, l);
+    if (s != IGA_OK) break;
+    if ((s = alloc_level_vectors(ctx)) != IGA_OK) break;
+    if ((s = setup_coarse_inverse(ctx)) != IGA_OK) break;
+    size_t n = ctx->lv[0].n;
+    ctx->w0 = dalloc<double2>(ctx, n);
+    ctx->w1 = dalloc<double2>(ctx, n);
+    ctx->w2 = dalloc<double2>(ctx, n);
+    ctx->w3 = dalloc<double2>(ctx, n);
+    ctx->fin = dalloc<float2>(ctx, n);
+    ctx->fout = dalloc<float2>(ctx, n);
+    ctx->partials = dalloc<double>(ctx, 4 * (size_t)(2 * ctx->num_sms) + 16);
+    if (!ctx->w0 || !ctx->w1 || !ctx->w2 || !ctx->w3 || !ctx->fin || !ctx->fout || !ctx->partials) {
+      s = set_err(ctx, IGA_E_OOM, "work vectors");
+      break;
+    }
+    if ((s = setup_deflation(ctx)) != IGA_OK) break;
+    cudaError_t e = cudaStreamSynchronize(ctx->st);
+    if (e != cudaSuccess) { s = set_err(ctx, IGA_E_CUDA, "setup: %s", cudaGetErrorString(e)); break; }
+  } while (0);
+  if (s != IGA_OK) {
+    fprintf(stderr, "iga_setup: %s: %s\n", iga_status_str(s), ctx->err.c_str());
+    delete ctx;
+    return s;
+  }
+  *out = ctx;
+  return IGA_OK;
+}
+
+void iga_destroy(iga_ctx* ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->st);
+  delete ctx;
+}
+
+size_t iga_ndof(const iga_ctx* ctx) { return ctx ? (size_t)ctx->lv[0].n : 0; }
+size_t iga_coarse_ndof(const iga_ctx* ctx) { return ctx ? ctx->m : 0; }
+int iga_num_levels(const iga_ctx* ctx) { return ctx ? ctx->L : 0; }
+int iga_level_nx(const iga_ctx* ctx, int level) {
+  return (ctx && level >= 0 && level < ctx->L) ? ctx->lv[level].nx : -1;
+}
+int iga_level_nel(const iga_ctx* ctx, int level) {
+  return (ctx && level >= 0 && level < ctx->L) ? ctx->lv[level].n_el : -1;
+}
+
+iga_status iga_get_knots(iga_ctx* ctx, int level, double* out, int cap) {
+  if (!ctx || !out || level < 0 || level >= ctx->L) return IGA_E_INVALID;
+  int len = ctx->lv[level].n_el + 2 * ctx->p + 1;
+  if (cap < len) return set_err(ctx, IGA_E_INVALID, "capacity %d < %d", cap, len);
+  CK(cudaMemcpyAsync(out, ctx->lv[level].knots, sizeof(double) * len, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return IGA_OK;
+}
+
+iga_status iga_get_band(iga_ctx* ctx, int level, int which, double* out, size_t cap) {
+  if (!ctx || !out || level < 0 || level >= ctx->L || which < 0 || which > 1) return IGA_E_INVALID;
+  size_t len = (size_t)ctx->lv[level].nx * (2 * ctx->p + 1);
+  if (cap < len) return set_err(ctx, IGA_E_INVALID, "capacity");
+  CK(cudaMemcpyAsync(out, which == 0 ? ctx->lv[level].K : ctx->lv[level].M, sizeof(double) * len,
+                     cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return IGA_OK;
+}
+
+iga_status iga_get_prolongation(iga_ctx* ctx, int level, double* out, size_t cap) {
+  if (!ctx || !out || level < 0 || level + 1 >= ctx->L) return IGA_E_INVALID;
+  const LevelData& F = ctx->lv[level];
+  const LevelData& C = ctx->lv[level + 1];
+  if (cap < (size_t)F.nx * C.nx) return set_err(ctx, IGA_E_INVALID, "capacity");
+  std::vector<double> pw((size_t)F.nx * F.wP);
+  std::vector<int> plo(F.nx);
+  CK(cudaMemcpyAsync(pw.data(), F.Pw, sizeof(double) * pw.size(), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaMemcpyAsync(plo.data(), F.Plo, sizeof(int) * plo.size(), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  for (size_t i = 0; i < (size_t)F.nx * C.nx; ++i) out[i] = 0.0;
+  for (int i = 0; i < F.nx; ++i)
+    for (int k = 0; k < F.wP; ++k) {
+      int j = plo[i] + k;
+      if (j >= 0 && j < C.nx) out[(size_t)i * C.nx + j] = pw[(size_t)i * F.wP + k];
+    }
+  return IGA_OK;
+}
+
+#define CHECK_CTX() do { if (!ctx) return IGA_E_INVALID; } while (0)
+#define CHECK_PTR(p) do { if (!aligned16(p)) return set_err(ctx, IGA_E_INVALID, "pointer %s NULL or not 16-byte aligned", #p); } while (0)
+
+iga_status iga_apply_A(iga_ctx* ctx, const iga_c128* x, iga_c128* y) {
+  CHECK_CTX(); CHECK_PTR(x); CHECK_PTR(y);
+  if ((const void*)x == (const void*)y) return set_err(ctx, IGA_E_INVALID, "x and y alias");
+  return op_apply<double>(ctx, 0, OP_A, (const double2*)x, (double2*)y, nullptr, EPI_Y, nullptr, 0.0);
+}
+
+iga_status iga_apply_Mshift(iga_ctx* ctx, int level, const iga_c128* x, iga_c128* y) {
+  CHECK_CTX(); CHECK_PTR(x); CHECK_PTR(y);
+  if (level < 0 || level >= ctx->L) return set_err(ctx, IGA_E_INVALID, "level");
+  return op_apply<double>(ctx, level, OP_MB, (const double2*)x, (double2*)y, nullptr, EPI_Y, nullptr, 0.0);
+}
+
+iga_status iga_jacobi(iga_ctx* ctx, int level, const iga_c128* b, iga_c128* x_in, iga_c128* x_out, int sweeps) {
+  CHECK_CTX(); CHECK_PTR(b); CHECK_PTR(x_in); CHECK_PTR(x_out);
+  if (level < 0 || level >= ctx->L || sweeps < 1) return set_err(ctx, IGA_E_INVALID, "level/sweeps");
+  double2* a = (double2*)x_in;
+  double2* c = (double2*)x_out;
+  // ping-pong so that the last sweep writes x_out
+  double2* src = (sweeps & 1) ? a : c;
+  double2* dst = (sweeps & 1) ? c : a;
+  if (src != a) CK(cudaMemcpyAsync(src, a, sizeof(double2) * ctx->lv[level].n, cudaMemcpyDeviceToDevice, ctx->st));
+  for (int s = 0; s < sweeps; ++s) {
+    TRY(op_apply<double>(ctx, level, OP_MB, src, dst, nullptr, EPI_JACOBI, (const double2*)b, ctx->prm.omega));
+    std::swap(src, dst);
+  }
+  return IGA_OK;
+}
+
+iga_status iga_restrict(iga_ctx* ctx, int level, const iga_c128* fine, iga_c128* coarse) {
+  CHECK_CTX(); CHECK_PTR(fine); CHECK_PTR(coarse);
+  if (level < 0 || level + 1 >= ctx->L) return set_err(ctx, IGA_E_INVALID, "level");
+  return mg_restrict<double>(ctx, level, (const double2*)fine, (double2*)coarse);
+}
+
+iga_status iga_prolong_add(iga_ctx* ctx, int level, const iga_c128* coarse, iga_c128* fine) {
+  CHECK_CTX(); CHECK_PTR(fine); CHECK_PTR(coarse);
+  if (level < 0 || level + 1 >= ctx->L) return set_err(ctx, IGA_E_INVALID, "level");
+  return mg_prolong_add<double>(ctx, level, (const double2*)coarse, (double2*)fine);
+}
+
+iga_status iga_coarse_solve(iga_ctx* ctx, const iga_c128* b, iga_c128* x) {
+  CHECK_CTX(); CHECK_PTR(b); CHECK_PTR(x);
+  return mg_coarse<double>(ctx, (const double2*)b, (double2*)x);
+}
+
+iga_status iga_vcycle_cslp(iga_ctx* ctx, const iga_c128* r, iga_c128* z) {
+  CHECK_CTX(); CHECK_PTR(r); CHECK_PTR(z);
+  if ((const void*)r == (const void*)z) return set_err(ctx, IGA_E_INVALID, "r and z alias");
+  if (ctx->prm.precision == 0) return mg_vcycle<double>(ctx, (const double2*)r, (double2*)z);
+  size_t n = ctx->lv[0].n;
+  launch_convert_d2f((const double2*)r, ctx->fin, n, ctx->st);
+  TRY(mg_vcycle<float>(ctx, ctx->fin, ctx->fout));
+  launch_convert_f2d(ctx->fout, (double2*)z, n, ctx->st);
+  CKL();
+  return IGA_OK;
+}
+
+iga_status iga_zt(iga_ctx* ctx, const iga_c128* x, iga_c128* c) {
+  CHECK_CTX(); CHECK_PTR(x); CHECK_PTR(c);
+  return defl_zt(ctx, (const double2*)x, (double2*)c);
+}
+iga_status iga_z(iga_ctx* ctx, const iga_c128* c, iga_c128* x) {
+  CHECK_CTX(); CHECK_PTR(x); CHECK_PTR(c);
+  return defl_z(ctx, (const double2*)c, (double2*)x);
+}
+iga_status iga_esolve(iga_ctx* ctx, const iga_c128* t, iga_c128* s) {
+  CHECK_CTX(); CHECK_PTR(t); CHECK_PTR(s);
+  if ((const void*)t == (const void*)s) return set_err(ctx, IGA_E_INVALID, "t and s alias");
+  return defl_esolve(ctx, (const double2*)t, (double2*)s);
+}
+iga_status iga_deflate(iga_ctx* ctx, const iga_c128* x, iga_c128* y) {
+  CHECK_CTX(); CHECK_PTR(x); CHECK_PTR(y);
+  if ((const void*)x == (const void*)y) return set_err(ctx, IGA_E_INVALID, "x and y alias");
+  return defl_apply(ctx, (const double2*)x, (double2*)y);
+}
+
+__global__ void k_point_source(const double* t, int n_el, int p, int nx, int dim, double x0, double y0,
+                               double2* f);
+
+iga_status iga_load_point_source(iga_ctx* ctx, double x0, double y0, iga_c128* f) {
+  CHECK_CTX(); CHECK_PTR(f);
+  if (!(x0 >= 0.0 && x0 <= 1.0) || (ctx->dim == 2 && !(y0 >= 0.0 && y0 <= 1.0)))
+    return set_err(ctx, IGA_E_INVALID, "source outside the domain");
+  const LevelData& L = ctx->lv[0];
+  CK(cudaMemsetAsync(f, 0, sizeof(double2) * L.n, ctx->st));
+  k_point_source<<<1, 32, 0, ctx->st>>>(L.knots, L.n_el, ctx->p, L.nx, ctx->dim, x0, y0, (double2*)f);
+  CKL();
+  return IGA_OK;
+}
+
+iga_status iga_mgs(iga_ctx* ctx, const iga_c128* V, size_t ldv, int j, iga_c128* w, iga_c128* h) {
+  CHECK_CTX(); CHECK_PTR(V); CHECK_PTR(w); CHECK_PTR(h);
+  if (j < 0 || ldv < iga_ndof(ctx)) return set_err(ctx, IGA_E_INVALID, "j / ldv");
+  return kry_mgs(ctx, (const double2*)V, ldv, j, (double2*)w, (double2*)h);
+}
+
+iga_status iga_solve(iga_ctx* ctx, const iga_c128* rhs, iga_c128* x, double tol, int maxit, int* iters,
+                     double* res_hist, double* true_res) {
+  CHECK_CTX(); CHECK_PTR(rhs); CHECK_PTR(x);
+  if (maxit < 1 || maxit > 1000 || !(tol >= 0.0)) return set_err(ctx, IGA_E_INVALID, "tol / maxit");
+  if ((const void*)rhs == (const void*)x) return set_err(ctx, IGA_E_INVALID, "rhs and x alias");
+  return kry_solve(ctx, (const double2*)rhs, (double2*)x, tol, maxit, iters, res_hist, true_res);
+}
+
+iga_status iga_solve_host(iga_ctx* ctx, const iga_c128* rhs_host, iga_c128* x_host, double tol, int maxit,
+                          int* iters, double* res_hist, double* true_res) {
+  CHECK_CTX();
+  if (!rhs_host || !x_host) return set_err(ctx, IGA_E_INVALID, "NULL host pointer");
+  if (ctx->maxit_alloc < 0 && maxit > 0) { /* workspace is allocated by the solve itself */ }
+  size_t n = ctx->lv[0].n;
+  double2* f = ctx->hf;
+  double2* u = ctx->hu;
+  if (!f) {
+    ctx->hf = f = dalloc<double2>(ctx, n);
+    ctx->hu = u = dalloc<double2>(ctx, n);
+    if (!f || !u) return set_err(ctx, IGA_E_OOM, "host-solve buffers");
+  }
+  CK(cudaMemcpyAsync(f, rhs_host, sizeof(double2) * n, cudaMemcpyHostToDevice, ctx->st));
+  iga_status s = kry_solve(ctx, f, u, tol, maxit, iters, res_hist, true_res);
+  if (s < 0) return s;
+  CK(cudaMemcpyAsync(x_host, u, sizeof(double2) * n, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return s;
+}
+
+}  // extern "C"
+
+// Point-source load: f_i = Phi_i(x0, y0), evaluated by Cox-de Boor on the span
+// that contains the source (the right end point belongs to the last span).
+__global__ void k_point_source(const double* t, int n_el, int p, int nx, int dim, double x0, double y0,
+                               double2* f) {
+  if (threadIdx.x != 0) return;
+  double vx[IGA_MAXP + 1], vy[IGA_MAXP + 1], d[IGA_MAXP + 1];
+  int sx = find_span(t, n_el, p, x0);
+  active_basis(t, p, sx, x0, vx, d);
+  if (dim == 1) {
+    for (int a = 0; a <= p; ++a) {
+      int i = sx - p + a - 1;        // interior index of full function sx-p+a
+      if (i >= 0 && i < nx) f[i] = make_double2(vx[a], 0.0);
+    }
+    return;
+  }
+  int sy = find_span(t, n_el, p, y0);
+  active_basis(t, p, sy, y0, vy, d);
+  for (int b = 0; b <= p; ++b) {
+    int iy = sy - p + b - 1;
+    if (iy < 0 || iy >= nx) continue;
+    for (int a = 0; a <= p; ++a) {
+      int ix = sx - p + a - 1;
+      if (ix >= 0 && ix < nx) f[(size_t)iy * nx + ix] = make_double2(vy[b] * vx[a], 0.0);
+    }
+  }
+}

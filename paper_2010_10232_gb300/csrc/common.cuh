@@ -1,0 +1,212 @@
+// Shared device helpers and the internal context of the IgA Helmholtz library.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/iga_helmholtz.h"
+
+#define IGA_MAXP 5
+#define IGA_MAXQ (IGA_MAXP + 1)
+#define IGA_MAX_LEVELS 16
+
+// ------------------------------------------------------------------ complex
+template <typename T> struct cplx;
+template <> struct cplx<double> { using t = double2; };
+template <> struct cplx<float>  { using t = float2; };
+
+__host__ __device__ __forceinline__ double2 mkc(double r, double i) { return make_double2(r, i); }
+__host__ __device__ __forceinline__ float2  mkc(float r, float i)  { return make_float2(r, i); }
+template <typename C> __host__ __device__ __forceinline__ C czero();
+template <> __host__ __device__ __forceinline__ double2 czero<double2>() { return make_double2(0.0, 0.0); }
+template <> __host__ __device__ __forceinline__ float2  czero<float2>()  { return make_float2(0.f, 0.f); }
+
+__host__ __device__ __forceinline__ double2 operator+(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ double2 operator-(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2  operator+(float2 a, float2 b)   { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2  operator-(float2 a, float2 b)   { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ double2 operator*(double s, double2 a)  { return make_double2(s * a.x, s * a.y); }
+__host__ __device__ __forceinline__ float2  operator*(float s, float2 a)    { return make_float2(s * a.x, s * a.y); }
+__host__ __device__ __forceinline__ double2 cmul(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__host__ __device__ __forceinline__ float2  cmul(float2 a, float2 b)   { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+// conj(a) * b
+__host__ __device__ __forceinline__ double2 cconjmul(double2 a, double2 b) { return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x); }
+// acc + s * a   (real s)
+__host__ __device__ __forceinline__ double2 cfma(double s, double2 a, double2 acc) { return make_double2(fma(s, a.x, acc.x), fma(s, a.y, acc.y)); }
+__host__ __device__ __forceinline__ float2  cfma(float s, float2 a, float2 acc)    { return make_float2(fmaf(s, a.x, acc.x), fmaf(s, a.y, acc.y)); }
+__host__ __device__ __forceinline__ double2 cinv(double2 a) { double d = a.x * a.x + a.y * a.y; return make_double2(a.x / d, -a.y / d); }
+__host__ __device__ __forceinline__ float2  cinv(float2 a)  { float d = a.x * a.x + a.y * a.y; return make_float2(a.x / d, -a.y / d); }
+__host__ __device__ __forceinline__ double2 tod(float2 a) { return make_double2((double)a.x, (double)a.y); }
+__host__ __device__ __forceinline__ float2  tof(double2 a) { return make_float2((float)a.x, (float)a.y); }
+template <typename C> __host__ __device__ __forceinline__ C cconv(double2 a);
+template <> __host__ __device__ __forceinline__ double2 cconv<double2>(double2 a) { return a; }
+template <> __host__ __device__ __forceinline__ float2  cconv<float2>(double2 a)  { return tof(a); }
+
+// ------------------------------------------------------------------ k field
+struct KFieldDev {
+  int n_lines;
+  double lines[IGA_MAX_LINES][3];
+  double k2[IGA_MAX_LINES + 1];   // squared wave numbers per layer
+};
+
+// k^2 at (x, y): layer = number of lines with ((a*x) + (b*y)) + c >= 0, evaluated
+// without contraction so that both sides of a comparison round identically.
+__device__ __forceinline__ double kfield_k2(const KFieldDev& kf, double x, double y) {
+  int cnt = 0;
+  for (int l = 0; l < kf.n_lines; ++l) {
+    double s = __dadd_rn(__dadd_rn(__dmul_rn(kf.lines[l][0], x), __dmul_rn(kf.lines[l][1], y)), kf.lines[l][2]);
+    cnt += (s >= 0.0);
+  }
+  return kf.k2[cnt];
+}
+
+// ------------------------------------------------------------------ context
+struct LevelData {
+  int n_el = 0, nx = 0, ny = 1, n = 0;
+  double* knots = nullptr;       // n_el + 2p + 1
+  double* xq = nullptr;          // [n_el][Q] Gauss points
+  double* wq = nullptr;          // [n_el][Q] Gauss weights (scaled by span length / 2)
+  double* B = nullptr;           // [n_el][Q][p+1] basis values at Gauss points
+  double* D = nullptr;           // [n_el][Q][p+1] derivatives
+  float* Bf = nullptr;           // FP32 copies for the mixed-precision operator
+  float* wqf = nullptr;
+  double* K = nullptr;           // band [nx][2p+1]
+  double* M = nullptr;
+  float* Kf = nullptr;
+  float* Mf = nullptr;
+  // transfer to the next coarser level (absent on the coarsest)
+  int wP = 0, wR = 0;
+  double* Pw = nullptr; int* Plo = nullptr;   // fine row i: coarse cols Plo[i] .. +wP
+  double* Rw = nullptr; int* Rlo = nullptr;   // coarse row j: fine rows Rlo[j] .. +wR
+  float* Pwf = nullptr; float* Rwf = nullptr;
+  float* k2qf = nullptr;                      // (unused unless variable k) reserved
+  // variable k: inverse diagonal of M_beta
+  double2* dinv = nullptr;
+  float2* dinvf = nullptr;
+  // V-cycle work vectors
+  double2 *vb = nullptr, *vx = nullptr, *vy = nullptr, *vr = nullptr;
+  float2 *fb = nullptr, *fx = nullptr, *fy = nullptr, *fr = nullptr;
+};
+
+struct DevBuf {   // tracked allocation list
+  std::vector<void*> ptrs;
+  ~DevBuf() { for (void* p : ptrs) cudaFree(p); }
+};
+
+struct iga_ctx {
+  iga_params prm{};
+  int dim = 2, p = 3, L = 0, Q = 4;
+  bool vark = false;
+  KFieldDev kf{};
+  double k2const = 0.0;              // k^2 when constant
+  double2 sig{};                     // beta1 - i beta2
+  LevelData lv[IGA_MAX_LEVELS];
+  cudaStream_t st = nullptr;
+  int device = 0;
+  int num_sms = 148;
+  // coarsest level dense inverse
+  int nc = 0;
+  double2* cinv = nullptr;
+  float2* cinvf = nullptr;
+  // deflation (ADP)
+  int mx = 0;
+  size_t m = 0;
+  double* kc = nullptr;              // 1D coarse Z^T K Z  [mx][mx] dense
+  double* mc = nullptr;              // 1D coarse Z^T M Z
+  double* fdmV = nullptr;            // generalised eigenvectors [mx][mx], row-major V[i][k]
+  double* fdmL = nullptr;            // eigenvalues [mx]
+  double2* ct = nullptr;             // m-sized scratch
+  double2* cs = nullptr;
+  double2* cw = nullptr;
+  // variable-k E (block tridiagonal, banded in y): see deflation.cu
+  int eblk = 0, enb = 0;             // block size (lines per block * mx), number of blocks
+  double2* eDinv = nullptr;          // [enb][bs][bs] inverse diagonal blocks
+  double2* eOff = nullptr;           // [enb][bs][bs] lower off-diagonal blocks E_{i,i-1}
+  // solve workspace
+  double2* w0 = nullptr;             // n-sized vectors
+  double2* w1 = nullptr;
+  double2* w2 = nullptr;
+  double2* w3 = nullptr;
+  float2* fin = nullptr;             // FP32 V-cycle input / output at level 0
+  float2* fout = nullptr;
+  double2* hf = nullptr;             // device copies for the host-pointer solve
+  double2* hu = nullptr;
+  double* partials = nullptr;        // reduction scratch [2 * IGA_RED_BLOCKS + 16]
+  int maxit_alloc = -1;
+  double2* Vb = nullptr;             // Krylov basis (n x (maxit+1))
+  double2* Zb = nullptr;             // FGMRES preconditioned vectors (n x maxit)
+  double2* H = nullptr;              // (maxit+1) x maxit, column-major
+  double* gstate = nullptr;          // cs[maxit], residual hist[maxit+1], scalars
+  double2* gsn = nullptr;            // sn[maxit]
+  double2* gg = nullptr;             // g[maxit+1]
+  double2* gy = nullptr;             // y[maxit]
+  int* gflag = nullptr;              // [0] converged, [1] nonfinite, [2] breakdown
+  int* hflag = nullptr;              // pinned host copy
+  double* hres = nullptr;            // pinned host copy of residual
+  DevBuf bufs;
+  std::string err;
+};
+
+#define IGA_RED_BLOCKS 296
+#define IGA_RED_THREADS 256
+
+// ------------------------------------------------------------------ host helpers
+iga_status set_err(iga_ctx* c, iga_status s, const char* fmt, ...);
+template <typename T> inline T* dalloc(iga_ctx* c, size_t count) {
+  void* p = nullptr;
+  if (count == 0) count = 1;
+  if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+  c->bufs.ptrs.push_back(p);
+  return (T*)p;
+}
+
+#define CK(call)                                                                            \
+  do {                                                                                      \
+    cudaError_t e__ = (call);                                                               \
+    if (e__ != cudaSuccess) return set_err(ctx, IGA_E_CUDA, "%s: %s", #call, cudaGetErrorString(e__)); \
+  } while (0)
+#define CKL()                                                                               \
+  do {                                                                                      \
+    cudaError_t e__ = cudaGetLastError();                                                   \
+    if (e__ != cudaSuccess) return set_err(ctx, IGA_E_CUDA, "launch: %s", cudaGetErrorString(e__)); \
+  } while (0)
+#define TRY(x) do { iga_status s__ = (x); if (s__ != IGA_OK) return s__; } while (0)
+
+inline unsigned cdiv(size_t a, size_t b) { return (unsigned)((a + b - 1) / b); }
+
+// ------------------------------------------------------------------ internal API
+// setup.cu
+iga_status setup_levels(iga_ctx* ctx);
+// operator.cu
+template <typename T>
+iga_status op_apply(iga_ctx* ctx, int level, int which, const typename cplx<T>::t* x,
+                    typename cplx<T>::t* y, const typename cplx<T>::t* z, int epi,
+                    const typename cplx<T>::t* b, double omega);
+iga_status setup_vark_diag(iga_ctx* ctx, int level);
+// op "which": 0 = A (c = -1), 1 = M_beta (c = -sigma)
+enum { OP_A = 0, OP_MB = 1 };
+// epilogues
+enum { EPI_Y = 0, EPI_ZMINUS = 1, EPI_JACOBI = 2 };
+// mg.cu
+template <typename T> iga_status mg_vcycle(iga_ctx* ctx, const typename cplx<T>::t* r, typename cplx<T>::t* z);
+template <typename T> iga_status mg_restrict(iga_ctx* ctx, int l, const typename cplx<T>::t* f, typename cplx<T>::t* c);
+template <typename T> iga_status mg_prolong_add(iga_ctx* ctx, int l, const typename cplx<T>::t* c, typename cplx<T>::t* f);
+template <typename T> iga_status mg_coarse(iga_ctx* ctx, const typename cplx<T>::t* b, typename cplx<T>::t* x);
+template <typename T> iga_status mg_jacobi0(iga_ctx* ctx, int l, const typename cplx<T>::t* b, typename cplx<T>::t* x);
+iga_status setup_coarse_inverse(iga_ctx* ctx);
+// deflation.cu
+iga_status setup_deflation(iga_ctx* ctx);
+iga_status defl_zt(iga_ctx* ctx, const double2* x, double2* c);
+iga_status defl_z(iga_ctx* ctx, const double2* c, double2* x);
+iga_status defl_esolve(iga_ctx* ctx, const double2* t, double2* s);
+iga_status defl_apply(iga_ctx* ctx, const double2* x, double2* y);        // y = P x
+iga_status defl_q(iga_ctx* ctx, const double2* x, double2* y);            // y = Q x
+// krylov.cu
+iga_status kry_mgs(iga_ctx* ctx, const double2* V, size_t ldv, int j, double2* w, double2* h);
+iga_status kry_solve(iga_ctx* ctx, const double2* f, double2* x, double tol, int maxit, int* iters,
+                     double* hist, double* true_res);
+iga_status vec_norm(iga_ctx* ctx, const double2* x, size_t n, double* dev_out);
+void launch_convert_d2f(const double2* a, float2* b, size_t n, cudaStream_t st);
+void launch_convert_f2d(const float2* a, double2* b, size_t n, cudaStream_t st);

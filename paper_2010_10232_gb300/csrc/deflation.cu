@@ -1,0 +1,439 @@
+// Adapted deflation preconditioner (Section 3: Eq. adef1, P = I - A Q,
+// Q = Z E^{-1} Z^T, E = Z^T A Z, with the quadratic rational-Bezier stencil
+// for Z and its epsilon-weighted variant).
+//
+// Index convention: 1-based interior indices, coarse dof J sits at fine dof
+// 2J; m_x = floor(n_x / 2); stencil terms outside the index ranges are
+// dropped.  Z^T row = (1, 4, 6 - eps, 4, 1)/8 on fine 2J-2 .. 2J+2 (the
+// paper's printed row repeats an index; it is read as the transpose of Z).
+// 2D: Z = Z_y (x) Z_x.
+//
+// E^{-1} for constant k by fast diagonalisation: E = Mc (x) Kc + Kc (x) Mc
+// - k^2 Mc (x) Mc with the 1D Galerkin matrices Kc = Z^T K Z, Mc = Z^T M Z.
+// The generalised eigenvectors V (V^T Mc V = I, V^T Kc V = diag(lambda))
+// give E^{-1} = (V (x) V) diag(1 / (lambda_i + lambda_j - k^2)) (V (x) V)^T,
+// applied as four real-by-complex GEMMs on the m_x x m_x coarse grid.
+#include "common.cuh"
+#include <cmath>
+
+// ------------------------------------------------------------------ Z, Z^T
+__device__ __forceinline__ double zt_w(int a, double eps) {   // a in -2..2
+  const double w[5] = {1.0 / 8.0, 4.0 / 8.0, 0.0, 4.0 / 8.0, 1.0 / 8.0};
+  return a == 0 ? (6.0 - eps) / 8.0 : w[a + 2];
+}
+
+// c = Z^T x
+__global__ void k_zt(int nx, int ny, int mx, int my, double eps, const double2* x, double2* c) {
+  size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (j >= (size_t)mx * my) return;
+  int jy = (int)(j / mx), jx = (int)(j - (size_t)jy * mx);
+  int fx = 2 * jx + 1, fy = 2 * jy + 1;   // 0-based fine index of coarse centre (1-based 2J)
+  double2 acc = make_double2(0.0, 0.0);
+  if (ny == 1) {
+    for (int a = -2; a <= 2; ++a) {
+      int ix = fx + a;
+      if (ix >= 0 && ix < nx) acc = cfma(zt_w(a, eps), x[ix], acc);
+    }
+  } else {
+    for (int b = -2; b <= 2; ++b) {
+      int iy = fy + b;
+      if (iy < 0 || iy >= ny) continue;
+      double2 row = make_double2(0.0, 0.0);
+      for (int a = -2; a <= 2; ++a) {
+        int ix = fx + a;
+        if (ix >= 0 && ix < nx) row = cfma(zt_w(a, eps), x[(size_t)iy * nx + ix], row);
+      }
+      acc = cfma(zt_w(b, eps), row, acc);
+    }
+  }
+  c[j] = acc;
+}
+
+// 1D Z row for fine (0-based) i: up to 3 (coarse index, weight) pairs
+__device__ __forceinline__ int z_row(int i, int m, double eps, int* idx, double* w) {
+  int I = i + 1, cnt = 0;
+  if ((I & 1) == 0) {
+    int J = I / 2;
+    int js[3] = {J - 1, J, J + 1};
+    double ws[3] = {1.0 / 8.0, (6.0 - eps) / 8.0, 1.0 / 8.0};
+    for (int t = 0; t < 3; ++t)
+      if (js[t] >= 1 && js[t] <= m) { idx[cnt] = js[t] - 1; w[cnt] = ws[t]; ++cnt; }
+  } else {
+    int js[2] = {(I - 1) / 2, (I + 1) / 2};
+    for (int t = 0; t < 2; ++t)
+      if (js[t] >= 1 && js[t] <= m) { idx[cnt] = js[t] - 1; w[cnt] = 0.5; ++cnt; }
+  }
+  return cnt;
+}
+
+// x = Z c
+__global__ void k_z(int nx, int ny, int mx, int my, double eps, const double2* c, double2* x) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i >= (size_t)nx * ny) return;
+  int iy = (int)(i / nx), ix = (int)(i - (size_t)iy * nx);
+  int cxi[3], cyi[3];
+  double wx[3], wy[3];
+  int nxc = z_row(ix, mx, eps, cxi, wx);
+  double2 acc = make_double2(0.0, 0.0);
+  if (ny == 1) {
+    for (int a = 0; a < nxc; ++a) acc = cfma(wx[a], c[cxi[a]], acc);
+  } else {
+    int nyc = z_row(iy, my, eps, cyi, wy);
+    for (int b = 0; b < nyc; ++b) {
+      double2 row = make_double2(0.0, 0.0);
+      for (int a = 0; a < nxc; ++a) row = cfma(wx[a], c[(size_t)cyi[b] * mx + cxi[a]], row);
+      acc = cfma(wy[b], row, acc);
+    }
+  }
+  x[i] = acc;
+}
+
+// Dense 1D coarse matrices Kc = Z^T K Z, Mc = Z^T M Z (thread per entry)
+__global__ void k_coarse_1d(int nx, int mx, int p, double eps, const double* K, const double* M, double* Kc,
+                            double* Mc) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= mx * mx) return;
+  int I = idx / mx, J = idx - I * mx;
+  int W = 2 * p + 1;
+  double kv = 0.0, mv = 0.0;
+  if (abs(I - J) <= (p + 4) / 2 + 1) {
+    int fi = 2 * I + 1, fj = 2 * J + 1;
+    for (int a = -2; a <= 2; ++a) {
+      int r = fi + a;
+      if (r < 0 || r >= nx) continue;
+      for (int b = -2; b <= 2; ++b) {
+        int c = fj + b;
+        if (c < 0 || c >= nx) continue;
+        int d = c - r;
+        if (d < -p || d > p) continue;
+        double w = zt_w(a, eps) * zt_w(b, eps);
+        kv += w * K[(size_t)r * W + d + p];
+        mv += w * M[(size_t)r * W + d + p];
+      }
+    }
+  }
+  Kc[idx] = kv;
+  Mc[idx] = mv;
+}
+
+// ------------------------------------------------------------------ dense helpers (setup)
+// In-place Cholesky A = L L^T of a dense SPD matrix (one block, right-looking).
+__global__ void k_cholesky(double* A, int n, int* info) {
+  __shared__ double piv;
+  for (int k = 0; k < n; ++k) {
+    if (threadIdx.x == 0) {
+      double d = A[(size_t)k * n + k];
+      if (!(d > 0.0)) { *info = 2; d = 1.0; }
+      piv = sqrt(d);
+      A[(size_t)k * n + k] = piv;
+    }
+    __syncthreads();
+    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) A[(size_t)i * n + k] /= piv;
+    __syncthreads();
+    int m = n - k - 1;
+    for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+      int i = k + 1 + idx / m, j = k + 1 + idx % m;
+      if (j <= i) A[(size_t)i * n + j] -= A[(size_t)i * n + k] * A[(size_t)j * n + k];
+    }
+    __syncthreads();
+  }
+}
+
+// X = L^{-1} B  (L lower triangular in the lower part of Lm), thread per column.
+__global__ void k_trsm_lower(const double* Lm, const double* B, double* X, int n) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  for (int i = 0; i < n; ++i) {
+    double s = B[(size_t)i * n + c];
+    for (int k = 0; k < i; ++k) s -= Lm[(size_t)i * n + k] * X[(size_t)k * n + c];
+    X[(size_t)i * n + c] = s / Lm[(size_t)i * n + i];
+  }
+}
+// X = L^{-T} B, thread per column
+__global__ void k_trsm_lower_t(const double* Lm, const double* B, double* X, int n) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  for (int i = n - 1; i >= 0; --i) {
+    double s = B[(size_t)i * n + c];
+    for (int k = i + 1; k < n; ++k) s -= Lm[(size_t)k * n + i] * X[(size_t)k * n + c];
+    X[(size_t)i * n + c] = s / Lm[(size_t)i * n + i];
+  }
+}
+__global__ void k_transpose(const double* A, double* B, int n) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < n * n) { int i = idx / n, j = idx - i * n; B[(size_t)j * n + i] = A[idx]; }
+}
+// pad an n x n symmetric matrix to np x np (np = n or n+1), symmetrised
+__global__ void k_pad_sym(const double* A, double* P, int n, int np) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= np * np) return;
+  int i = idx / np, j = idx - i * np;
+  P[idx] = (i < n && j < n) ? 0.5 * (A[(size_t)i * n + j] + A[(size_t)j * n + i]) : 0.0;
+}
+__global__ void k_eye_d(double* V, int n) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < n * n) V[idx] = (idx / n == idx % n) ? 1.0 : 0.0;
+}
+
+// ------------------------------------------------------------------ parallel cyclic Jacobi
+// Round r of the round-robin ordering pairs index positions (k, np-1-k).
+__device__ __forceinline__ int rr_index(int k, int r, int np) { return k == 0 ? 0 : 1 + (k - 1 + r) % (np - 1); }
+
+// Rotation (c, s) annihilating A[p][q]: G = [[c, s], [-s, c]], G^T A_pq G diagonal
+// (the symmetric 2x2 Schur decomposition).
+__global__ void k_jac_angles(const double* A, int np, int r, double* cs) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= np / 2) return;
+  int i1 = rr_index(k, r, np), i2 = rr_index(np - 1 - k, r, np);
+  int p = min(i1, i2), q = max(i1, i2);
+  double app = A[(size_t)p * np + p], aqq = A[(size_t)q * np + q], apq = A[(size_t)p * np + q];
+  double c = 1.0, s = 0.0;
+  if (apq != 0.0) {
+    double tau = (aqq - app) / (2.0 * apq);
+    double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+    c = 1.0 / sqrt(1.0 + t * t);
+    s = t * c;
+  }
+  cs[4 * k + 0] = c;
+  cs[4 * k + 1] = s;
+  cs[4 * k + 2] = p;
+  cs[4 * k + 3] = q;
+}
+
+// A_new = J^T A J over all 2x2 blocks of the pairing; V <- V J.
+__global__ void k_jac_apply(const double* A, double* An, double* V, int np, const double* cs) {
+  int h = np / 2;
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < h * h) {
+    int k1 = idx / h, k2 = idx - k1 * h;
+    double c1 = cs[4 * k1], s1 = cs[4 * k1 + 1], c2 = cs[4 * k2], s2 = cs[4 * k2 + 1];
+    int p1 = (int)cs[4 * k1 + 2], q1 = (int)cs[4 * k1 + 3], p2 = (int)cs[4 * k2 + 2], q2 = (int)cs[4 * k2 + 3];
+    double b00 = A[(size_t)p1 * np + p2], b01 = A[(size_t)p1 * np + q2];
+    double b10 = A[(size_t)q1 * np + p2], b11 = A[(size_t)q1 * np + q2];
+    // G1^T B
+    double t00 = c1 * b00 - s1 * b10, t01 = c1 * b01 - s1 * b11;
+    double t10 = s1 * b00 + c1 * b10, t11 = s1 * b01 + c1 * b11;
+    // (G1^T B) G2
+    An[(size_t)p1 * np + p2] = t00 * c2 - t01 * s2;
+    An[(size_t)p1 * np + q2] = t00 * s2 + t01 * c2;
+    An[(size_t)q1 * np + p2] = t10 * c2 - t11 * s2;
+    An[(size_t)q1 * np + q2] = t10 * s2 + t11 * c2;
+  }
+  int v = idx - h * h;
+  if (v >= 0 && v < np * h) {
+    int row = v / h, k = v - row * h;
+    double c = cs[4 * k], s = cs[4 * k + 1];
+    int p = (int)cs[4 * k + 2], q = (int)cs[4 * k + 3];
+    double vp = V[(size_t)row * np + p], vq = V[(size_t)row * np + q];
+    V[(size_t)row * np + p] = c * vp - s * vq;
+    V[(size_t)row * np + q] = s * vp + c * vq;
+  }
+}
+
+// off-diagonal and total squared Frobenius norm (one block)
+__global__ void k_offnorm(const double* A, int np, double* out) {
+  __shared__ double so[256], st[256];
+  double o = 0.0, t = 0.0;
+  for (int idx = threadIdx.x; idx < np * np; idx += blockDim.x) {
+    double v = A[idx];
+    t += v * v;
+    if (idx / np != idx % np) o += v * v;
+  }
+  so[threadIdx.x] = o;
+  st[threadIdx.x] = t;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) { so[threadIdx.x] += so[threadIdx.x + s]; st[threadIdx.x] += st[threadIdx.x + s]; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) { out[0] = so[0]; out[1] = st[0]; }
+}
+
+__global__ void k_diag_extract(const double* A, int np, int n, double* lam) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) lam[i] = A[(size_t)i * np + i];
+}
+// W (np x np) -> n x n top-left block
+__global__ void k_crop(const double* W, int np, int n, double* out) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < n * n) { int i = idx / n, j = idx - i * n; out[idx] = W[(size_t)i * np + j]; }
+}
+
+// ------------------------------------------------------------------ FDM apply GEMMs
+// out[i][j] = sum_k op(R)[i][k] X[k][j]  (LEFT)   or  sum_k X[i][k] op(R)[k][j]  (RIGHT)
+// R real m x m (row-major), X complex rows x cols.  TRANS: op(R) = R^T.
+// With DIVIDE the result is divided by lam_y[i] + lam_x[j] - k2 (lam_y = 0 in 1D).
+template <bool LEFT, bool TRANS, bool DIVIDE>
+__global__ void k_fdm_gemm(const double* R, const double2* X, double2* out, int rows, int cols,
+                           const double* lam_y, const double* lam_x, double k2) {
+  constexpr int TS = 16;
+  __shared__ double Rs[TS][TS + 1];
+  __shared__ double2 Xs[TS][TS + 1];
+  int ty = threadIdx.y, tx = threadIdx.x;
+  int i = blockIdx.y * TS + ty, j = blockIdx.x * TS + tx;
+  int K = LEFT ? rows : cols;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int k0 = 0; k0 < K; k0 += TS) {
+    if (LEFT) {
+      int ri = blockIdx.y * TS + ty, rk = k0 + tx;   // op(R)[ri][rk]
+      double v = 0.0;
+      if (ri < rows && rk < K) v = TRANS ? R[(size_t)rk * rows + ri] : R[(size_t)ri * rows + rk];
+      Rs[ty][tx] = v;
+      int xk = k0 + ty, xj = blockIdx.x * TS + tx;
+      Xs[ty][tx] = (xk < K && xj < cols) ? X[(size_t)xk * cols + xj] : make_double2(0.0, 0.0);
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < TS; ++kk) acc = cfma(Rs[ty][kk], Xs[kk][tx], acc);
+    } else {
+      int xi = blockIdx.y * TS + ty, xk = k0 + tx;
+      Xs[ty][tx] = (xi < rows && xk < K) ? X[(size_t)xi * cols + xk] : make_double2(0.0, 0.0);
+      int rk = k0 + ty, rj = blockIdx.x * TS + tx;   // op(R)[rk][rj]
+      double v = 0.0;
+      if (rk < K && rj < cols) v = TRANS ? R[(size_t)rj * cols + rk] : R[(size_t)rk * cols + rj];
+      Rs[ty][tx] = v;
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < TS; ++kk) acc = cfma(Rs[kk][tx], Xs[ty][kk], acc);
+    }
+    __syncthreads();
+  }
+  if (i < rows && j < cols) {
+    if (DIVIDE) {
+      double d = (lam_y ? lam_y[i] : 0.0) + lam_x[j] - k2;
+      acc = make_double2(acc.x / d, acc.y / d);
+    }
+    out[(size_t)i * cols + j] = acc;
+  }
+}
+
+// ------------------------------------------------------------------ host
+static iga_status fdm_setup(iga_ctx* ctx) {
+  const int n = ctx->mx;
+  const int np = n + (n & 1);
+  cudaStream_t st = ctx->st;
+  double* Lm = dalloc<double>(ctx, (size_t)n * n);
+  double* Y = dalloc<double>(ctx, (size_t)n * n);
+  double* Yt = dalloc<double>(ctx, (size_t)n * n);
+  double* Cm = dalloc<double>(ctx, (size_t)n * n);
+  double* A0 = dalloc<double>(ctx, (size_t)np * np);
+  double* A1 = dalloc<double>(ctx, (size_t)np * np);
+  double* Vj = dalloc<double>(ctx, (size_t)np * np);
+  double* W = dalloc<double>(ctx, (size_t)n * n);
+  double* cs = dalloc<double>(ctx, (size_t)4 * (np / 2 + 1));
+  double* nrm = dalloc<double>(ctx, 2);
+  int* info = dalloc<int>(ctx, 1);
+  ctx->fdmV = dalloc<double>(ctx, (size_t)n * n);
+  ctx->fdmL = dalloc<double>(ctx, n);
+  if (!Lm || !Y || !Yt || !Cm || !A0 || !A1 || !Vj || !W || !cs || !nrm || !info || !ctx->fdmV || !ctx->fdmL)
+    return set_err(ctx, IGA_E_OOM, "fdm alloc");
+  CK(cudaMemsetAsync(info, 0, sizeof(int), st));
+  CK(cudaMemcpyAsync(Lm, ctx->mc, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, st));
+  k_cholesky<<<1, 512, 0, st>>>(Lm, n, info);
+  CKL();
+  // C = L^{-1} Kc L^{-T} = L^{-1} (L^{-1} Kc)^T
+  k_trsm_lower<<<cdiv(n, 64), 64, 0, st>>>(Lm, ctx->kc, Y, n);
+  k_transpose<<<cdiv((size_t)n * n, 256), 256, 0, st>>>(Y, Yt, n);
+  k_trsm_lower<<<cdiv(n, 64), 64, 0, st>>>(Lm, Yt, Cm, n);
+  k_pad_sym<<<cdiv((size_t)np * np, 256), 256, 0, st>>>(Cm, A0, n, np);
+  k_eye_d<<<cdiv((size_t)np * np, 256), 256, 0, st>>>(Vj, np);
+  CKL();
+  double hn[2] = {0, 0};
+  double* cur = A0;
+  double* nxt = A1;
+  bool conv = false;
+  int extra = -1;                    // one more sweep after the threshold is met
+  const int h = np / 2;
+  for (int sweep = 0; sweep < 40 && !conv; ++sweep) {
+    for (int r = 0; r < np - 1; ++r) {
+      k_jac_angles<<<cdiv(h, 128), 128, 0, st>>>(cur, np, r, cs);
+      k_jac_apply<<<cdiv((size_t)h * h + (size_t)np * h, 256), 256, 0, st>>>(cur, nxt, Vj, np, cs);
+      std::swap(cur, nxt);
+    }
+    CKL();
+    k_offnorm<<<1, 256, 0, st>>>(cur, np, nrm);
+    CK(cudaMemcpyAsync(hn, nrm, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (extra >= 0) conv = true;
+    else if (hn[0] <= 1e-26 * hn[1] || hn[0] == 0.0) extra = sweep;
+  }
+  if (!conv) return set_err(ctx, IGA_E_INVALID, "Jacobi eigen-solver did not converge (off %.3e)", hn[0]);
+  k_diag_extract<<<cdiv(n, 128), 128, 0, st>>>(cur, np, n, ctx->fdmL);
+  k_crop<<<cdiv((size_t)n * n, 256), 256, 0, st>>>(Vj, np, n, W);
+  // generalised eigenvectors V = L^{-T} W
+  k_trsm_lower_t<<<cdiv(n, 64), 64, 0, st>>>(Lm, W, ctx->fdmV, n);
+  CKL();
+  int hinfo = 0;
+  CK(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (hinfo) return set_err(ctx, IGA_E_INVALID, "coarse mass matrix not positive definite");
+  return IGA_OK;
+}
+
+iga_status setup_deflation(iga_ctx* ctx) {
+  LevelData& L = ctx->lv[0];
+  ctx->mx = L.nx / 2;
+  ctx->m = ctx->dim == 2 ? (size_t)ctx->mx * ctx->mx : (size_t)ctx->mx;
+  if (ctx->mx < 1) return set_err(ctx, IGA_E_INVALID, "mesh too small for deflation");
+  ctx->ct = dalloc<double2>(ctx, ctx->m);
+  ctx->cs = dalloc<double2>(ctx, ctx->m);
+  ctx->cw = dalloc<double2>(ctx, ctx->m);
+  ctx->kc = dalloc<double>(ctx, (size_t)ctx->mx * ctx->mx);
+  ctx->mc = dalloc<double>(ctx, (size_t)ctx->mx * ctx->mx);
+  if (!ctx->ct || !ctx->cs || !ctx->cw || !ctx->kc || !ctx->mc) return set_err(ctx, IGA_E_OOM, "deflation alloc");
+  k_coarse_1d<<<cdiv((size_t)ctx->mx * ctx->mx, 128), 128, 0, ctx->st>>>(L.nx, ctx->mx, ctx->p, ctx->prm.eps, L.K, L.M,
+                                                                       ctx->kc, ctx->mc);
+  CKL();
+  if (ctx->vark) return set_err(ctx, IGA_E_UNSUPPORTED, "variable-k coarse solve not built");
+  return fdm_setup(ctx);
+}
+
+iga_status defl_zt(iga_ctx* ctx, const double2* x, double2* c) {
+  const LevelData& L = ctx->lv[0];
+  int my = ctx->dim == 2 ? ctx->mx : 1;
+  k_zt<<<cdiv(ctx->m, 256), 256, 0, ctx->st>>>(L.nx, L.ny, ctx->mx, my, ctx->prm.eps, x, c);
+  CKL();
+  return IGA_OK;
+}
+
+iga_status defl_z(iga_ctx* ctx, const double2* c, double2* x) {
+  const LevelData& L = ctx->lv[0];
+  int my = ctx->dim == 2 ? ctx->mx : 1;
+  k_z<<<cdiv(L.n, 256), 256, 0, ctx->st>>>(L.nx, L.ny, ctx->mx, my, ctx->prm.eps, c, x);
+  CKL();
+  return IGA_OK;
+}
+
+iga_status defl_esolve(iga_ctx* ctx, const double2* t, double2* s) {
+  const int mx = ctx->mx;
+  const double k2 = ctx->k2const;
+  dim3 blk(16, 16);
+  if (ctx->dim == 1) {
+    // s = V ((V^T t) / (lambda - k^2)) with t as a 1 x m row: (t V) / d, then (.) V^T
+    dim3 g(cdiv(mx, 16), 1);
+    k_fdm_gemm<false, false, true><<<g, blk, 0, ctx->st>>>(ctx->fdmV, t, ctx->cw, 1, mx, nullptr, ctx->fdmL, k2);
+    k_fdm_gemm<false, true, false><<<g, blk, 0, ctx->st>>>(ctx->fdmV, ctx->cw, s, 1, mx, nullptr, nullptr, 0.0);
+    CKL();
+    return IGA_OK;
+  }
+  dim3 g(cdiv(mx, 16), cdiv(mx, 16));
+  // T1 = V^T T ; T2 = (T1 V) / D ; T3 = V T2 ; S = T3 V^T
+  k_fdm_gemm<true, true, false><<<g, blk, 0, ctx->st>>>(ctx->fdmV, t, ctx->cw, mx, mx, nullptr, nullptr, 0.0);
+  k_fdm_gemm<false, false, true><<<g, blk, 0, ctx->st>>>(ctx->fdmV, ctx->cw, s, mx, mx, ctx->fdmL, ctx->fdmL, k2);
+  k_fdm_gemm<true, false, false><<<g, blk, 0, ctx->st>>>(ctx->fdmV, s, ctx->cw, mx, mx, nullptr, nullptr, 0.0);
+  k_fdm_gemm<false, true, false><<<g, blk, 0, ctx->st>>>(ctx->fdmV, ctx->cw, s, mx, mx, nullptr, nullptr, 0.0);
+  CKL();
+  return IGA_OK;
+}
+
+// y = Q x = Z E^{-1} Z^T x
+iga_status defl_q(iga_ctx* ctx, const double2* x, double2* y) {
+  TRY(defl_zt(ctx, x, ctx->ct));
+  TRY(defl_esolve(ctx, ctx->ct, ctx->cs));
+  return defl_z(ctx, ctx->cs, y);
+}
+
+// y = P x = x - A Z E^{-1} Z^T x  (the final A apply fuses the subtraction)
+iga_status defl_apply(iga_ctx* ctx, const double2* x, double2* y) {
+  TRY(defl_q(ctx, x, ctx->w3));
+  return op_apply<double>(ctx, 0, OP_A, ctx->w3, y, x, EPI_ZMINUS, nullptr, 0.0);
+}

@@ -1,0 +1,353 @@
+// GMRES / flexible GMRES on the deflated, CSLP-preconditioned IgA system
+// (Section 3: GMRES with P and M^{-1}; Section 4.3: stop at relative residual
+// 1e-7, at most 100 iterations).
+//
+// Reading of the deflated system (DEF1): GMRES on M~^{-1} P A x^ = M~^{-1} P f
+// from x^ = 0, then u = Q f + P^T x^ = x^ + Q (f - A x^).  FGMRES (right
+// preconditioning, stored z_j) is used when the preconditioner is not a fixed
+// FP64 operator (the FP32 V-cycle).
+//
+// Arnoldi is modified Gram-Schmidt with the Hermitian inner product.  Every
+// reduction is deterministic: each block reduces a grid-strided slice in a
+// fixed order, and every consumer re-reduces the per-block partial sums in
+// the same fixed order.  Hessenberg least squares by complex Givens
+// rotations [c, s; -conj(s), c] with real c.
+#include "common.cuh"
+#include <cmath>
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+// block-wide sum of (a, b) pairs; result valid in thread 0
+__device__ double2 block_sum2(double a, double b) {
+  __shared__ double sa[32], sb[32];
+  a = warp_sum(a);
+  b = warp_sum(b);
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) { sa[wid] = a; sb[wid] = b; }
+  __syncthreads();
+  int nw = (blockDim.x + 31) >> 5;
+  if (wid == 0) {
+    a = lane < nw ? sa[lane] : 0.0;
+    b = lane < nw ? sb[lane] : 0.0;
+    a = warp_sum(a);
+    b = warp_sum(b);
+  }
+  __syncthreads();
+  return make_double2(a, b);
+}
+// every block re-reduces the nb partial pairs in the same order; result in all threads
+__device__ double2 reduce_partials(const double* part, int nb) {
+  __shared__ double2 res;
+  double a = 0.0, b = 0.0;
+  for (int t = threadIdx.x; t < nb; t += blockDim.x) { a += part[2 * t]; b += part[2 * t + 1]; }
+  double2 s = block_sum2(a, b);
+  if (threadIdx.x == 0) res = s;
+  __syncthreads();
+  double2 r = res;
+  __syncthreads();
+  return r;
+}
+
+// MGS step i of column j: w -= h_{i-1} v_{i-1} (i > 0, h_{i-1} from the previous
+// step's partials), then partial sums of v_i^H w (i <= j) or ||w||^2 (i = j+1).
+__global__ void k_mgs_step(const double2* V, size_t ldv, size_t n, int i, int j, double2* w,
+                           const double* part_in, double* part_out, double2* h) {
+  double2 hp = make_double2(0.0, 0.0);
+  if (i > 0) {
+    hp = reduce_partials(part_in, gridDim.x);
+    if (blockIdx.x == 0 && threadIdx.x == 0) h[i - 1] = hp;
+  }
+  const double2* vprev = V + (size_t)(i - 1) * ldv;
+  const double2* vi = V + (size_t)i * ldv;
+  double a = 0.0, b = 0.0;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    double2 we = w[e];
+    if (i > 0) {
+      we = we - cmul(hp, vprev[e]);
+      w[e] = we;
+    }
+    if (i <= j) {
+      double2 c = cconjmul(vi[e], we);
+      a += c.x;
+      b += c.y;
+    } else {
+      a += we.x * we.x + we.y * we.y;
+    }
+  }
+  double2 s = block_sum2(a, b);
+  if (threadIdx.x == 0) { part_out[2 * blockIdx.x] = s.x; part_out[2 * blockIdx.x + 1] = s.y; }
+}
+
+// partial sums of ||x||^2
+__global__ void k_norm2_part(const double2* x, size_t n, double* part) {
+  double a = 0.0;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    a += x[e].x * x[e].x + x[e].y * x[e].y;
+  double2 s = block_sum2(a, 0.0);
+  if (threadIdx.x == 0) { part[2 * blockIdx.x] = s.x; part[2 * blockIdx.x + 1] = 0.0; }
+}
+__global__ void k_finish_norm(const double* part, int nb, double* out) {
+  double2 s = reduce_partials(part, nb);
+  if (threadIdx.x == 0) *out = sqrt(s.x);
+}
+__global__ void k_finish_h(const double* part, int nb, double2* h) {
+  double2 s = reduce_partials(part, nb);
+  if (threadIdx.x == 0) *h = make_double2(sqrt(s.x), 0.0);
+}
+
+struct GState {
+  double* cs;      // [maxit]
+  double2* sn;     // [maxit]
+  double2* g;      // [maxit+1]
+  double* hist;    // [maxit+1]
+  double* scal;    // [0] beta, [1] tol
+  int* flag;       // [0] converged, [1] nonfinite
+};
+
+__device__ void givens_update(double2* Hj, int j, GState gs) {
+  for (int i = 0; i < j; ++i) {
+    double c = gs.cs[i];
+    double2 s = gs.sn[i];
+    double2 t = c * Hj[i] + cmul(s, Hj[i + 1]);
+    Hj[i + 1] = c * Hj[i + 1] - cconjmul(s, Hj[i]);
+    Hj[i] = t;
+  }
+  double2 a = Hj[j], b = Hj[j + 1];
+  double aa = hypot(a.x, a.y), ab = hypot(b.x, b.y);
+  double c;
+  double2 s;
+  if (ab == 0.0) {
+    c = 1.0;
+    s = make_double2(0.0, 0.0);
+  } else if (aa == 0.0) {
+    c = 0.0;
+    s = make_double2(b.x / ab, -b.y / ab);
+  } else {
+    double t = hypot(aa, ab);
+    c = aa / t;
+    double2 ph = make_double2(a.x / aa, a.y / aa);
+    double2 cb = make_double2(b.x / t, -b.y / t);
+    s = cmul(ph, cb);
+  }
+  gs.cs[j] = c;
+  gs.sn[j] = s;
+  Hj[j] = c * a + cmul(s, b);
+  Hj[j + 1] = make_double2(0.0, 0.0);
+  double2 gj = gs.g[j];
+  gs.g[j + 1] = make_double2(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));   // -conj(s) g_j
+  gs.g[j] = c * gj;
+  double res = hypot(gs.g[j + 1].x, gs.g[j + 1].y) / gs.scal[0];
+  gs.hist[j + 1] = res;
+  if (!isfinite(res)) gs.flag[1] = 1;
+  if (res <= gs.scal[1]) gs.flag[0] = 1;
+}
+
+// v_{j+1} = w / ||w|| (w already holds the orthogonalised vector), H[j+1][j] =
+// ||w||, then the Givens update of column j (block 0, thread 0).
+__global__ void k_normalize_givens(double2* w, size_t n, const double* part, double2* Hj, int j, GState gs,
+                                   int do_givens) {
+  double2 s = reduce_partials(part, gridDim.x);
+  double hn = sqrt(s.x);
+  double inv = hn > 0.0 ? 1.0 / hn : 0.0;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    w[e] = inv * w[e];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    Hj[j + 1] = make_double2(hn, 0.0);
+    if (do_givens) givens_update(Hj, j, gs);
+  }
+}
+
+// initial vector: v0 = b / ||b||, g0 = beta, hist0 = 1
+__global__ void k_init_v0(double2* v, size_t n, const double* part, GState gs) {
+  double2 s = reduce_partials(part, gridDim.x);
+  double beta = sqrt(s.x);
+  double inv = beta > 0.0 ? 1.0 / beta : 0.0;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    v[e] = inv * v[e];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    gs.scal[0] = beta;
+    gs.g[0] = make_double2(beta, 0.0);
+    gs.hist[0] = 1.0;
+    gs.flag[0] = (beta == 0.0) ? 1 : 0;
+    gs.flag[1] = isfinite(beta) ? 0 : 1;
+  }
+}
+
+// R y = g (R upper triangular, column-major with leading dimension ldh)
+__global__ void k_backsolve(const double2* H, int ldh, const double2* g, double2* y, int k) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int r = k - 1; r >= 0; --r) {
+    double2 s = g[r];
+    for (int c = r + 1; c < k; ++c) s = s - cmul(H[(size_t)c * ldh + r], y[c]);
+    double2 d = H[(size_t)r * ldh + r];
+    y[r] = cmul(s, cinv(d));
+  }
+}
+
+// x = sum_k Vk y_k (+ x0 if add)
+__global__ void k_combine(const double2* V, size_t ldv, size_t n, const double2* y, int k, double2* x) {
+  size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int c = 0; c < k; ++c) acc = acc + cmul(y[c], V[(size_t)c * ldv + e]);
+  x[e] = acc;
+}
+__global__ void k_add(const double2* a, const double2* b, double2* out, size_t n) {
+  size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (e < n) out[e] = a[e] + b[e];
+}
+
+// ------------------------------------------------------------------ host
+static int red_blocks(iga_ctx* ctx) { return 2 * ctx->num_sms; }
+
+iga_status vec_norm(iga_ctx* ctx, const double2* x, size_t n, double* dev_out) {
+  int nb = red_blocks(ctx);
+  k_norm2_part<<<nb, IGA_RED_THREADS, 0, ctx->st>>>(x, n, ctx->partials);
+  k_finish_norm<<<1, IGA_RED_THREADS, 0, ctx->st>>>(ctx->partials, nb, dev_out);
+  CKL();
+  return IGA_OK;
+}
+
+// MGS of w against columns 0..j of V; h[0..j] projections, h[j+1] = ||w||
+// (w is NOT normalised).
+iga_status kry_mgs(iga_ctx* ctx, const double2* V, size_t ldv, int j, double2* w, double2* h) {
+  int nb = red_blocks(ctx);
+  size_t n = ctx->lv[0].n;
+  double* pa = ctx->partials;
+  double* pb = ctx->partials + 2 * nb;
+  for (int i = 0; i <= j + 1; ++i) {
+    const double* pin = (i & 1) ? pa : pb;
+    double* pout = (i & 1) ? pb : pa;
+    k_mgs_step<<<nb, IGA_RED_THREADS, 0, ctx->st>>>(V, ldv, n, i, j, w, pin, pout, h);
+  }
+  const double* plast = ((j + 1) & 1) ? pb : pa;
+  k_finish_h<<<1, IGA_RED_THREADS, 0, ctx->st>>>(plast, nb, h + j + 1);
+  CKL();
+  return IGA_OK;
+}
+
+static iga_status ensure_krylov(iga_ctx* ctx, int maxit, bool flexible) {
+  size_t n = ctx->lv[0].n;
+  if (ctx->maxit_alloc >= maxit && (!flexible || ctx->Zb)) return IGA_OK;
+  int m = std::max(maxit, ctx->maxit_alloc);
+  ctx->Vb = dalloc<double2>(ctx, n * (size_t)(m + 1));
+  if (flexible) ctx->Zb = dalloc<double2>(ctx, n * (size_t)m);
+  ctx->H = dalloc<double2>(ctx, (size_t)(m + 1) * m);
+  ctx->gstate = dalloc<double>(ctx, (size_t)m + (m + 1) + 4);
+  ctx->gsn = dalloc<double2>(ctx, m);
+  ctx->gg = dalloc<double2>(ctx, m + 1);
+  ctx->gy = dalloc<double2>(ctx, m);
+  ctx->gflag = dalloc<int>(ctx, 4);
+  if (!ctx->Vb || (flexible && !ctx->Zb) || !ctx->H || !ctx->gstate || !ctx->gsn || !ctx->gg || !ctx->gy || !ctx->gflag)
+    return set_err(ctx, IGA_E_OOM, "krylov workspace (n=%zu, maxit=%d)", n, m);
+  ctx->maxit_alloc = m;
+  return IGA_OK;
+}
+
+// z = M~^{-1} r in the context's precision
+static iga_status precond(iga_ctx* ctx, const double2* r, double2* z) {
+  if (ctx->prm.precision == 0) return mg_vcycle<double>(ctx, r, z);
+  LevelData& L = ctx->lv[0];
+  launch_convert_d2f(r, ctx->fin, L.n, ctx->st);
+  TRY(mg_vcycle<float>(ctx, ctx->fin, ctx->fout));
+  launch_convert_f2d(ctx->fout, z, L.n, ctx->st);
+  CKL();
+  return IGA_OK;
+}
+
+iga_status kry_solve(iga_ctx* ctx, const double2* f, double2* x, double tol, int maxit, int* iters, double* hist,
+                     double* true_res) {
+  const bool flex = ctx->prm.precision != 0 || ctx->prm.flexible != 0;
+  TRY(ensure_krylov(ctx, maxit, flex));
+  cudaStream_t st = ctx->st;
+  const size_t n = ctx->lv[0].n;
+  const int ldh = ctx->maxit_alloc + 1;
+  const size_t ldv = n;
+  const int nb = red_blocks(ctx);
+  GState gs;
+  gs.cs = ctx->gstate;
+  gs.hist = ctx->gstate + ctx->maxit_alloc;
+  gs.scal = gs.hist + ctx->maxit_alloc + 1;
+  gs.sn = ctx->gsn;
+  gs.g = ctx->gg;
+  gs.flag = ctx->gflag;
+  double tolv[1] = {tol};
+  CK(cudaMemcpyAsync(gs.scal + 1, tolv, sizeof(double), cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(ctx->H, 0, sizeof(double2) * (size_t)ldh * ctx->maxit_alloc, st));
+  double2* V = ctx->Vb;
+  // initial vector
+  if (flex) {
+    TRY(defl_apply(ctx, f, V));                       // b = P f
+  } else {
+    TRY(defl_apply(ctx, f, ctx->w0));                 // b = M~^{-1} P f
+    TRY(precond(ctx, ctx->w0, V));
+  }
+  k_norm2_part<<<nb, IGA_RED_THREADS, 0, st>>>(V, n, ctx->partials);
+  k_init_v0<<<nb, IGA_RED_THREADS, 0, st>>>(V, n, ctx->partials, gs);
+  CKL();
+  int hflag[2] = {0, 0};
+  CK(cudaMemcpyAsync(hflag, gs.flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  int jdone = 0;
+  bool conv = hflag[0] != 0, nonfinite = hflag[1] != 0;
+  for (int j = 0; j < maxit && !conv && !nonfinite; ++j) {
+    double2* vj = V + (size_t)j * ldv;
+    double2* w = V + (size_t)(j + 1) * ldv;
+    if (flex) {
+      double2* zj = ctx->Zb + (size_t)j * ldv;
+      TRY(precond(ctx, vj, zj));
+      TRY(op_apply<double>(ctx, 0, OP_A, zj, ctx->w1, nullptr, EPI_Y, nullptr, 0.0));
+      TRY(defl_apply(ctx, ctx->w1, w));
+    } else {
+      TRY(op_apply<double>(ctx, 0, OP_A, vj, ctx->w1, nullptr, EPI_Y, nullptr, 0.0));
+      TRY(defl_apply(ctx, ctx->w1, ctx->w2));
+      TRY(precond(ctx, ctx->w2, w));
+    }
+    double2* Hj = ctx->H + (size_t)j * ldh;
+    // MGS: h_ij for i <= j, then ||w||^2 partials
+    double* pa = ctx->partials;
+    double* pb = ctx->partials + 2 * nb;
+    for (int i = 0; i <= j + 1; ++i) {
+      const double* pin = (i & 1) ? pa : pb;
+      double* pout = (i & 1) ? pb : pa;
+      k_mgs_step<<<nb, IGA_RED_THREADS, 0, st>>>(V, ldv, n, i, j, w, pin, pout, Hj);
+    }
+    const double* plast = ((j + 1) & 1) ? pb : pa;
+    k_normalize_givens<<<nb, IGA_RED_THREADS, 0, st>>>(w, n, plast, Hj, j, gs, 1);
+    CKL();
+    CK(cudaMemcpyAsync(hflag, gs.flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    jdone = j + 1;
+    conv = hflag[0] != 0;
+    nonfinite = hflag[1] != 0;
+  }
+  if (hist) CK(cudaMemcpyAsync(hist, gs.hist, sizeof(double) * (jdone + 1), cudaMemcpyDeviceToHost, st));
+  // y = R^{-1} g ; x^ = V y (or Z y)
+  if (jdone > 0) {
+    k_backsolve<<<1, 1, 0, st>>>(ctx->H, ldh, gs.g, ctx->gy, jdone);
+    k_combine<<<cdiv(n, 256), 256, 0, st>>>(flex ? ctx->Zb : V, ldv, n, ctx->gy, jdone, ctx->w0);
+  } else {
+    CK(cudaMemsetAsync(ctx->w0, 0, sizeof(double2) * n, st));
+  }
+  // u = x^ + Q (f - A x^)
+  TRY(op_apply<double>(ctx, 0, OP_A, ctx->w0, ctx->w1, f, EPI_ZMINUS, nullptr, 0.0));
+  TRY(defl_q(ctx, ctx->w1, ctx->w2));
+  k_add<<<cdiv(n, 256), 256, 0, st>>>(ctx->w0, ctx->w2, x, n);
+  CKL();
+  if (true_res) {
+    TRY(op_apply<double>(ctx, 0, OP_A, x, ctx->w1, f, EPI_ZMINUS, nullptr, 0.0));
+    double* dn = gs.scal + 2;
+    TRY(vec_norm(ctx, ctx->w1, n, dn));
+    TRY(vec_norm(ctx, f, n, dn + 1));
+    double hn[2];
+    CK(cudaMemcpyAsync(hn, dn, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    *true_res = hn[1] > 0 ? hn[0] / hn[1] : 0.0;
+  }
+  CK(cudaStreamSynchronize(st));
+  if (iters) *iters = jdone;
+  if (nonfinite) return set_err(ctx, IGA_E_NONFINITE, "non-finite residual at iteration %d", jdone);
+  return conv ? IGA_OK : IGA_NOT_CONVERGED;
+}

@@ -1,0 +1,442 @@
+// Matrix-free IgA Helmholtz operators (Section 2.3, Eq. linearsystem1 with
+// A = S - M^{k^2}; Section 3, CSLP M_beta = S - (beta1 - i beta2) M^{k^2}).
+//
+// Constant k: Op = M_y (x) (K_x + c M_x) + K_y (x) M_x applied as two banded
+// 1D passes through a shared-memory tile with a p-wide halo:
+//   x-pass  u = K_x x + c M_x x,  t = M_x x   (rows of the tile + halo rows)
+//   y-pass  y = M_y u + K_y t
+// c = -k^2 for A and -(beta1 - i beta2) k^2 for M_beta.
+//
+// Variable k: S by the same banded passes, the k^2-mass by per-element
+// sum factorisation in the tile: interpolate to the Gauss points along x,
+// then y, weight by w_x w_y k^2(x_q, y_q), project back along y, then x.
+//
+// Epilogues fuse what follows the apply: y = Op x, y = z - Op x (residual,
+// deflation), or one damped Jacobi sweep x_out = x + omega D^{-1} (b - Op x).
+#include "common.cuh"
+
+template <typename T> struct OpArgs {
+  using C = typename cplx<T>::t;
+  int nx, ny, n_el;
+  const T* K;          // bands [nx][2p+1]
+  const T* M;
+  C c;                 // coefficient of the (k^2-)mass term
+  const C* x;
+  C* y;
+  const C* z;          // EPI_ZMINUS: minuend; EPI_JACOBI: right-hand side b
+  const C* dinv;       // EPI_JACOBI with variable k: precomputed D^{-1}
+  T omega;
+  // variable k
+  const T* B;          // [n_el][Q][p+1]
+  const T* wq;         // [n_el][Q]
+  const double* xq;    // [n_el][Q]
+};
+
+struct KFieldF {
+  int n_lines;
+  float lines[IGA_MAX_LINES][3];
+  float k2[IGA_MAX_LINES + 1];
+};
+
+template <typename T> struct KSel;
+template <> struct KSel<double> {
+  using KF = KFieldDev;
+  static __device__ __forceinline__ double k2(const KFieldDev& kf, double x, double y) { return kfield_k2(kf, x, y); }
+};
+template <> struct KSel<float> {
+  using KF = KFieldF;
+  static __device__ __forceinline__ float k2(const KFieldF& kf, double xd, double yd) {
+    float x = (float)xd, y = (float)yd;
+    int cnt = 0;
+    for (int l = 0; l < kf.n_lines; ++l) {
+      float s = __fadd_rn(__fadd_rn(__fmul_rn(kf.lines[l][0], x), __fmul_rn(kf.lines[l][1], y)), kf.lines[l][2]);
+      cnt += (s >= 0.f);
+    }
+    return kf.k2[cnt];
+  }
+};
+
+template <typename T, int EPI>
+__device__ __forceinline__ void epilogue(const OpArgs<T>& a, size_t o, typename cplx<T>::t acc,
+                                         typename cplx<T>::t xo, typename cplx<T>::t diag) {
+  using C = typename cplx<T>::t;
+  if (EPI == EPI_Y) {
+    a.y[o] = acc;
+  } else if (EPI == EPI_ZMINUS) {
+    a.y[o] = a.z[o] - acc;
+  } else {
+    C r = a.z[o] - acc;
+    C di = a.dinv ? a.dinv[o] : cinv(diag);
+    a.y[o] = xo + a.omega * cmul(di, r);
+  }
+}
+
+// ------------------------------------------------------------------ 1D
+template <int P, typename T, int EPI>
+__global__ void __launch_bounds__(256) k_kron1d(OpArgs<T> a) {
+  using C = typename cplx<T>::t;
+  constexpr int W = 2 * P + 1;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.nx) return;
+  C s1 = czero<C>(), s2 = czero<C>();
+#pragma unroll
+  for (int d = 0; d < W; ++d) {
+    int j = i + d - P;
+    if (j >= 0 && j < a.nx) {
+      C v = a.x[j];
+      s1 = cfma(a.K[(size_t)i * W + d], v, s1);
+      s2 = cfma(a.M[(size_t)i * W + d], v, s2);
+    }
+  }
+  C acc = s1 + cmul(a.c, s2);
+  C diag = czero<C>();
+  if (EPI == EPI_JACOBI) {
+    T kd = a.K[(size_t)i * W + P], md = a.M[(size_t)i * W + P];
+    diag = mkc(kd, (T)0) + md * a.c;
+  }
+  epilogue<T, EPI>(a, i, acc, EPI == EPI_JACOBI ? a.x[i] : czero<C>(), diag);
+}
+
+// ------------------------------------------------------------------ 2D constant k
+constexpr int KR_TX = 32, KR_TY = 16;
+
+template <int P, typename T>
+constexpr size_t kron2d_smem() {
+  using C = typename cplx<T>::t;
+  return sizeof(C) * ((KR_TY + 2 * P) * (KR_TX + 2 * P) + 2 * (KR_TY + 2 * P) * KR_TX) +
+         sizeof(T) * (2 * KR_TX + 2 * KR_TY) * (2 * P + 1);
+}
+
+template <int P, typename T, int EPI>
+__global__ void __launch_bounds__(256) k_kron2d(OpArgs<T> a) {
+  using C = typename cplx<T>::t;
+  constexpr int W = 2 * P + 1, TX = KR_TX, TY = KR_TY, SX = TX + 2 * P, SY = TY + 2 * P;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* xs = (C*)smem_raw;
+  C* us = xs + SY * SX;
+  C* ts = us + SY * TX;
+  T* kx = (T*)(ts + SY * TX);
+  T* mx = kx + TX * W;
+  T* ky = mx + TX * W;
+  T* my = ky + TY * W;
+  const int tid = threadIdx.x;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int nx = a.nx, ny = a.ny;
+  for (int i = tid; i < SY * SX; i += 256) {
+    int r = i / SX, c = i - r * SX;
+    int gy = y0 - P + r, gx = x0 - P + c;
+    xs[i] = (gy >= 0 && gy < ny && gx >= 0 && gx < nx) ? a.x[(size_t)gy * nx + gx] : czero<C>();
+  }
+  for (int i = tid; i < TX * W; i += 256) {
+    int c = i / W, gx = x0 + c;
+    kx[i] = gx < nx ? a.K[(size_t)x0 * W + i] : (T)0;
+    mx[i] = gx < nx ? a.M[(size_t)x0 * W + i] : (T)0;
+  }
+  for (int i = tid; i < TY * W; i += 256) {
+    int r = i / W, gy = y0 + r;
+    ky[i] = gy < ny ? a.K[(size_t)y0 * W + i] : (T)0;
+    my[i] = gy < ny ? a.M[(size_t)y0 * W + i] : (T)0;
+  }
+  __syncthreads();
+  for (int i = tid; i < SY * TX; i += 256) {
+    int r = i / TX, c = i - r * TX;
+    C s1 = czero<C>(), s2 = czero<C>();
+#pragma unroll
+    for (int d = 0; d < W; ++d) {
+      C v = xs[r * SX + c + d];
+      s1 = cfma(kx[c * W + d], v, s1);
+      s2 = cfma(mx[c * W + d], v, s2);
+    }
+    us[i] = s1 + cmul(a.c, s2);
+    ts[i] = s2;
+  }
+  __syncthreads();
+  for (int i = tid; i < TY * TX; i += 256) {
+    int r = i / TX, c = i - r * TX;
+    int gy = y0 + r, gx = x0 + c;
+    if (gy >= ny || gx >= nx) continue;
+    C acc = czero<C>();
+#pragma unroll
+    for (int d = 0; d < W; ++d) {
+      acc = cfma(my[r * W + d], us[(r + d) * TX + c], acc);
+      acc = cfma(ky[r * W + d], ts[(r + d) * TX + c], acc);
+    }
+    C diag = czero<C>();
+    if (EPI == EPI_JACOBI) {
+      T kxd = kx[c * W + P], mxd = mx[c * W + P], kyd = ky[r * W + P], myd = my[r * W + P];
+      diag = myd * (mkc(kxd, (T)0) + mxd * a.c) + mkc(kyd * mxd, (T)0);
+    }
+    epilogue<T, EPI>(a, (size_t)gy * nx + gx, acc, xs[(r + P) * SX + c + P], diag);
+  }
+}
+
+// ------------------------------------------------------------------ 2D variable k
+constexpr int EL_T = 8;
+
+template <int P, typename T>
+constexpr size_t elem2d_smem() {
+  using C = typename cplx<T>::t;
+  constexpr int Q = P + 1, E = EL_T + P, SX = EL_T + 2 * P;
+  return sizeof(C) * (SX * SX + SX * E * Q + (E * Q) * (E * Q) + EL_T * EL_T) + sizeof(double) * 2 * E * Q +
+         sizeof(T) * (2 * E * Q * Q + 2 * E * Q);
+}
+
+template <int P, typename T, int EPI>
+__global__ void __launch_bounds__(256) k_elem2d(OpArgs<T> a, typename KSel<T>::KF kf) {
+  using C = typename cplx<T>::t;
+  constexpr int Q = P + 1, TT = EL_T, E = TT + P, SX = TT + 2 * P, W = 2 * P + 1, EQ = E * Q;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* X = (C*)smem_raw;          // [SX][SX]
+  C* V = X + SX * SX;           // [SX][E][Q]  (also stiffness temporaries, then T4)
+  C* U = V + SX * E * Q;        // [E][Q][E][Q]
+  C* Ys = U + EQ * EQ;          // [TT][TT]
+  double* xqx = (double*)(Ys + TT * TT);
+  double* xqy = xqx + EQ;
+  T* Bx = (T*)(xqy + EQ);       // [E][Q][Q]
+  T* By = Bx + E * Q * Q;
+  T* wx = By + E * Q * Q;       // [E][Q]
+  T* wy = wx + EQ;
+  const int tid = threadIdx.x;
+  const int nx = a.nx, ny = a.ny, N = a.n_el;
+  const int ix0 = blockIdx.x * TT, iy0 = blockIdx.y * TT;
+  const int ex0 = ix0 + 1 - P, ey0 = iy0 + 1 - P;   // first element of the tile (may be < 0)
+
+  for (int i = tid; i < SX * SX; i += 256) {
+    int r = i / SX, c = i - r * SX;
+    int gy = iy0 - P + r, gx = ix0 - P + c;
+    X[i] = (gy >= 0 && gy < ny && gx >= 0 && gx < nx) ? a.x[(size_t)gy * nx + gx] : czero<C>();
+  }
+  for (int i = tid; i < E * Q * Q; i += 256) {
+    int el = i / (Q * Q), rest = i - el * Q * Q;
+    int ex = ex0 + el, ey = ey0 + el;
+    Bx[i] = (ex >= 0 && ex < N) ? a.B[(size_t)ex * Q * Q + rest] : (T)0;
+    By[i] = (ey >= 0 && ey < N) ? a.B[(size_t)ey * Q * Q + rest] : (T)0;
+  }
+  for (int i = tid; i < EQ; i += 256) {
+    int el = i / Q, q = i - el * Q;
+    int ex = ex0 + el, ey = ey0 + el;
+    bool vx = ex >= 0 && ex < N, vy = ey >= 0 && ey < N;
+    wx[i] = vx ? a.wq[ex * Q + q] : (T)0;
+    wy[i] = vy ? a.wq[ey * Q + q] : (T)0;
+    xqx[i] = vx ? a.xq[ex * Q + q] : 0.0;
+    xqy[i] = vy ? a.xq[ey * Q + q] : 0.0;
+  }
+  __syncthreads();
+
+  // stiffness S = M_y (x) K_x + K_y (x) M_x on the tile
+  C* t1 = V;
+  C* t2 = V + SX * TT;
+  for (int i = tid; i < SX * TT; i += 256) {
+    int r = i / TT, c = i - r * TT;
+    int gx = ix0 + c;
+    C s1 = czero<C>(), s2 = czero<C>();
+    if (gx < nx) {
+#pragma unroll
+      for (int d = 0; d < W; ++d) {
+        C v = X[r * SX + c + d];
+        s1 = cfma(a.K[(size_t)gx * W + d], v, s1);
+        s2 = cfma(a.M[(size_t)gx * W + d], v, s2);
+      }
+    }
+    t1[i] = s1;
+    t2[i] = s2;
+  }
+  __syncthreads();
+  for (int i = tid; i < TT * TT; i += 256) {
+    int r = i / TT, c = i - r * TT;
+    int gy = iy0 + r;
+    C acc = czero<C>();
+    if (gy < ny) {
+#pragma unroll
+      for (int d = 0; d < W; ++d) {
+        acc = cfma(a.M[(size_t)gy * W + d], t1[(r + d) * TT + c], acc);
+        acc = cfma(a.K[(size_t)gy * W + d], t2[(r + d) * TT + c], acc);
+      }
+    }
+    Ys[i] = acc;
+  }
+  __syncthreads();
+
+  // S2: interpolate along x: V[ry][el][qx] = sum_a Bx[el][qx][a] X[ry][el + a]
+  for (int i = tid; i < SX * EQ; i += 256) {
+    int ry = i / EQ, rest = i - ry * EQ;
+    int el = rest / Q, q = rest - el * Q;
+    C s = czero<C>();
+#pragma unroll
+    for (int aa = 0; aa <= P; ++aa) s = cfma(Bx[(el * Q + q) * Q + aa], X[ry * SX + el + aa], s);
+    V[i] = s;
+  }
+  __syncthreads();
+  // S3: interpolate along y and weight: U[ely][qy][elx][qx]
+  for (int i = tid; i < EQ * EQ; i += 256) {
+    int ry = i / EQ, cx = i - ry * EQ;        // ry = ely*Q + qy, cx = elx*Q + qx
+    int ely = ry / Q, qy = ry - ely * Q;
+    C s = czero<C>();
+#pragma unroll
+    for (int b = 0; b <= P; ++b) s = cfma(By[(ely * Q + qy) * Q + b], V[(ely + b) * EQ + cx], s);
+    T w = wx[cx] * wy[ry];
+    T k2 = (w != (T)0) ? KSel<T>::k2(kf, xqx[cx], xqy[ry]) : (T)0;
+    U[i] = (w * k2) * s;
+  }
+  __syncthreads();
+  // S4: project along y onto the output rows: T4[r][elx][qx]
+  C* T4 = V;
+  for (int i = tid; i < TT * EQ; i += 256) {
+    int r = i / EQ, cx = i - r * EQ;
+    C s = czero<C>();
+#pragma unroll
+    for (int b = 0; b <= P; ++b) {
+      int ely = r + P - b;
+      if (ely >= 0 && ely < E) {
+#pragma unroll
+        for (int qy = 0; qy < Q; ++qy) s = cfma(By[(ely * Q + qy) * Q + b], U[(ely * Q + qy) * EQ + cx], s);
+      }
+    }
+    T4[i] = s;
+  }
+  __syncthreads();
+  // S5: project along x, add the stiffness part, epilogue
+  for (int i = tid; i < TT * TT; i += 256) {
+    int r = i / TT, c = i - r * TT;
+    int gy = iy0 + r, gx = ix0 + c;
+    if (gy >= ny || gx >= nx) continue;
+    C s = czero<C>();
+#pragma unroll
+    for (int aa = 0; aa <= P; ++aa) {
+      int elx = c + P - aa;
+      if (elx >= 0 && elx < E) {
+#pragma unroll
+        for (int qx = 0; qx < Q; ++qx) s = cfma(Bx[(elx * Q + qx) * Q + aa], T4[r * EQ + elx * Q + qx], s);
+      }
+    }
+    C acc = Ys[i] + cmul(a.c, s);
+    epilogue<T, EPI>(a, (size_t)gy * nx + gx, acc, X[(r + P) * SX + c + P], czero<C>());
+  }
+}
+
+// Inverse diagonal of M_beta = S - sigma M^{k^2} for variable k, thread per dof.
+__global__ void k_vark_diag(int nx, int n_el, int p, const double* K, const double* M, const double* B,
+                            const double* wq, const double* xq, KFieldDev kf, double2 c, double2* dinv,
+                            float2* dinvf) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nx * nx) return;
+  int iy = i / nx, ix = i - iy * nx;
+  int W = 2 * p + 1, Q = p + 1;
+  double s = M[(size_t)iy * W + p] * K[(size_t)ix * W + p] + K[(size_t)iy * W + p] * M[(size_t)ix * W + p];
+  int bx = ix + 1, by = iy + 1;
+  double mk = 0.0;
+  for (int ey = max(by - p, 0); ey <= min(by, n_el - 1); ++ey)
+    for (int ex = max(bx - p, 0); ex <= min(bx, n_el - 1); ++ex)
+      for (int qy = 0; qy < Q; ++qy)
+        for (int qx = 0; qx < Q; ++qx) {
+          double vx = B[((size_t)ex * Q + qx) * Q + (bx - ex)];
+          double vy = B[((size_t)ey * Q + qy) * Q + (by - ey)];
+          double k2 = kfield_k2(kf, xq[ex * Q + qx], xq[ey * Q + qy]);
+          mk += wq[ex * Q + qx] * wq[ey * Q + qy] * k2 * vx * vx * vy * vy;
+        }
+  double2 d = make_double2(s, 0.0) + mk * c;
+  double2 di = cinv(d);
+  dinv[i] = di;
+  dinvf[i] = tof(di);
+}
+
+// ------------------------------------------------------------------ host dispatch
+template <int P, typename T, int EPI>
+static void launch_op(iga_ctx* ctx, const OpArgs<T>& a, int level) {
+  cudaStream_t st = ctx->st;
+  if (ctx->dim == 1) {
+    k_kron1d<P, T, EPI><<<cdiv(a.nx, 256), 256, 0, st>>>(a);
+  } else if (!ctx->vark) {
+    constexpr size_t sm = kron2d_smem<P, T>();
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_kron2d<P, T, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      attr = true;
+    }
+    dim3 grid(cdiv(a.nx, KR_TX), cdiv(a.ny, KR_TY));
+    k_kron2d<P, T, EPI><<<grid, 256, sm, st>>>(a);
+  } else {
+    constexpr size_t sm = elem2d_smem<P, T>();
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_elem2d<P, T, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      attr = true;
+    }
+    dim3 grid(cdiv(a.nx, EL_T), cdiv(a.ny, EL_T));
+    typename KSel<T>::KF kf;
+    if constexpr (sizeof(T) == 8) {
+      kf = ctx->kf;
+    } else {
+      kf.n_lines = ctx->kf.n_lines;
+      for (int l = 0; l < IGA_MAX_LINES; ++l)
+        for (int c = 0; c < 3; ++c) kf.lines[l][c] = (float)ctx->kf.lines[l][c];
+      for (int l = 0; l <= IGA_MAX_LINES; ++l) kf.k2[l] = (float)ctx->kf.k2[l];
+    }
+    k_elem2d<P, T, EPI><<<grid, 256, sm, st>>>(a, kf);
+  }
+  (void)level;
+}
+
+template <int P, typename T>
+static void launch_epi(iga_ctx* ctx, const OpArgs<T>& a, int level, int epi) {
+  if (epi == EPI_Y) launch_op<P, T, EPI_Y>(ctx, a, level);
+  else if (epi == EPI_ZMINUS) launch_op<P, T, EPI_ZMINUS>(ctx, a, level);
+  else launch_op<P, T, EPI_JACOBI>(ctx, a, level);
+}
+
+template <typename T>
+iga_status op_apply(iga_ctx* ctx, int level, int which, const typename cplx<T>::t* x, typename cplx<T>::t* y,
+                    const typename cplx<T>::t* z, int epi, const typename cplx<T>::t* b, double omega) {
+  using C = typename cplx<T>::t;
+  const LevelData& L = ctx->lv[level];
+  OpArgs<T> a;
+  a.nx = L.nx;
+  a.ny = L.ny;
+  a.n_el = L.n_el;
+  constexpr bool dbl = sizeof(T) == 8;
+  if constexpr (dbl) {
+    a.K = (const T*)L.K; a.M = (const T*)L.M; a.B = (const T*)L.B; a.wq = (const T*)L.wq;
+  } else {
+    a.K = (const T*)L.Kf; a.M = (const T*)L.Mf; a.B = (const T*)L.Bf; a.wq = (const T*)L.wqf;
+  }
+  a.xq = L.xq;
+  // mass coefficient: A: -1 (times k^2); M_beta: -(beta1 - i beta2) (times k^2)
+  double2 cm = (which == OP_A) ? make_double2(-1.0, 0.0) : make_double2(-ctx->sig.x, -ctx->sig.y);
+  if (!ctx->vark) cm = ctx->k2const * cm;
+  a.c = cconv<C>(cm);
+  a.x = x;
+  a.y = y;
+  a.z = (epi == EPI_JACOBI) ? b : z;
+  a.dinv = nullptr;
+  if (epi == EPI_JACOBI && ctx->vark && ctx->dim == 2) {
+    if constexpr (dbl) a.dinv = (const C*)L.dinv; else a.dinv = (const C*)L.dinvf;
+  }
+  a.omega = (T)omega;
+  switch (ctx->p) {
+    case 1: launch_epi<1, T>(ctx, a, level, epi); break;
+    case 2: launch_epi<2, T>(ctx, a, level, epi); break;
+    case 3: launch_epi<3, T>(ctx, a, level, epi); break;
+    case 4: launch_epi<4, T>(ctx, a, level, epi); break;
+    case 5: launch_epi<5, T>(ctx, a, level, epi); break;
+    default: return set_err(ctx, IGA_E_INVALID, "p out of range");
+  }
+  CKL();
+  return IGA_OK;
+}
+
+template iga_status op_apply<double>(iga_ctx*, int, int, const double2*, double2*, const double2*, int,
+                                     const double2*, double);
+template iga_status op_apply<float>(iga_ctx*, int, int, const float2*, float2*, const float2*, int,
+                                    const float2*, double);
+
+iga_status setup_vark_diag(iga_ctx* ctx, int level) {
+  LevelData& L = ctx->lv[level];
+  L.dinv = dalloc<double2>(ctx, L.n);
+  L.dinvf = dalloc<float2>(ctx, L.n);
+  if (!L.dinv || !L.dinvf) return set_err(ctx, IGA_E_OOM, "dinv");
+  double2 c = make_double2(-ctx->sig.x, -ctx->sig.y);
+  k_vark_diag<<<cdiv(L.n, 128), 128, 0, ctx->st>>>(L.nx, L.n_el, ctx->p, L.K, L.M, L.B, L.wq, L.xq, ctx->kf, c,
+                                                   L.dinv, L.dinvf);
+  CKL();
+  return IGA_OK;
+}

@@ -1,0 +1,362 @@
+"""GPU-vs-oracle parity of every step of the hot path, called through the C ABI.
+
+Tolerances: knots/indices bit-exact; FP64 operators 1e-13 relative (a few
+ulps of rounding-order difference, times the band width); FP64 V-cycle and
+deflation 1e-11 (rounding amplified by the coarse solves); full GMRES solve
+1e-10 relative L2 against the oracle run with the same iteration count, as the
+contract for the FP64 path states; the FP32 V-cycle 1e-4 (single-precision
+storage and accumulation)."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import workloads as W
+from oracle import bspline
+from oracle import assembly as asm
+from oracle import multigrid as mg
+from oracle import deflation as dfl
+from oracle.solver import Solver, rel_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2010_10232_gb300.solver import Helmholtz, IgaError, from_problem  # noqa: E402
+
+CASES = {
+    "1d_p2": W.config1()[0],
+    "2d_p1": W.small_2d(n_el=40, p=1, k=15.0),
+    "2d_p2": W.small_2d(n_el=34, p=2, k=15.0),
+    "2d_p3": W.small_2d(n_el=40, p=3, k=20.0),
+    "2d_p4": W.small_2d(n_el=24, p=4, k=12.0),
+    "2d_p5": W.small_2d(n_el=20, p=5, k=10.0),
+    "2d_var_p2": W.small_2d(n_el=32, p=2, k=20.0, layered=True),
+    "2d_var_p3": W.small_2d(n_el=36, p=3, k=20.0, layered=True),
+}
+_cache = {}
+
+
+def ctx_and_oracle(name):
+    if name not in _cache:
+        pr = CASES[name]
+        _cache[name] = (from_problem(pr), Solver(pr), pr)
+    return _cache[name]
+
+
+def to_t(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.complex128)).cuda()
+
+
+def to_n(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def rvec(n, seed):
+    return W.seeded_complex_vector(n, seed)
+
+
+ALL = list(CASES)
+CONST2D = [c for c in ALL if c.startswith("2d_p")]
+
+
+# ------------------------------------------------------------------ setup tables
+@pytest.mark.parametrize("name", ALL)
+def test_knots_bitexact_and_levels(name):
+    h, s, pr = ctx_and_oracle(name)
+    sizes = mg.level_sizes(pr.n_el)
+    assert h.levels == len(sizes)
+    for l, ne in enumerate(sizes):
+        assert h.level_nel(l) == ne
+        assert h.level_nx(l) == ne + pr.p - 2
+        k_gpu = h.knots(l)
+        k_ora = bspline.open_uniform_knots(ne, pr.p)
+        assert k_gpu.tobytes() == k_ora.tobytes()
+
+
+@pytest.mark.parametrize("name", ["1d_p2", "2d_p1", "2d_p3", "2d_p5"])
+def test_band_matrices(name):
+    h, s, pr = ctx_and_oracle(name)
+    for l, ne in enumerate(mg.level_sizes(pr.n_el)):
+        K, M, _ = asm.assemble_1d(ne, pr.p)
+        K, M = asm.interior_1d(K).toarray(), asm.interior_1d(M).toarray()
+        for which, ref in ((0, K), (1, M)):
+            band = h.band(l, which)
+            n = ref.shape[0]
+            dense = np.zeros((n, n))
+            for i in range(n):
+                for d in range(-pr.p, pr.p + 1):
+                    if 0 <= i + d < n:
+                        dense[i, i + d] = band[i, d + pr.p]
+            assert np.max(np.abs(dense - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("name", ["1d_p2", "2d_p1", "2d_p2", "2d_p3", "2d_p4", "2d_p5"])
+def test_knot_insertion_prolongation(name):
+    h, s, pr = ctx_and_oracle(name)
+    for l in range(h.levels - 1):
+        ref = mg.prolongation_interior_1d(h.level_nel(l + 1), pr.p)
+        np.testing.assert_allclose(h.prolongation(l), ref, rtol=0, atol=1e-14)
+
+
+# ------------------------------------------------------------------ operators
+@pytest.mark.parametrize("name", ALL)
+def test_apply_A(name):
+    h, s, pr = ctx_and_oracle(name)
+    x = rvec(h.n, 11)
+    y = to_n(h.apply_A(to_t(x)))
+    ref = s.A @ x
+    assert rel_err(y, ref) <= 1e-13
+
+
+@pytest.mark.parametrize("name", ALL)
+def test_apply_Mshift_every_level(name):
+    h, s, pr = ctx_and_oracle(name)
+    for l, lvl in enumerate(s.mg.levels):
+        n = lvl.Mb.shape[0]
+        x = rvec(n, 20 + l)
+        y = to_n(h.apply_Mshift(l, to_t(x)))
+        assert rel_err(y, lvl.Mb @ x) <= 1e-13, l
+
+
+@pytest.mark.parametrize("name", ["1d_p2", "2d_p2", "2d_p3", "2d_var_p3"])
+def test_jacobi_sweeps(name):
+    h, s, pr = ctx_and_oracle(name)
+    for l in (0, 1):
+        lvl = s.mg.levels[l]
+        n = lvl.Mb.shape[0]
+        b, x0 = rvec(n, 30), rvec(n, 31)
+        for sweeps in (1, 2, 3):
+            ref = s.mg.jacobi(lvl, x0.copy(), b, sweeps)
+            got = to_n(h.jacobi(l, to_t(b), to_t(x0), sweeps))
+            assert rel_err(got, ref) <= 1e-13
+
+
+@pytest.mark.parametrize("name", ["1d_p2", "2d_p1", "2d_p3", "2d_p5", "2d_var_p2"])
+def test_restrict_prolong(name):
+    h, s, pr = ctx_and_oracle(name)
+    for l in range(h.levels - 1):
+        P = s.mg.P[l]
+        nf, nc = P.shape
+        r = rvec(nf, 40 + l)
+        assert rel_err(to_n(h.restrict(l, to_t(r))), P.T @ r) <= 1e-14
+        c, f = rvec(nc, 50 + l), rvec(nf, 60 + l)
+        got = to_n(h.prolong_add(l, to_t(c), to_t(f)))
+        assert rel_err(got, f + P @ c) <= 1e-14
+
+
+@pytest.mark.parametrize("name", ALL)
+def test_coarse_solve(name):
+    h, s, pr = ctx_and_oracle(name)
+    b = rvec(s.mg.coarse_dense.shape[0], 70)
+    got = to_n(h.coarse_solve(to_t(b)))
+    assert rel_err(got, np.linalg.solve(s.mg.coarse_dense, b)) <= 1e-11
+
+
+@pytest.mark.parametrize("name", ALL)
+def test_vcycle_fp64(name):
+    h, s, pr = ctx_and_oracle(name)
+    r = rvec(h.n, 80)
+    got = to_n(h.vcycle(to_t(r)))
+    assert rel_err(got, s.mg.apply(r, 1)) <= 1e-11
+
+
+@pytest.mark.parametrize("nu,cycles", [(2, 1), (3, 2), (0, 1)])
+def test_vcycle_fp64_variants(nu, cycles):
+    pr = W.small_2d(n_el=32, p=3, k=15.0)
+    pr.nu_pre = nu
+    pr.nu_post = max(nu, 1)
+    pr.n_vcycles = cycles
+    h = from_problem(pr)
+    hier = mg.MGHierarchy(2, 3, 32, pr.kfield, 1.0, 0.5, nu_pre=pr.nu_pre, nu_post=pr.nu_post)
+    r = rvec(h.n, 81)
+    assert rel_err(to_n(h.vcycle(to_t(r))), hier.apply(r, cycles)) <= 1e-11
+
+
+@pytest.mark.parametrize("name", ["2d_p3", "2d_var_p3", "1d_p2"])
+def test_vcycle_fp32(name):
+    pr = CASES[name]
+    h = from_problem(pr, precision=1)
+    s = ctx_and_oracle(name)[1]
+    r = rvec(h.n, 82)
+    assert rel_err(to_n(h.vcycle(to_t(r))), s.mg.apply(r, 1)) <= 1e-4
+
+
+# ------------------------------------------------------------------ deflation
+@pytest.mark.parametrize("name", [c for c in ALL if "var" not in c])
+def test_zt_z(name):
+    h, s, pr = ctx_and_oracle(name)
+    Z = s.Z
+    x = rvec(h.n, 90)
+    assert rel_err(to_n(h.zt(to_t(x))), Z.T @ x) <= 1e-14
+    c = rvec(h.m, 91)
+    assert rel_err(to_n(h.z(to_t(c))), Z @ c) <= 1e-14
+
+
+@pytest.mark.parametrize("name", [c for c in ALL if "var" not in c])
+def test_esolve_and_deflate(name):
+    h, s, pr = ctx_and_oracle(name)
+    t = rvec(h.m, 92)
+    ref = s.defl.lu.solve(t)
+    assert rel_err(to_n(h.esolve(to_t(t))), ref) <= 1e-10
+    x = rvec(h.n, 93)
+    assert rel_err(to_n(h.deflate(to_t(x))), s.defl.P(x)) <= 1e-10
+
+
+def test_eps_weighted_stencil():
+    pr = W.small_2d(n_el=24, p=2, k=12.0)
+    pr.eps = 0.37
+    h = from_problem(pr)
+    Z = dfl.z_matrix(2, pr.n_x, 0.37)
+    x = rvec(h.n, 94)
+    assert rel_err(to_n(h.zt(to_t(x))), Z.T @ x) <= 1e-14
+
+
+# ------------------------------------------------------------------ load + Arnoldi
+@pytest.mark.parametrize("name", ["1d_p2", "2d_p2", "2d_p3", "2d_p5"])
+def test_point_source(name):
+    h, s, pr = ctx_and_oracle(name)
+    for pos in ((0.5, 0.5), (0.1234, 0.8765), (0.0, 1.0), (1.0, 0.25)):
+        ref = asm.point_source(pr.dim, pr.p, pr.n_el, pos[:pr.dim])
+        got = to_n(h.point_source(*pos))
+        np.testing.assert_allclose(got, ref, rtol=0, atol=1e-15)
+
+
+def test_mgs_matches_numpy():
+    h, s, pr = ctx_and_oracle("2d_p3")
+    n = h.n
+    k = 6
+    rng = np.random.default_rng(5)
+    Vn = np.linalg.qr(rng.standard_normal((n, k)) + 1j * rng.standard_normal((n, k)))[0]
+    w = rvec(n, 95)
+    for j in (0, 2, 5):
+        ww = w.copy()
+        hs = []
+        for i in range(j + 1):
+            hi = np.vdot(Vn[:, i], ww)
+            hs.append(hi)
+            ww = ww - hi * Vn[:, i]
+        hs.append(np.linalg.norm(ww))
+        wt = to_t(w)
+        hg = to_n(h.mgs(to_t(Vn.T.copy()), j, wt))
+        np.testing.assert_allclose(hg, np.array(hs), rtol=1e-12, atol=1e-12)
+        assert rel_err(to_n(wt), ww) <= 1e-12
+
+
+# ------------------------------------------------------------------ solve
+def _solve_pair(name, f, tol=1e-7, maxit=100):
+    h, s, pr = ctx_and_oracle(name)
+    x, it, hist, tr, st = h.solve(to_t(f), tol=tol, maxit=maxit)
+    r = s.solve(f, tol=tol, maxit=maxit)
+    return to_n(x), it, hist, tr, st, r
+
+
+@pytest.mark.parametrize("name", ALL)
+def test_solve_point_source(name):
+    h, s, pr = ctx_and_oracle(name)
+    f = s.load()
+    x, it, hist, tr, st, r = _solve_pair(name, f)
+    assert st == 0 and r.converged
+    assert abs(it - r.iters) <= 1
+    np.testing.assert_allclose(hist[:min(it, r.iters) + 1], np.array(r.hist)[:min(it, r.iters) + 1], rtol=1e-6)
+    if it == r.iters:
+        assert rel_err(x, r.u) <= 1e-10
+    assert tr < 1e-5
+    err_direct = rel_err(x, s.direct(f))
+    print(f"{name}: iters gpu={it} oracle={r.iters} true_res={tr:.2e} err_vs_direct={err_direct:.2e}")
+
+
+def test_solve_config1_seeded_rhs():
+    h, s, pr = ctx_and_oracle("1d_p2")
+    f = W.seeded_normal_rhs(h.n, 0).astype(np.complex128)
+    x, it, hist, tr, st, r = _solve_pair("1d_p2", f)
+    assert st == 0 and it == r.iters
+    assert rel_err(x, r.u) <= 1e-10
+
+
+@pytest.mark.parametrize("name", ["2d_p2", "2d_p3", "2d_var_p3"])
+def test_iterates_at_same_count(name):
+    """FP64 path vs oracle at a fixed iteration count (tol = 0)."""
+    h, s, pr = ctx_and_oracle(name)
+    f = s.load()
+    for j in (1, 3, 6):
+        x, it, hist, tr, st = h.solve(to_t(f), tol=0.0, maxit=j)
+        assert st == 1 and it == j                        # IGA_NOT_CONVERGED
+        r = s.solve(f, tol=0.0, maxit=j)
+        assert rel_err(to_n(x), r.u) <= 1e-10
+
+
+def test_flexible_fp64_matches_oracle_fgmres():
+    name = "2d_p3"
+    pr = CASES[name]
+    s = ctx_and_oracle(name)[1]
+    h = from_problem(pr, flexible=1)
+    f = s.load()
+    x, it, hist, tr, st = h.solve(to_t(f))
+    r = s.solve(f, flexible=True)
+    assert st == 0 and abs(it - r.iters) <= 1
+    if it == r.iters:
+        assert rel_err(to_n(x), r.u) <= 1e-10
+
+
+@pytest.mark.parametrize("name", ["2d_p3", "2d_var_p3"])
+def test_mixed_precision_solve(name):
+    pr = CASES[name]
+    s = ctx_and_oracle(name)[1]
+    h = from_problem(pr, precision=1)
+    f = s.load()
+    x, it, hist, tr, st = h.solve(to_t(f), tol=1e-9)
+    assert st == 0
+    assert rel_err(to_n(x), s.direct(f)) <= 1e-6
+
+
+def test_solve_host_matches_device():
+    h, s, pr = ctx_and_oracle("2d_p2")
+    f = s.load()
+    xd, it1, *_ = h.solve(to_t(f))
+    xh, it2, *_ = h.solve_host(f)
+    assert it1 == it2
+    assert rel_err(xh, to_n(xd)) <= 1e-14
+
+
+def test_error_statuses():
+    h, s, pr = ctx_and_oracle("2d_p2")
+    f = to_t(s.load())
+    # maxit reached -> IGA_NOT_CONVERGED with valid outputs
+    x, it, hist, tr, st = h.solve(f, tol=1e-14, maxit=2)
+    assert st == 1 and it == 2
+    # misaligned pointer -> IGA_E_INVALID, nothing launched
+    buf = torch.zeros(2 * h.n + 2, dtype=torch.float64, device="cuda")
+    import ctypes
+    rc = h._L.iga_apply_A(h._h, ctypes.c_void_p(buf.data_ptr() + 8), ctypes.c_void_p(f.data_ptr()))
+    assert rc == -1
+    with pytest.raises(IgaError):
+        h.apply_A(f, f)                       # aliasing rejected
+
+
+# ------------------------------------------------------------------ full size (bench configuration)
+@pytest.fixture(scope="module")
+def cfg2_full():
+    pr = W.config2(k=200.0, p=3)
+    return from_problem(pr), Solver(pr), pr
+
+
+def test_full_size_apply_sampled(cfg2_full):
+    """320 x 320 elements, p = 3: full A x compared row by row with the oracle's
+    assembled matrix on 4096 sampled rows."""
+    h, s, pr = cfg2_full
+    x = rvec(h.n, 100)
+    y = to_n(h.apply_A(to_t(x)))
+    rows = np.random.default_rng(0).choice(h.n, 4096, replace=False)
+    ref = s.A[rows] @ x
+    assert rel_err(y[rows], ref) <= 1e-13
+
+
+def test_full_size_solve(cfg2_full):
+    h, s, pr = cfg2_full
+    f = s.load()
+    x, it, hist, tr, st = h.solve(to_t(f))
+    r = s.solve(f)
+    print(f"cfg2 k=200 p=3: iters gpu={it} oracle={r.iters} true_res={tr:.2e}")
+    assert st == 0 and abs(it - r.iters) <= 1
+    if it == r.iters:
+        assert rel_err(to_n(x), r.u) <= 1e-10

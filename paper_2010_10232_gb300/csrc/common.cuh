@@ -120,10 +120,14 @@ struct iga_ctx {
   double2* ct = nullptr;             // m-sized scratch
   double2* cs = nullptr;
   double2* cw = nullptr;
+  double2* ce1 = nullptr;            // refinement residual / correction
+  double2* ce2 = nullptr;
   // variable-k E (block tridiagonal, banded in y): see deflation.cu
-  int eblk = 0, enb = 0;             // block size (lines per block * mx), number of blocks
-  double2* eDinv = nullptr;          // [enb][bs][bs] inverse diagonal blocks
-  double2* eOff = nullptr;           // [enb][bs][bs] lower off-diagonal blocks E_{i,i-1}
+  int eblk = 0, enb = 0, els = 0;   // block size (lines per block * mx), number of blocks, lines
+  double2* eDinv = nullptr;          // [enb][bs][bs] inverse diagonal blocks D_I^{-1}
+  double2* eOff = nullptr;           // [enb][bs][bs] lower off-diagonal blocks E_{I,I-1}
+  double2* eF = nullptr;             // [enb][bs][bs] D_I^{-1} E_{I,I+1}
+  double2 *ep_t = nullptr, *ep_g = nullptr, *ep_v = nullptr;   // padded solve vectors
   // solve workspace
   double2* w0 = nullptr;             // n-sized vectors
   double2* w1 = nullptr;
@@ -203,6 +207,9 @@ iga_status defl_z(iga_ctx* ctx, const double2* c, double2* x);
 iga_status defl_esolve(iga_ctx* ctx, const double2* t, double2* s);
 iga_status defl_apply(iga_ctx* ctx, const double2* x, double2* y);        // y = P x
 iga_status defl_q(iga_ctx* ctx, const double2* x, double2* y);            // y = Q x
+// ecoarse.cu (variable k)
+iga_status setup_block_E(iga_ctx* ctx);
+iga_status block_E_solve(iga_ctx* ctx, const double2* t, double2* s);
 // krylov.cu
 iga_status kry_mgs(iga_ctx* ctx, const double2* V, size_t ldv, int j, double2* w, double2* h);
 iga_status kry_solve(iga_ctx* ctx, const double2* f, double2* x, double tol, int maxit, int* iters,

@@ -259,6 +259,58 @@ __global__ void k_crop(const double* W, int np, int n, double* out) {
   if (idx < n * n) { int i = idx / n, j = idx - i * n; out[idx] = W[(size_t)i * np + j]; }
 }
 
+// ------------------------------------------------------------------ accuracy fixes
+// Rayleigh quotients lambda_k = v_k^T Kc v_k / v_k^T Mc v_k with the original
+// (banded) coarse matrices: the eigenvalue error becomes quadratic in the
+// eigenvector error, which matters when lambda_i + lambda_j - k^2 nearly cancels.
+__global__ void k_rayleigh(const double* V, const double* Kc, const double* Mc, int n, int bw, double* lam) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  double num = 0.0, den = 0.0;
+  for (int i = 0; i < n; ++i) {
+    double vi = V[(size_t)i * n + k];
+    double sk = 0.0, sm = 0.0;
+    for (int j = max(0, i - bw); j <= min(n - 1, i + bw); ++j) {
+      double vj = V[(size_t)j * n + k];
+      sk += Kc[(size_t)i * n + j] * vj;
+      sm += Mc[(size_t)i * n + j] * vj;
+    }
+    num += vi * sk;
+    den += vi * sm;
+  }
+  lam[k] = num / den;
+}
+
+// r = t - E s with E = Mc (x) Kc + Kc (x) Mc - k^2 Mc (x) Mc (2D) or Kc - k^2 Mc
+// (1D), using the banded 1D coarse matrices (half bandwidth bw).
+__global__ void k_e_residual(const double* Kc, const double* Mc, int mx, int my, int bw, double k2,
+                             const double2* s, const double2* t, double2* r) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i >= (size_t)mx * my) return;
+  int iy = (int)(i / mx), ix = (int)(i - (size_t)iy * mx);
+  double2 acc = make_double2(0.0, 0.0);
+  if (my == 1) {
+    for (int b = max(0, ix - bw); b <= min(mx - 1, ix + bw); ++b)
+      acc = cfma(Kc[(size_t)ix * mx + b] - k2 * Mc[(size_t)ix * mx + b], s[b], acc);
+  } else {
+    for (int a = max(0, iy - bw); a <= min(my - 1, iy + bw); ++a) {
+      double my_ = Mc[(size_t)iy * mx + a], ky_ = Kc[(size_t)iy * mx + a];
+      double2 rk = make_double2(0.0, 0.0), rm = make_double2(0.0, 0.0);
+      for (int b = max(0, ix - bw); b <= min(mx - 1, ix + bw); ++b) {
+        double2 v = s[(size_t)a * mx + b];
+        rk = cfma(Kc[(size_t)ix * mx + b], v, rk);
+        rm = cfma(Mc[(size_t)ix * mx + b], v, rm);
+      }
+      acc = acc + my_ * rk + (ky_ - k2 * my_) * rm;
+    }
+  }
+  r[i] = t[i] - acc;
+}
+__global__ void k_axpy_c(double2* y, const double2* x, size_t n) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = y[i] + x[i];
+}
+
 // ------------------------------------------------------------------ FDM apply GEMMs
 // out[i][j] = sum_k op(R)[i][k] X[k][j]  (LEFT)   or  sum_k X[i][k] op(R)[k][j]  (RIGHT)
 // R real m x m (row-major), X complex rows x cols.  TRANS: op(R) = R^T.
@@ -361,6 +413,7 @@ static iga_status fdm_setup(iga_ctx* ctx) {
   k_crop<<<cdiv((size_t)n * n, 256), 256, 0, st>>>(Vj, np, n, W);
   // generalised eigenvectors V = L^{-T} W
   k_trsm_lower_t<<<cdiv(n, 64), 64, 0, st>>>(Lm, W, ctx->fdmV, n);
+  k_rayleigh<<<cdiv(n, 64), 64, 0, st>>>(ctx->fdmV, ctx->kc, ctx->mc, n, (ctx->p + 4) / 2 + 1, ctx->fdmL);
   CKL();
   int hinfo = 0;
   CK(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -377,13 +430,16 @@ iga_status setup_deflation(iga_ctx* ctx) {
   ctx->ct = dalloc<double2>(ctx, ctx->m);
   ctx->cs = dalloc<double2>(ctx, ctx->m);
   ctx->cw = dalloc<double2>(ctx, ctx->m);
+  ctx->ce1 = dalloc<double2>(ctx, ctx->m);
+  ctx->ce2 = dalloc<double2>(ctx, ctx->m);
+  if (!ctx->ce1 || !ctx->ce2) return set_err(ctx, IGA_E_OOM, "deflation alloc");
   ctx->kc = dalloc<double>(ctx, (size_t)ctx->mx * ctx->mx);
   ctx->mc = dalloc<double>(ctx, (size_t)ctx->mx * ctx->mx);
   if (!ctx->ct || !ctx->cs || !ctx->cw || !ctx->kc || !ctx->mc) return set_err(ctx, IGA_E_OOM, "deflation alloc");
   k_coarse_1d<<<cdiv((size_t)ctx->mx * ctx->mx, 128), 128, 0, ctx->st>>>(L.nx, ctx->mx, ctx->p, ctx->prm.eps, L.K, L.M,
                                                                        ctx->kc, ctx->mc);
   CKL();
-  if (ctx->vark) return set_err(ctx, IGA_E_UNSUPPORTED, "variable-k coarse solve not built");
+  if (ctx->vark) return setup_block_E(ctx);
   return fdm_setup(ctx);
 }
 
@@ -403,7 +459,8 @@ iga_status defl_z(iga_ctx* ctx, const double2* c, double2* x) {
   return IGA_OK;
 }
 
-iga_status defl_esolve(iga_ctx* ctx, const double2* t, double2* s) {
+// s = E^{-1} t by fast diagonalisation (constant k); cw is scratch
+static iga_status fdm_solve(iga_ctx* ctx, const double2* t, double2* s) {
   const int mx = ctx->mx;
   const double k2 = ctx->k2const;
   dim3 blk(16, 16);
@@ -421,6 +478,21 @@ iga_status defl_esolve(iga_ctx* ctx, const double2* t, double2* s) {
   k_fdm_gemm<false, false, true><<<g, blk, 0, ctx->st>>>(ctx->fdmV, ctx->cw, s, mx, mx, ctx->fdmL, ctx->fdmL, k2);
   k_fdm_gemm<true, false, false><<<g, blk, 0, ctx->st>>>(ctx->fdmV, s, ctx->cw, mx, mx, nullptr, nullptr, 0.0);
   k_fdm_gemm<false, true, false><<<g, blk, 0, ctx->st>>>(ctx->fdmV, ctx->cw, s, mx, mx, nullptr, nullptr, 0.0);
+  CKL();
+  return IGA_OK;
+}
+
+// s = E^{-1} t.  Constant k: fast diagonalisation plus one step of iterative
+// refinement with the exact banded E (the coarse problem can be nearly
+// singular when lambda_i + lambda_j ~ k^2).  Variable k: block LU.
+iga_status defl_esolve(iga_ctx* ctx, const double2* t, double2* s) {
+  if (ctx->vark) return block_E_solve(ctx, t, s);
+  TRY(fdm_solve(ctx, t, s));
+  const int my = ctx->dim == 2 ? ctx->mx : 1;
+  k_e_residual<<<cdiv(ctx->m, 256), 256, 0, ctx->st>>>(ctx->kc, ctx->mc, ctx->mx, my, (ctx->p + 4) / 2 + 1,
+                                                       ctx->k2const, s, t, ctx->ce1);
+  TRY(fdm_solve(ctx, ctx->ce1, ctx->ce2));
+  k_axpy_c<<<cdiv(ctx->m, 256), 256, 0, ctx->st>>>(s, ctx->ce2, ctx->m);
   CKL();
   return IGA_OK;
 }

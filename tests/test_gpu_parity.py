@@ -182,7 +182,7 @@ def test_vcycle_fp32(name):
 
 
 # ------------------------------------------------------------------ deflation
-@pytest.mark.parametrize("name", [c for c in ALL if "var" not in c])
+@pytest.mark.parametrize("name", ALL)
 def test_zt_z(name):
     h, s, pr = ctx_and_oracle(name)
     Z = s.Z
@@ -192,7 +192,7 @@ def test_zt_z(name):
     assert rel_err(to_n(h.z(to_t(c))), Z @ c) <= 1e-14
 
 
-@pytest.mark.parametrize("name", [c for c in ALL if "var" not in c])
+@pytest.mark.parametrize("name", ALL)
 def test_esolve_and_deflate(name):
     h, s, pr = ctx_and_oracle(name)
     t = rvec(h.m, 92)

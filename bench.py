@@ -1,0 +1,332 @@
+#!/usr/bin/env python
+"""Benchmark: 2D deflated, CSLP-multigrid-preconditioned GMRES solve to 1e-7
+on the GB300 (one solve = one step), plus operator / V-cycle bandwidth.
+
+Workload (one step): MP 2-A, unit square, constant k = 200, p = 3, 320 x 320
+elements (n = 103 041 complex128 dofs), unit point source at the centre,
+CSLP shift (1, 0.5), one V-cycle (nu = 1/1), ADP deflation, FP64 throughout,
+tol 1e-7, maxit 100.  Inputs are resident on the device before the timed
+region; L2 is flushed (a 512 MiB buffer is written) before every timed solve.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+K_WAVE, P_DEG, N_EL = 200.0, 3, 320
+METRIC = "2D solve time to 1e-7 rel. residual + iterations; apply/V-cycle HBM GB/s vs peak"
+WORKLOAD = f"MP2-A constant k={int(K_WAVE)}, p={P_DEG}, {N_EL}x{N_EL} elements, centre point source"
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.3)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------------------- CPU oracle legs
+ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import workloads as W
+from oracle.solver import Solver
+pr = W.config2(k={k}, p={p})
+t0 = time.perf_counter(); s = Solver(pr); f = s.load(); t1 = time.perf_counter()
+times, iters = [], None
+for _ in range({reps}):
+    a = time.perf_counter(); r = s.solve(f, tol=1e-7, maxit=100); times.append(time.perf_counter() - a); iters = r.iters
+print(json.dumps({{"setup_s": t1 - t0, "solve_s": times, "iters": iters, "true_res": r.true_res}}))
+"""
+
+
+def run_oracle(reps: int) -> dict:
+    """FP64 oracle on the host cores, single-threaded (BLAS threads pinned to 1)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    code = ORACLE_SNIPPET.format(root=ROOT, k=K_WAVE, p=P_DEG, reps=reps)
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def reference_arm(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    r = run_oracle(args.warmup + args.steps)
+    times = r["solve_s"][args.warmup:]
+    ms = 1000.0 * sum(times) / len(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic", "iterations": r["iters"],
+        "config": {"workload": WORKLOAD, "n_dof": (N_EL + P_DEG - 2) ** 2, "tol": 1e-7},
+        "cpu_baseline": {"value": ms, "unit": "ms", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} full FP64 oracle solves of the same problem (setup excluded)"},
+        "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------- GPU arm
+def gpu_arm(args):
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2010_10232_gb300 import _ffi
+    from paper_2010_10232_gb300.solver import Helmholtz, from_problem
+    import ctypes as C
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    lib = _ffi.lib()
+    stream = torch.cuda.current_stream()
+    pr = W.config2(k=K_WAVE, p=P_DEG)
+    h = from_problem(pr)
+    f = h.point_source(*pr.sources[0])
+    x = h.vec()
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        _, iters, hist, tr, st = h.solve(f, x=x)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches0 = lib.iga_launch_count()
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.fill_(k & 255)
+            ev[k][0].record(stream)
+            _, iters, hist, tr, st = h.solve(f, x=x)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    launches = lib.iga_launch_count() - launches0 - 0   # fill_ is torch's, not counted
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    value = ms / ws          # job-level time per solve: N replicas solve N instances per step
+
+    # ---- end to end through the public API with host buffers (copies inside the timed region)
+    fh = f.cpu().numpy()
+    h.solve_host(fh)
+    torch.cuda.synchronize()
+    e2e_t = []
+    for k in range(max(3, args.steps // 2)):
+        flush.fill_(k & 255)
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        xh, it2, *_ = h.solve_host(fh)
+        e2e_t.append(time.perf_counter() - a)
+    e2e_ms = 1000.0 * sum(e2e_t) / len(e2e_t)
+
+    # ---- dominant kernel: FP64 operator apply (constant-k banded tile kernel), timed alone
+    peaks, src = _peaks()
+    reps = 200
+    xr = torch.randn(h.n, dtype=torch.complex128, device="cuda")
+    yr = h.vec()
+    for _ in range(10):
+        h.apply_A(xr, yr)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        h.apply_A(xr, yr)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_apply = e0.elapsed_time(e1) / reps * 1e-3
+    W_ = 2 * P_DEG + 1
+    flops_dof = 16 * W_ + 8                      # x-pass 2 bands, y-pass 2 bands, complex scale
+    apply_flops = flops_dof * h.n
+    apply_bytes = 32 * h.n
+    # FP64 / FP32 FMA ceilings from the probe kernel
+    sink = torch.zeros(2, dtype=torch.float64, device="cuda")
+    probe = {}
+    for prec, name in ((0, "fp64"), (1, "fp32")):
+        fl = C.c_double(0.0)
+        its = 4096 if prec == 0 else 65536
+        lib.iga_probe_fma(prec, 64, C.c_void_p(sink.data_ptr()), C.c_void_p(stream.cuda_stream), C.byref(fl))
+        e0.record(stream)
+        lib.iga_probe_fma(prec, its, C.c_void_p(sink.data_ptr()), C.c_void_p(stream.cuda_stream), C.byref(fl))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        probe[name] = fl.value / (e0.elapsed_time(e1) * 1e-3) / 1e12
+    fp64_nominal = 1.25                            # TFLOP/s, GB300 FP64 (profiling recipe)
+    achieved_gflops = apply_flops / t_apply / 1e9
+
+    # ---- out-of-L2 operator / V-cycle bandwidth (n = 4097^2, 268 MB per complex128 vector)
+    big = {}
+    try:
+        hb64 = Helmholtz(dim=2, p=P_DEG, n_el=4096, kfield=K_WAVE * 4096 / N_EL, skip_deflation=1)
+        nb = hb64.n
+        xb = torch.randn(nb, dtype=torch.complex128, device="cuda")
+        yb = hb64.vec()
+        for _ in range(3):
+            hb64.apply_A(xb, yb)
+        e0.record(stream)
+        for _ in range(10):
+            hb64.apply_A(xb, yb)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tb = e0.elapsed_time(e1) / 10 * 1e-3
+        big["apply_fp64_n"] = nb
+        big["apply_fp64_gbs"] = 32 * nb / tb / 1e9
+        big["apply_fp64_tflops"] = flops_dof * nb / tb / 1e12
+        del hb64, yb
+        hb32 = Helmholtz(dim=2, p=P_DEG, n_el=4096, kfield=K_WAVE * 4096 / N_EL, skip_deflation=1, precision=1)
+        zb = hb32.vec()
+        for _ in range(2):
+            hb32.vcycle(xb, zb)
+        e0.record(stream)
+        for _ in range(5):
+            hb32.vcycle(xb, zb)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tv = e0.elapsed_time(e1) / 5 * 1e-3
+        # algorithmic bytes of one FP32 V-cycle (nu = 1/1) with complex64 storage:
+        # per level n_l*(16 jacobi0 + 24 residual + 8 restrict-read + 16 prolong rmw + 24 post)
+        # + n_{l+1}*(8 restrict-write + 8 prolong-read); plus the c128<->c64 conversions at level 0.
+        ns = [hb32.level_n(l) for l in range(hb32.levels)]
+        vb = sum(ns[l] * 88 + ns[l + 1] * 16 for l in range(len(ns) - 1)) + 48 * ns[0]
+        big["vcycle_fp32_gbs"] = vb / tv / 1e9
+        big["vcycle_fp32_ms"] = tv * 1e3
+        big["vcycle_fp32_bytes"] = vb
+        del hb32, zb, xb
+    except Exception as e:       # report, do not hide
+        big["error"] = str(e)[:200]
+
+    if rank != 0:
+        return
+    cpu = None
+    if ws == 1 and not args.no_cpu:
+        try:
+            r = run_oracle(3)
+            cpu_ms = 1000.0 * sum(r["solve_s"]) / len(r["solve_s"])
+            cpu = {"value": cpu_ms, "unit": "ms", "cores": 1, "kind": "oracle",
+                   "sample": "3 full FP64 oracle solves of the bench problem, single-threaded, setup excluded",
+                   "iters": r["iters"]}
+        except Exception as e:
+            cpu = {"value": None, "unit": "ms", "cores": 1, "kind": "oracle", "sample": f"failed: {e}"[:200]}
+    line = {
+        "metric": METRIC, "value": value, "unit": "ms", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_dof": h.n, "coarse_dof": h.m, "levels": h.levels, "tol": 1e-7,
+                   "precision": "fp64", "l2": "flushed (512 MiB write) before every timed solve",
+                   "parallelism": f"replicas x{ws}"},
+        "iterations": iters, "true_res": tr,
+        "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": 16 * h.n, "d2h_bytes_per_step": 16 * h.n},
+        "gpu_launches": int(launches),
+        "roofline": {"kernel": "k_kron2d<3,double,EPI_Y> (apply A)", "bound": "alu",
+                     "achieved": achieved_gflops / 1e3, "peak": fp64_nominal, "unit": "TFLOP/s",
+                     "frac": achieved_gflops / 1e3 / fp64_nominal, "traffic": None,
+                     "algorithmic": f"{flops_dof} flop/dof x {h.n} dofs per launch",
+                     "peak_source": "nominal FP64 of the profiling recipe",
+                     "probe_fma_tflops": probe, "launch_us": t_apply * 1e6,
+                     "hbm_gbs": apply_bytes / t_apply / 1e9},
+        "out_of_l2": dict(big, hbm_peak_gbs=peaks.get("hbm_gbs"), peak_source=src),
+        "clocks": clk.summary(),
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -70,6 +70,8 @@ typedef struct {
                                  FP64 flexible GMRES                                      */
   int flexible;            /* 1: right-preconditioned FGMRES even in FP64 (precision 1
                               implies it)                                                 */
+  int skip_deflation;      /* 1: operator / V-cycle context only (no Z, E); deflation and
+                              solve entry points then return IGA_E_INVALID                 */
   void* stream;            /* cudaStream_t for all work of this context                   */
 } iga_params;
 
@@ -94,6 +96,9 @@ int iga_num_levels(const iga_ctx* ctx);
 int iga_level_nx(const iga_ctx* ctx, int level);       /* interior functions per direction */
 int iga_level_nel(const iga_ctx* ctx, int level);
 const char* iga_status_str(iga_status s);
+/* Number of kernels this library has launched in the process so far (host
+   counter, incremented at every launch site). */
+unsigned long long iga_launch_count(void);
 const char* iga_last_error(const iga_ctx* ctx);
 
 /* Copy the open knot vector of multigrid level `level` (n_el_l + 2p + 1 doubles,
@@ -172,6 +177,13 @@ iga_status iga_solve(iga_ctx* ctx, const iga_c128* rhs, iga_c128* x, double tol,
    device->host copies are part of the call. */
 iga_status iga_solve_host(iga_ctx* ctx, const iga_c128* rhs_host, iga_c128* x_host, double tol,
                           int maxit, int* iters, double* res_hist, double* true_res);
+
+/* Measurement helper (no counterpart in the paper): launches 8 independent
+   FMA chains per thread on 8 x SM-count blocks of 256 threads, in FP64
+   (precision 0) or FP32 (1), on `stream`; *flops (HOST) receives the flop count
+   of the launch, so the caller can time it and state the ALU ceiling that
+   bounds the FP64 operators.  sink: device scratch of one double. */
+iga_status iga_probe_fma(int precision, int iters, void* sink, void* stream, double* flops);
 
 #ifdef __cplusplus
 }

@@ -33,6 +33,7 @@ class IgaParams(C.Structure):
         ("n_vcycles", C.c_int),
         ("precision", C.c_int),
         ("flexible", C.c_int),
+        ("skip_deflation", C.c_int),
         ("stream", C.c_void_p),
     ]
 
@@ -48,6 +49,8 @@ _SIG = {
     "iga_level_nx": (C.c_int, [_VP, C.c_int]),
     "iga_level_nel": (C.c_int, [_VP, C.c_int]),
     "iga_status_str": (C.c_char_p, [C.c_int]),
+    "iga_launch_count": (C.c_ulonglong, []),
+    "iga_probe_fma": (C.c_int, [C.c_int, C.c_int, _VP, _VP, C.POINTER(C.c_double)]),
     "iga_last_error": (C.c_char_p, [_VP]),
     "iga_get_knots": (C.c_int, [_VP, C.c_int, _VP, C.c_int]),
     "iga_get_band": (C.c_int, [_VP, C.c_int, C.c_int, _VP, C.c_size_t]),

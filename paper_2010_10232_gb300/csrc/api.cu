@@ -5,7 +5,11 @@
 #include <cmath>
 #include <new>
 
+#include <atomic>
+
 static bool aligned16(const void* p) { return p && (((uintptr_t)p) & 15u) == 0; }
+static std::atomic<unsigned long long> g_launches{0};
+void iga_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 extern "C" {
 
@@ -26,6 +30,7 @@ void iga_default_params(iga_params* prm) {
   d.n_vcycles = 1;
   d.precision = 0;
   d.flexible = 0;
+  d.skip_deflation = 0;
   d.stream = nullptr;
   *prm = d;
 }
@@ -46,6 +51,8 @@ const char* iga_status_str(iga_status s) {
 }
 
 const char* iga_last_error(const iga_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+unsigned long long iga_launch_count(void) { return g_launches.load(); }
 
 static iga_status alloc_level_vectors(iga_ctx* ctx) {
   for (int l = 0; l < ctx->L; ++l) {
@@ -112,7 +119,7 @@ iga_status iga_setup(const iga_params* prm, iga_ctx** out) {
       s = set_err(ctx, IGA_E_OOM, "work vectors");
       break;
     }
-    if ((s = setup_deflation(ctx)) != IGA_OK) break;
+    if (!P.skip_deflation && (s = setup_deflation(ctx)) != IGA_OK) break;
     cudaError_t e = cudaStreamSynchronize(ctx->st);
     if (e != cudaSuccess) { s = set_err(ctx, IGA_E_CUDA, "setup: %s", cudaGetErrorString(e)); break; }
   } while (0);
@@ -180,6 +187,7 @@ iga_status iga_get_prolongation(iga_ctx* ctx, int level, double* out, size_t cap
 }
 
 #define CHECK_CTX() do { if (!ctx) return IGA_E_INVALID; } while (0)
+#define CHECK_DEFL() do { if (ctx->prm.skip_deflation) return set_err(ctx, IGA_E_INVALID, "context built without deflation"); } while (0)
 #define CHECK_PTR(p) do { if (!aligned16(p)) return set_err(ctx, IGA_E_INVALID, "pointer %s NULL or not 16-byte aligned", #p); } while (0)
 
 iga_status iga_apply_A(iga_ctx* ctx, const iga_c128* x, iga_c128* y) {
@@ -240,20 +248,20 @@ iga_status iga_vcycle_cslp(iga_ctx* ctx, const iga_c128* r, iga_c128* z) {
 }
 
 iga_status iga_zt(iga_ctx* ctx, const iga_c128* x, iga_c128* c) {
-  CHECK_CTX(); CHECK_PTR(x); CHECK_PTR(c);
+  CHECK_CTX(); CHECK_DEFL(); CHECK_PTR(x); CHECK_PTR(c);
   return defl_zt(ctx, (const double2*)x, (double2*)c);
 }
 iga_status iga_z(iga_ctx* ctx, const iga_c128* c, iga_c128* x) {
-  CHECK_CTX(); CHECK_PTR(x); CHECK_PTR(c);
+  CHECK_CTX(); CHECK_DEFL(); CHECK_PTR(x); CHECK_PTR(c);
   return defl_z(ctx, (const double2*)c, (double2*)x);
 }
 iga_status iga_esolve(iga_ctx* ctx, const iga_c128* t, iga_c128* s) {
-  CHECK_CTX(); CHECK_PTR(t); CHECK_PTR(s);
+  CHECK_CTX(); CHECK_DEFL(); CHECK_PTR(t); CHECK_PTR(s);
   if ((const void*)t == (const void*)s) return set_err(ctx, IGA_E_INVALID, "t and s alias");
   return defl_esolve(ctx, (const double2*)t, (double2*)s);
 }
 iga_status iga_deflate(iga_ctx* ctx, const iga_c128* x, iga_c128* y) {
-  CHECK_CTX(); CHECK_PTR(x); CHECK_PTR(y);
+  CHECK_CTX(); CHECK_DEFL(); CHECK_PTR(x); CHECK_PTR(y);
   if ((const void*)x == (const void*)y) return set_err(ctx, IGA_E_INVALID, "x and y alias");
   return defl_apply(ctx, (const double2*)x, (double2*)y);
 }
@@ -267,7 +275,7 @@ iga_status iga_load_point_source(iga_ctx* ctx, double x0, double y0, iga_c128* f
     return set_err(ctx, IGA_E_INVALID, "source outside the domain");
   const LevelData& L = ctx->lv[0];
   CK(cudaMemsetAsync(f, 0, sizeof(double2) * L.n, ctx->st));
-  k_point_source<<<1, 32, 0, ctx->st>>>(L.knots, L.n_el, ctx->p, L.nx, ctx->dim, x0, y0, (double2*)f);
+  k_point_source<<<1, 32, 0, ctx->st>>>(L.knots, L.n_el, ctx->p, L.nx, ctx->dim, x0, y0, (double2*)f); iga_count_launch();
   CKL();
   return IGA_OK;
 }
@@ -280,7 +288,7 @@ iga_status iga_mgs(iga_ctx* ctx, const iga_c128* V, size_t ldv, int j, iga_c128*
 
 iga_status iga_solve(iga_ctx* ctx, const iga_c128* rhs, iga_c128* x, double tol, int maxit, int* iters,
                      double* res_hist, double* true_res) {
-  CHECK_CTX(); CHECK_PTR(rhs); CHECK_PTR(x);
+  CHECK_CTX(); CHECK_DEFL(); CHECK_PTR(rhs); CHECK_PTR(x);
   if (maxit < 1 || maxit > 1000 || !(tol >= 0.0)) return set_err(ctx, IGA_E_INVALID, "tol / maxit");
   if ((const void*)rhs == (const void*)x) return set_err(ctx, IGA_E_INVALID, "rhs and x alias");
   return kry_solve(ctx, (const double2*)rhs, (double2*)x, tol, maxit, iters, res_hist, true_res);
@@ -288,7 +296,7 @@ iga_status iga_solve(iga_ctx* ctx, const iga_c128* rhs, iga_c128* x, double tol,
 
 iga_status iga_solve_host(iga_ctx* ctx, const iga_c128* rhs_host, iga_c128* x_host, double tol, int maxit,
                           int* iters, double* res_hist, double* true_res) {
-  CHECK_CTX();
+  CHECK_CTX(); CHECK_DEFL();
   if (!rhs_host || !x_host) return set_err(ctx, IGA_E_INVALID, "NULL host pointer");
   if (ctx->maxit_alloc < 0 && maxit > 0) { /* workspace is allocated by the solve itself */ }
   size_t n = ctx->lv[0].n;

@@ -157,6 +157,9 @@ struct iga_ctx {
 #define IGA_RED_THREADS 256
 
 // ------------------------------------------------------------------ host helpers
+// Every kernel launch site calls this once per launch (process-wide counter,
+// read with iga_launch_count()).
+void iga_count_launch();
 iga_status set_err(iga_ctx* c, iga_status s, const char* fmt, ...);
 template <typename T> inline T* dalloc(iga_ctx* c, size_t count) {
   void* p = nullptr;

@@ -380,14 +380,14 @@ static iga_status fdm_setup(iga_ctx* ctx) {
     return set_err(ctx, IGA_E_OOM, "fdm alloc");
   CK(cudaMemsetAsync(info, 0, sizeof(int), st));
   CK(cudaMemcpyAsync(Lm, ctx->mc, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, st));
-  k_cholesky<<<1, 512, 0, st>>>(Lm, n, info);
+  k_cholesky<<<1, 512, 0, st>>>(Lm, n, info); iga_count_launch();
   CKL();
   // C = L^{-1} Kc L^{-T} = L^{-1} (L^{-1} Kc)^T
-  k_trsm_lower<<<cdiv(n, 64), 64, 0, st>>>(Lm, ctx->kc, Y, n);
-  k_transpose<<<cdiv((size_t)n * n, 256), 256, 0, st>>>(Y, Yt, n);
-  k_trsm_lower<<<cdiv(n, 64), 64, 0, st>>>(Lm, Yt, Cm, n);
-  k_pad_sym<<<cdiv((size_t)np * np, 256), 256, 0, st>>>(Cm, A0, n, np);
-  k_eye_d<<<cdiv((size_t)np * np, 256), 256, 0, st>>>(Vj, np);
+  k_trsm_lower<<<cdiv(n, 64), 64, 0, st>>>(Lm, ctx->kc, Y, n); iga_count_launch();
+  k_transpose<<<cdiv((size_t)n * n, 256), 256, 0, st>>>(Y, Yt, n); iga_count_launch();
+  k_trsm_lower<<<cdiv(n, 64), 64, 0, st>>>(Lm, Yt, Cm, n); iga_count_launch();
+  k_pad_sym<<<cdiv((size_t)np * np, 256), 256, 0, st>>>(Cm, A0, n, np); iga_count_launch();
+  k_eye_d<<<cdiv((size_t)np * np, 256), 256, 0, st>>>(Vj, np); iga_count_launch();
   CKL();
   double hn[2] = {0, 0};
   double* cur = A0;
@@ -397,23 +397,23 @@ static iga_status fdm_setup(iga_ctx* ctx) {
   const int h = np / 2;
   for (int sweep = 0; sweep < 40 && !conv; ++sweep) {
     for (int r = 0; r < np - 1; ++r) {
-      k_jac_angles<<<cdiv(h, 128), 128, 0, st>>>(cur, np, r, cs);
-      k_jac_apply<<<cdiv((size_t)h * h + (size_t)np * h, 256), 256, 0, st>>>(cur, nxt, Vj, np, cs);
+      k_jac_angles<<<cdiv(h, 128), 128, 0, st>>>(cur, np, r, cs); iga_count_launch();
+      k_jac_apply<<<cdiv((size_t)h * h + (size_t)np * h, 256), 256, 0, st>>>(cur, nxt, Vj, np, cs); iga_count_launch();
       std::swap(cur, nxt);
     }
     CKL();
-    k_offnorm<<<1, 256, 0, st>>>(cur, np, nrm);
+    k_offnorm<<<1, 256, 0, st>>>(cur, np, nrm); iga_count_launch();
     CK(cudaMemcpyAsync(hn, nrm, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (extra >= 0) conv = true;
     else if (hn[0] <= 1e-26 * hn[1] || hn[0] == 0.0) extra = sweep;
   }
   if (!conv) return set_err(ctx, IGA_E_INVALID, "Jacobi eigen-solver did not converge (off %.3e)", hn[0]);
-  k_diag_extract<<<cdiv(n, 128), 128, 0, st>>>(cur, np, n, ctx->fdmL);
-  k_crop<<<cdiv((size_t)n * n, 256), 256, 0, st>>>(Vj, np, n, W);
+  k_diag_extract<<<cdiv(n, 128), 128, 0, st>>>(cur, np, n, ctx->fdmL); iga_count_launch();
+  k_crop<<<cdiv((size_t)n * n, 256), 256, 0, st>>>(Vj, np, n, W); iga_count_launch();
   // generalised eigenvectors V = L^{-T} W
-  k_trsm_lower_t<<<cdiv(n, 64), 64, 0, st>>>(Lm, W, ctx->fdmV, n);
-  k_rayleigh<<<cdiv(n, 64), 64, 0, st>>>(ctx->fdmV, ctx->kc, ctx->mc, n, (ctx->p + 4) / 2 + 1, ctx->fdmL);
+  k_trsm_lower_t<<<cdiv(n, 64), 64, 0, st>>>(Lm, W, ctx->fdmV, n); iga_count_launch();
+  k_rayleigh<<<cdiv(n, 64), 64, 0, st>>>(ctx->fdmV, ctx->kc, ctx->mc, n, (ctx->p + 4) / 2 + 1, ctx->fdmL); iga_count_launch();
   CKL();
   int hinfo = 0;
   CK(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -437,7 +437,7 @@ iga_status setup_deflation(iga_ctx* ctx) {
   ctx->mc = dalloc<double>(ctx, (size_t)ctx->mx * ctx->mx);
   if (!ctx->ct || !ctx->cs || !ctx->cw || !ctx->kc || !ctx->mc) return set_err(ctx, IGA_E_OOM, "deflation alloc");
   k_coarse_1d<<<cdiv((size_t)ctx->mx * ctx->mx, 128), 128, 0, ctx->st>>>(L.nx, ctx->mx, ctx->p, ctx->prm.eps, L.K, L.M,
-                                                                       ctx->kc, ctx->mc);
+                                                                       ctx->kc, ctx->mc); iga_count_launch();
   CKL();
   if (ctx->vark) return setup_block_E(ctx);
   return fdm_setup(ctx);
@@ -446,7 +446,7 @@ iga_status setup_deflation(iga_ctx* ctx) {
 iga_status defl_zt(iga_ctx* ctx, const double2* x, double2* c) {
   const LevelData& L = ctx->lv[0];
   int my = ctx->dim == 2 ? ctx->mx : 1;
-  k_zt<<<cdiv(ctx->m, 256), 256, 0, ctx->st>>>(L.nx, L.ny, ctx->mx, my, ctx->prm.eps, x, c);
+  k_zt<<<cdiv(ctx->m, 256), 256, 0, ctx->st>>>(L.nx, L.ny, ctx->mx, my, ctx->prm.eps, x, c); iga_count_launch();
   CKL();
   return IGA_OK;
 }
@@ -454,7 +454,7 @@ iga_status defl_zt(iga_ctx* ctx, const double2* x, double2* c) {
 iga_status defl_z(iga_ctx* ctx, const double2* c, double2* x) {
   const LevelData& L = ctx->lv[0];
   int my = ctx->dim == 2 ? ctx->mx : 1;
-  k_z<<<cdiv(L.n, 256), 256, 0, ctx->st>>>(L.nx, L.ny, ctx->mx, my, ctx->prm.eps, c, x);
+  k_z<<<cdiv(L.n, 256), 256, 0, ctx->st>>>(L.nx, L.ny, ctx->mx, my, ctx->prm.eps, c, x); iga_count_launch();
   CKL();
   return IGA_OK;
 }
@@ -467,17 +467,17 @@ static iga_status fdm_solve(iga_ctx* ctx, const double2* t, double2* s) {
   if (ctx->dim == 1) {
     // s = V ((V^T t) / (lambda - k^2)) with t as a 1 x m row: (t V) / d, then (.) V^T
     dim3 g(cdiv(mx, 16), 1);
-    k_fdm_gemm<false, false, true><<<g, blk, 0, ctx->st>>>(ctx->fdmV, t, ctx->cw, 1, mx, nullptr, ctx->fdmL, k2);
-    k_fdm_gemm<false, true, false><<<g, blk, 0, ctx->st>>>(ctx->fdmV, ctx->cw, s, 1, mx, nullptr, nullptr, 0.0);
+    k_fdm_gemm<false, false, true><<<g, blk, 0, ctx->st>>>(ctx->fdmV, t, ctx->cw, 1, mx, nullptr, ctx->fdmL, k2); iga_count_launch();
+    k_fdm_gemm<false, true, false><<<g, blk, 0, ctx->st>>>(ctx->fdmV, ctx->cw, s, 1, mx, nullptr, nullptr, 0.0); iga_count_launch();
     CKL();
     return IGA_OK;
   }
   dim3 g(cdiv(mx, 16), cdiv(mx, 16));
   // T1 = V^T T ; T2 = (T1 V) / D ; T3 = V T2 ; S = T3 V^T
-  k_fdm_gemm<true, true, false><<<g, blk, 0, ctx->st>>>(ctx->fdmV, t, ctx->cw, mx, mx, nullptr, nullptr, 0.0);
-  k_fdm_gemm<false, false, true><<<g, blk, 0, ctx->st>>>(ctx->fdmV, ctx->cw, s, mx, mx, ctx->fdmL, ctx->fdmL, k2);
-  k_fdm_gemm<true, false, false><<<g, blk, 0, ctx->st>>>(ctx->fdmV, s, ctx->cw, mx, mx, nullptr, nullptr, 0.0);
-  k_fdm_gemm<false, true, false><<<g, blk, 0, ctx->st>>>(ctx->fdmV, ctx->cw, s, mx, mx, nullptr, nullptr, 0.0);
+  k_fdm_gemm<true, true, false><<<g, blk, 0, ctx->st>>>(ctx->fdmV, t, ctx->cw, mx, mx, nullptr, nullptr, 0.0); iga_count_launch();
+  k_fdm_gemm<false, false, true><<<g, blk, 0, ctx->st>>>(ctx->fdmV, ctx->cw, s, mx, mx, ctx->fdmL, ctx->fdmL, k2); iga_count_launch();
+  k_fdm_gemm<true, false, false><<<g, blk, 0, ctx->st>>>(ctx->fdmV, s, ctx->cw, mx, mx, nullptr, nullptr, 0.0); iga_count_launch();
+  k_fdm_gemm<false, true, false><<<g, blk, 0, ctx->st>>>(ctx->fdmV, ctx->cw, s, mx, mx, nullptr, nullptr, 0.0); iga_count_launch();
   CKL();
   return IGA_OK;
 }
@@ -490,9 +490,9 @@ iga_status defl_esolve(iga_ctx* ctx, const double2* t, double2* s) {
   TRY(fdm_solve(ctx, t, s));
   const int my = ctx->dim == 2 ? ctx->mx : 1;
   k_e_residual<<<cdiv(ctx->m, 256), 256, 0, ctx->st>>>(ctx->kc, ctx->mc, ctx->mx, my, (ctx->p + 4) / 2 + 1,
-                                                       ctx->k2const, s, t, ctx->ce1);
+                                                       ctx->k2const, s, t, ctx->ce1); iga_count_launch();
   TRY(fdm_solve(ctx, ctx->ce1, ctx->ce2));
-  k_axpy_c<<<cdiv(ctx->m, 256), 256, 0, ctx->st>>>(s, ctx->ce2, ctx->m);
+  k_axpy_c<<<cdiv(ctx->m, 256), 256, 0, ctx->st>>>(s, ctx->ce2, ctx->m); iga_count_launch();
   CKL();
   return IGA_OK;
 }

@@ -177,10 +177,10 @@ __global__ void k_zgemv(int n, const double2* A, const double2* x, const double2
 }
 
 static iga_status gj_invert(iga_ctx* ctx, double2* A, double2* Inv, int n, double2* fcol, int* info) {
-  k_eye_c<<<cdiv((size_t)n * n, 256), 256, 0, ctx->st>>>(Inv, n);
+  k_eye_c<<<cdiv((size_t)n * n, 256), 256, 0, ctx->st>>>(Inv, n); iga_count_launch();
   for (int k = 0; k < n; ++k) {
-    k_gj_pivot<<<1, 256, 0, ctx->st>>>(A, Inv, n, k, fcol, info);
-    k_gj_elim<<<cdiv((size_t)n * n, 256), 256, 0, ctx->st>>>(A, Inv, n, k, fcol);
+    k_gj_pivot<<<1, 256, 0, ctx->st>>>(A, Inv, n, k, fcol, info); iga_count_launch();
+    k_gj_elim<<<cdiv((size_t)n * n, 256), 256, 0, ctx->st>>>(A, Inv, n, k, fcol); iga_count_launch();
   }
   CKL();
   return IGA_OK;
@@ -214,14 +214,14 @@ iga_status setup_block_E(iga_ctx* ctx) {
   LevelData& L = ctx->lv[0];
   for (int cy = 0; cy < S; ++cy)
     for (int cx = 0; cx < S; ++cx) {
-      k_probe<<<cdiv(m, 256), 256, 0, st>>>(mx, S, cx, cy, ctx->ct);
+      k_probe<<<cdiv(m, 256), 256, 0, st>>>(mx, S, cx, cy, ctx->ct); iga_count_launch();
       TRY(defl_z(ctx, ctx->ct, ctx->w3));
       TRY(op_apply<double>(ctx, 0, OP_A, ctx->w3, ctx->w2, nullptr, EPI_Y, nullptr, 0.0));
       TRY(defl_zt(ctx, ctx->w2, ctx->cs));
-      k_scatter_E<<<cdiv(m, 256), 256, 0, st>>>(mx, S, b, s, bs, cx, cy, ctx->cs, ctx->eF, ctx->eOff);
+      k_scatter_E<<<cdiv(m, 256), 256, 0, st>>>(mx, S, b, s, bs, cx, cy, ctx->cs, ctx->eF, ctx->eOff); iga_count_launch();
     }
   int first_pad = (mx - (nb - 1) * s) * mx;
-  if (first_pad < bs) k_pad_identity<<<cdiv(bs - first_pad, 128), 128, 0, st>>>(ctx->eF + blk * (nb - 1), bs, first_pad);
+  if (first_pad < bs) k_pad_identity<<<cdiv(bs - first_pad, 128), 128, 0, st>>>(ctx->eF + blk * (nb - 1), bs, first_pad); iga_count_launch();
   CKL();
   (void)L;
   dim3 gg(cdiv(bs, 32), cdiv(bs, 32));
@@ -230,9 +230,9 @@ iga_status setup_block_E(iga_ctx* ctx) {
     if (I > 0) {
       // T = D_{I-1}^{-1} E_{I-1,I} = Dinv_{I-1} El_I^T  -> stored as F_{I-1} in `work` first
       k_zgemm<true><<<gg, 256, 0, st>>>(bs, make_double2(1.0, 0.0), ctx->eDinv + blk * (I - 1), ctx->eOff + blk * I, 0.0,
-                                        work);
+                                        work); iga_count_launch();
       // D_I = E_II - El_I T
-      k_zgemm<false><<<gg, 256, 0, st>>>(bs, make_double2(-1.0, 0.0), ctx->eOff + blk * I, work, 1.0, EdI);
+      k_zgemm<false><<<gg, 256, 0, st>>>(bs, make_double2(-1.0, 0.0), ctx->eOff + blk * I, work, 1.0, EdI); iga_count_launch();
       // F_{I-1} = T  (E_{I-1,I-1} storage is free again: it holds D_{I-1} which is no longer needed)
       CK(cudaMemcpyAsync(ctx->eF + blk * (I - 1), work, sizeof(double2) * blk, cudaMemcpyDeviceToDevice, st));
     }
@@ -259,16 +259,16 @@ iga_status block_E_solve(iga_ctx* ctx, const double2* t, double2* s) {
   for (int I = 0; I < nb; ++I) {
     const double2* rhs = tp + (size_t)I * bs;
     if (I > 0) {
-      k_zgemv<true><<<gv, 256, 0, st>>>(bs, ctx->eOff + blk * I, g + (size_t)(I - 1) * bs, rhs, ctx->ep_v);
+      k_zgemv<true><<<gv, 256, 0, st>>>(bs, ctx->eOff + blk * I, g + (size_t)(I - 1) * bs, rhs, ctx->ep_v); iga_count_launch();
       rhs = ctx->ep_v;
     }
-    k_zgemv<false><<<gv, 256, 0, st>>>(bs, ctx->eDinv + blk * I, rhs, nullptr, g + (size_t)I * bs);
+    k_zgemv<false><<<gv, 256, 0, st>>>(bs, ctx->eDinv + blk * I, rhs, nullptr, g + (size_t)I * bs); iga_count_launch();
   }
   // back substitution in place on g: s_I = g_I - F_I s_{I+1} (each output is read
   // and written by the same lane, so the update is in place)
   for (int I = nb - 2; I >= 0; --I)
     k_zgemv<true><<<gv, 256, 0, st>>>(bs, ctx->eF + blk * I, g + (size_t)(I + 1) * bs, g + (size_t)I * bs,
-                                      g + (size_t)I * bs);
+                                      g + (size_t)I * bs); iga_count_launch();
   CK(cudaMemcpyAsync(s, g, sizeof(double2) * m, cudaMemcpyDeviceToDevice, st));
   CKL();
   return IGA_OK;

@@ -204,8 +204,8 @@ static int red_blocks(iga_ctx* ctx) { return 2 * ctx->num_sms; }
 
 iga_status vec_norm(iga_ctx* ctx, const double2* x, size_t n, double* dev_out) {
   int nb = red_blocks(ctx);
-  k_norm2_part<<<nb, IGA_RED_THREADS, 0, ctx->st>>>(x, n, ctx->partials);
-  k_finish_norm<<<1, IGA_RED_THREADS, 0, ctx->st>>>(ctx->partials, nb, dev_out);
+  k_norm2_part<<<nb, IGA_RED_THREADS, 0, ctx->st>>>(x, n, ctx->partials); iga_count_launch();
+  k_finish_norm<<<1, IGA_RED_THREADS, 0, ctx->st>>>(ctx->partials, nb, dev_out); iga_count_launch();
   CKL();
   return IGA_OK;
 }
@@ -220,10 +220,10 @@ iga_status kry_mgs(iga_ctx* ctx, const double2* V, size_t ldv, int j, double2* w
   for (int i = 0; i <= j + 1; ++i) {
     const double* pin = (i & 1) ? pa : pb;
     double* pout = (i & 1) ? pb : pa;
-    k_mgs_step<<<nb, IGA_RED_THREADS, 0, ctx->st>>>(V, ldv, n, i, j, w, pin, pout, h);
+    k_mgs_step<<<nb, IGA_RED_THREADS, 0, ctx->st>>>(V, ldv, n, i, j, w, pin, pout, h); iga_count_launch();
   }
   const double* plast = ((j + 1) & 1) ? pb : pa;
-  k_finish_h<<<1, IGA_RED_THREADS, 0, ctx->st>>>(plast, nb, h + j + 1);
+  k_finish_h<<<1, IGA_RED_THREADS, 0, ctx->st>>>(plast, nb, h + j + 1); iga_count_launch();
   CKL();
   return IGA_OK;
 }
@@ -284,8 +284,8 @@ iga_status kry_solve(iga_ctx* ctx, const double2* f, double2* x, double tol, int
     TRY(defl_apply(ctx, f, ctx->w0));                 // b = M~^{-1} P f
     TRY(precond(ctx, ctx->w0, V));
   }
-  k_norm2_part<<<nb, IGA_RED_THREADS, 0, st>>>(V, n, ctx->partials);
-  k_init_v0<<<nb, IGA_RED_THREADS, 0, st>>>(V, n, ctx->partials, gs);
+  k_norm2_part<<<nb, IGA_RED_THREADS, 0, st>>>(V, n, ctx->partials); iga_count_launch();
+  k_init_v0<<<nb, IGA_RED_THREADS, 0, st>>>(V, n, ctx->partials, gs); iga_count_launch();
   CKL();
   int hflag[2] = {0, 0};
   CK(cudaMemcpyAsync(hflag, gs.flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -312,10 +312,10 @@ iga_status kry_solve(iga_ctx* ctx, const double2* f, double2* x, double tol, int
     for (int i = 0; i <= j + 1; ++i) {
       const double* pin = (i & 1) ? pa : pb;
       double* pout = (i & 1) ? pb : pa;
-      k_mgs_step<<<nb, IGA_RED_THREADS, 0, st>>>(V, ldv, n, i, j, w, pin, pout, Hj);
+      k_mgs_step<<<nb, IGA_RED_THREADS, 0, st>>>(V, ldv, n, i, j, w, pin, pout, Hj); iga_count_launch();
     }
     const double* plast = ((j + 1) & 1) ? pb : pa;
-    k_normalize_givens<<<nb, IGA_RED_THREADS, 0, st>>>(w, n, plast, Hj, j, gs, 1);
+    k_normalize_givens<<<nb, IGA_RED_THREADS, 0, st>>>(w, n, plast, Hj, j, gs, 1); iga_count_launch();
     CKL();
     CK(cudaMemcpyAsync(hflag, gs.flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -326,15 +326,15 @@ iga_status kry_solve(iga_ctx* ctx, const double2* f, double2* x, double tol, int
   if (hist) CK(cudaMemcpyAsync(hist, gs.hist, sizeof(double) * (jdone + 1), cudaMemcpyDeviceToHost, st));
   // y = R^{-1} g ; x^ = V y (or Z y)
   if (jdone > 0) {
-    k_backsolve<<<1, 1, 0, st>>>(ctx->H, ldh, gs.g, ctx->gy, jdone);
-    k_combine<<<cdiv(n, 256), 256, 0, st>>>(flex ? ctx->Zb : V, ldv, n, ctx->gy, jdone, ctx->w0);
+    k_backsolve<<<1, 1, 0, st>>>(ctx->H, ldh, gs.g, ctx->gy, jdone); iga_count_launch();
+    k_combine<<<cdiv(n, 256), 256, 0, st>>>(flex ? ctx->Zb : V, ldv, n, ctx->gy, jdone, ctx->w0); iga_count_launch();
   } else {
     CK(cudaMemsetAsync(ctx->w0, 0, sizeof(double2) * n, st));
   }
   // u = x^ + Q (f - A x^)
   TRY(op_apply<double>(ctx, 0, OP_A, ctx->w0, ctx->w1, f, EPI_ZMINUS, nullptr, 0.0));
   TRY(defl_q(ctx, ctx->w1, ctx->w2));
-  k_add<<<cdiv(n, 256), 256, 0, st>>>(ctx->w0, ctx->w2, x, n);
+  k_add<<<cdiv(n, 256), 256, 0, st>>>(ctx->w0, ctx->w2, x, n); iga_count_launch();
   CKL();
   if (true_res) {
     TRY(op_apply<double>(ctx, 0, OP_A, x, ctx->w1, f, EPI_ZMINUS, nullptr, 0.0));

@@ -185,10 +185,10 @@ __global__ void k_axpy1(C* y, const C* x, size_t n) {   // y += x
 }
 
 void launch_convert_d2f(const double2* a, float2* b, size_t n, cudaStream_t st) {
-  k_c2f<<<cdiv(n, 256), 256, 0, st>>>(a, b, n);
+  k_c2f<<<cdiv(n, 256), 256, 0, st>>>(a, b, n); iga_count_launch();
 }
 void launch_convert_f2d(const float2* a, double2* b, size_t n, cudaStream_t st) {
-  k_f2d<<<cdiv(n, 256), 256, 0, st>>>(a, b, n);
+  k_f2d<<<cdiv(n, 256), 256, 0, st>>>(a, b, n); iga_count_launch();
 }
 
 // ------------------------------------------------------------------ host
@@ -205,15 +205,15 @@ iga_status setup_coarse_inverse(iga_ctx* ctx) {
   int* info = dalloc<int>(ctx, 1);
   if (!cols || !A || !e || !ctx->cinv || !ctx->cinvf || !info) return set_err(ctx, IGA_E_OOM, "coarse alloc");
   for (int j = 0; j < n; ++j) {
-    k_unit<<<cdiv(n, 128), 128, 0, ctx->st>>>(e, n, j);
+    k_unit<<<cdiv(n, 128), 128, 0, ctx->st>>>(e, n, j); iga_count_launch();
     TRY(op_apply<double>(ctx, l, OP_MB, e, cols + (size_t)j * n, nullptr, EPI_Y, nullptr, 0.0));
   }
-  k_transpose_c<<<cdiv((size_t)n * n, 256), 256, 0, ctx->st>>>(cols, A, n);
-  k_eye<<<cdiv((size_t)n * n, 256), 256, 0, ctx->st>>>(ctx->cinv, n);
+  k_transpose_c<<<cdiv((size_t)n * n, 256), 256, 0, ctx->st>>>(cols, A, n); iga_count_launch();
+  k_eye<<<cdiv((size_t)n * n, 256), 256, 0, ctx->st>>>(ctx->cinv, n); iga_count_launch();
   CK(cudaMemsetAsync(info, 0, sizeof(int), ctx->st));
-  k_gauss_jordan<<<1, 256, n * sizeof(double2), ctx->st>>>(A, ctx->cinv, n, info);
+  k_gauss_jordan<<<1, 256, n * sizeof(double2), ctx->st>>>(A, ctx->cinv, n, info); iga_count_launch();
   CKL();
-  k_c2f<<<cdiv((size_t)n * n, 256), 256, 0, ctx->st>>>(ctx->cinv, ctx->cinvf, (size_t)n * n);
+  k_c2f<<<cdiv((size_t)n * n, 256), 256, 0, ctx->st>>>(ctx->cinv, ctx->cinvf, (size_t)n * n); iga_count_launch();
   int hinfo = 0;
   CK(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
@@ -255,7 +255,7 @@ iga_status mg_jacobi0(iga_ctx* ctx, int l, const typename cplx<T>::t* b, typenam
   if (!ctx->vark) cm = ctx->k2const * cm;
   const C* dinv = (ctx->vark && ctx->dim == 2) ? LvBuf<T>::dinv(L) : nullptr;
   k_jacobi0<T><<<cdiv(L.n, 256), 256, 0, ctx->st>>>(L.nx, L.ny, ctx->p, LvBuf<T>::K(L), LvBuf<T>::M(L),
-                                                    cconv<C>(cm), dinv, b, x, (T)ctx->prm.omega);
+                                                    cconv<C>(cm), dinv, b, x, (T)ctx->prm.omega); iga_count_launch();
   CKL();
   return IGA_OK;
 }
@@ -264,7 +264,7 @@ template <typename T>
 iga_status mg_restrict(iga_ctx* ctx, int l, const typename cplx<T>::t* f, typename cplx<T>::t* c) {
   LevelData& F = ctx->lv[l];
   LevelData& Cc = ctx->lv[l + 1];
-  k_restrict<T><<<cdiv(Cc.n, 256), 256, 0, ctx->st>>>(F.nx, F.ny, Cc.nx, Cc.ny, F.wR, LvBuf<T>::Rw(F), F.Rlo, f, c);
+  k_restrict<T><<<cdiv(Cc.n, 256), 256, 0, ctx->st>>>(F.nx, F.ny, Cc.nx, Cc.ny, F.wR, LvBuf<T>::Rw(F), F.Rlo, f, c); iga_count_launch();
   CKL();
   return IGA_OK;
 }
@@ -273,7 +273,7 @@ template <typename T>
 iga_status mg_prolong_add(iga_ctx* ctx, int l, const typename cplx<T>::t* c, typename cplx<T>::t* f) {
   LevelData& F = ctx->lv[l];
   LevelData& Cc = ctx->lv[l + 1];
-  k_prolong_add<T><<<cdiv(F.n, 256), 256, 0, ctx->st>>>(F.nx, F.ny, Cc.nx, Cc.ny, F.wP, LvBuf<T>::Pw(F), F.Plo, c, f);
+  k_prolong_add<T><<<cdiv(F.n, 256), 256, 0, ctx->st>>>(F.nx, F.ny, Cc.nx, Cc.ny, F.wP, LvBuf<T>::Pw(F), F.Plo, c, f); iga_count_launch();
   CKL();
   return IGA_OK;
 }
@@ -281,7 +281,7 @@ iga_status mg_prolong_add(iga_ctx* ctx, int l, const typename cplx<T>::t* c, typ
 template <typename T>
 iga_status mg_coarse(iga_ctx* ctx, const typename cplx<T>::t* b, typename cplx<T>::t* x) {
   using C = typename cplx<T>::t;
-  k_dense_mv<C><<<1, 256, 0, ctx->st>>>(ctx->nc, LvBuf<T>::cinv(ctx), b, x);
+  k_dense_mv<C><<<1, 256, 0, ctx->st>>>(ctx->nc, LvBuf<T>::cinv(ctx), b, x); iga_count_launch();
   CKL();
   return IGA_OK;
 }
@@ -340,7 +340,7 @@ iga_status mg_vcycle(iga_ctx* ctx, const typename cplx<T>::t* r, typename cplx<T
     C* e = LvBuf<T>::x(L);
     TRY(op_apply<T>(ctx, 0, OP_MB, z, res, r, EPI_ZMINUS, nullptr, 0.0));
     TRY(vcycle_level<T>(ctx, 0, res, e, LvBuf<T>::y(L)));
-    k_axpy1<C><<<cdiv(L.n, 256), 256, 0, ctx->st>>>(z, e, L.n);
+    k_axpy1<C><<<cdiv(L.n, 256), 256, 0, ctx->st>>>(z, e, L.n); iga_count_launch();
     CKL();
   }
   return IGA_OK;

@@ -345,7 +345,7 @@ template <int P, typename T, int EPI>
 static void launch_op(iga_ctx* ctx, const OpArgs<T>& a, int level) {
   cudaStream_t st = ctx->st;
   if (ctx->dim == 1) {
-    k_kron1d<P, T, EPI><<<cdiv(a.nx, 256), 256, 0, st>>>(a);
+    k_kron1d<P, T, EPI><<<cdiv(a.nx, 256), 256, 0, st>>>(a); iga_count_launch();
   } else if (!ctx->vark) {
     constexpr size_t sm = kron2d_smem<P, T>();
     static bool attr = false;
@@ -354,7 +354,7 @@ static void launch_op(iga_ctx* ctx, const OpArgs<T>& a, int level) {
       attr = true;
     }
     dim3 grid(cdiv(a.nx, KR_TX), cdiv(a.ny, KR_TY));
-    k_kron2d<P, T, EPI><<<grid, 256, sm, st>>>(a);
+    k_kron2d<P, T, EPI><<<grid, 256, sm, st>>>(a); iga_count_launch();
   } else {
     constexpr size_t sm = elem2d_smem<P, T>();
     static bool attr = false;
@@ -372,7 +372,7 @@ static void launch_op(iga_ctx* ctx, const OpArgs<T>& a, int level) {
         for (int c = 0; c < 3; ++c) kf.lines[l][c] = (float)ctx->kf.lines[l][c];
       for (int l = 0; l <= IGA_MAX_LINES; ++l) kf.k2[l] = (float)ctx->kf.k2[l];
     }
-    k_elem2d<P, T, EPI><<<grid, 256, sm, st>>>(a, kf);
+    k_elem2d<P, T, EPI><<<grid, 256, sm, st>>>(a, kf); iga_count_launch();
   }
   (void)level;
 }
@@ -436,7 +436,7 @@ iga_status setup_vark_diag(iga_ctx* ctx, int level) {
   if (!L.dinv || !L.dinvf) return set_err(ctx, IGA_E_OOM, "dinv");
   double2 c = make_double2(-ctx->sig.x, -ctx->sig.y);
   k_vark_diag<<<cdiv(L.n, 128), 128, 0, ctx->st>>>(L.nx, L.n_el, ctx->p, L.K, L.M, L.B, L.wq, L.xq, ctx->kf, c,
-                                                   L.dinv, L.dinvf);
+                                                   L.dinv, L.dinvf); iga_count_launch();
   CKL();
   return IGA_OK;
 }

@@ -168,7 +168,7 @@ __global__ void k_d2f(const double* a, float* b, size_t n) {
 static iga_status to_float(iga_ctx* ctx, const double* a, float** out, size_t n) {
   *out = dalloc<float>(ctx, n);
   if (!*out) return set_err(ctx, IGA_E_OOM, "alloc");
-  k_d2f<<<cdiv(n, 256), 256, 0, ctx->st>>>(a, *out, n);
+  k_d2f<<<cdiv(n, 256), 256, 0, ctx->st>>>(a, *out, n); iga_count_launch();
   CKL();
   return IGA_OK;
 }
@@ -198,11 +198,11 @@ iga_status setup_levels(iga_ctx* ctx) {
     L.K = dalloc<double>(ctx, (size_t)L.nx * W);
     L.M = dalloc<double>(ctx, (size_t)L.nx * W);
     if (!L.knots || !L.xq || !L.wq || !L.B || !L.D || !L.K || !L.M) return set_err(ctx, IGA_E_OOM, "level alloc");
-    k_knots<<<cdiv(tl, 128), 128, 0, ctx->st>>>(L.knots, L.n_el, p);
+    k_knots<<<cdiv(tl, 128), 128, 0, ctx->st>>>(L.knots, L.n_el, p); iga_count_launch();
     CKL();
-    k_tables<<<cdiv(L.n_el * Q, 128), 128, 0, ctx->st>>>(L.knots, L.n_el, p, L.xq, L.wq, L.B, L.D);
+    k_tables<<<cdiv(L.n_el * Q, 128), 128, 0, ctx->st>>>(L.knots, L.n_el, p, L.xq, L.wq, L.B, L.D); iga_count_launch();
     CKL();
-    k_bands<<<cdiv(L.nx * W, 128), 128, 0, ctx->st>>>(L.n_el, p, L.nx, L.wq, L.B, L.D, L.K, L.M);
+    k_bands<<<cdiv(L.nx * W, 128), 128, 0, ctx->st>>>(L.n_el, p, L.nx, L.wq, L.B, L.D, L.K, L.M); iga_count_launch();
     CKL();
     TRY(to_float(ctx, L.K, &L.Kf, (size_t)L.nx * W));
     TRY(to_float(ctx, L.M, &L.Mf, (size_t)L.nx * W));
@@ -223,9 +223,9 @@ iga_status setup_levels(iga_ctx* ctx) {
     F.Rw = dalloc<double>(ctx, (size_t)C.nx * F.wR);
     F.Rlo = dalloc<int>(ctx, C.nx);
     if (!F.Pw || !F.Plo || !F.Rw || !F.Rlo) return set_err(ctx, IGA_E_OOM, "transfer alloc");
-    k_prolong_rows<<<cdiv(F.nx, 128), 128, 0, ctx->st>>>(C.knots, F.knots, p, nbc, nbf, F.wP, F.Pw, F.Plo, err);
+    k_prolong_rows<<<cdiv(F.nx, 128), 128, 0, ctx->st>>>(C.knots, F.knots, p, nbc, nbf, F.wP, F.Pw, F.Plo, err); iga_count_launch();
     CKL();
-    k_restrict_rows<<<cdiv(C.nx, 128), 128, 0, ctx->st>>>(C.knots, F.knots, p, nbc, nbf, F.wR, F.Rw, F.Rlo, err);
+    k_restrict_rows<<<cdiv(C.nx, 128), 128, 0, ctx->st>>>(C.knots, F.knots, p, nbc, nbf, F.wR, F.Rw, F.Rlo, err); iga_count_launch();
     CKL();
     TRY(to_float(ctx, F.Pw, &F.Pwf, (size_t)F.nx * F.wP));
     TRY(to_float(ctx, F.Rw, &F.Rwf, (size_t)C.nx * F.wR));

@@ -1,0 +1,43 @@
+"""Small, self-contained launch sequences for Nsight Compute captures.
+
+    python -m paper_2010_10232_gb300.profile_cases apply   # FP64 constant-k apply, bench size
+    python -m paper_2010_10232_gb300.profile_cases apply32 # FP32 M_beta Jacobi sweep, 4097^2 dofs
+    python -m paper_2010_10232_gb300.profile_cases solve   # one bench solve
+
+Each case launches a handful of kernels on inputs of the bench problem so a
+capture (-k <kernel> -c <count>) ends in seconds.
+"""
+from __future__ import annotations
+
+import sys
+
+import torch
+
+from .solver import Helmholtz
+
+
+def main(case: str) -> None:
+    torch.cuda.set_device(0)
+    if case == "apply":
+        h = Helmholtz(dim=2, p=3, n_el=320, kfield=200.0, skip_deflation=1)
+        x = torch.randn(h.n, dtype=torch.complex128, device="cuda")
+        y = h.vec()
+        for _ in range(4):
+            h.apply_A(x, y)
+    elif case == "apply32":
+        h = Helmholtz(dim=2, p=3, n_el=4096, kfield=2560.0, skip_deflation=1, precision=1)
+        x = torch.randn(h.n, dtype=torch.complex128, device="cuda")
+        z = h.vec()
+        h.vcycle(x, z)
+    elif case == "solve":
+        h = Helmholtz(dim=2, p=3, n_el=320, kfield=200.0)
+        f = h.point_source(0.5, 0.5)
+        h.solve(f)
+    else:
+        raise SystemExit(f"unknown case {case}")
+    torch.cuda.synchronize()
+    print("ok", case)
+
+
+if __name__ == "__main__":
+    main(sys.argv[1] if len(sys.argv) > 1 else "apply")

@@ -352,11 +352,25 @@ def test_full_size_apply_sampled(cfg2_full):
 
 
 def test_full_size_solve(cfg2_full):
+    """At 320 x 320, k = 200 the coarse matrix E is nearly singular
+    (min |lambda_i + lambda_j - k^2| = 0.022, cond ~ 2e7) and the 1e-7 GMRES
+    answer is only determined to ~1e-6 by its data: a 1e-15 relative
+    perturbation of f moves the oracle's own result by ~2e-6.  So the full-size
+    check is: same iteration count (+-1) and a GPU-oracle gap no larger than
+    ten times that measured self-sensitivity; the strict 1e-10 bar applies to
+    the smaller cases above, where the problem is well conditioned."""
     h, s, pr = cfg2_full
     f = s.load()
     x, it, hist, tr, st = h.solve(to_t(f))
     r = s.solve(f)
-    print(f"cfg2 k=200 p=3: iters gpu={it} oracle={r.iters} true_res={tr:.2e}")
+    f2 = f * (1 + 1e-15 * W.seeded_normal_rhs(len(f), 9))
+    r2 = s.solve(f2)
+    self_sens = rel_err(r2.u, r.u)
+    gap = rel_err(to_n(x), r.u)
+    ud = s.direct(f)
+    print(f"cfg2 k=200 p=3: iters gpu={it} oracle={r.iters} true_res={tr:.2e} gap={gap:.2e} "
+          f"oracle_self_sensitivity={self_sens:.2e} err_vs_direct gpu={rel_err(to_n(x), ud):.2e} "
+          f"oracle={rel_err(r.u, ud):.2e}")
     assert st == 0 and abs(it - r.iters) <= 1
-    if it == r.iters:
-        assert rel_err(to_n(x), r.u) <= 1e-10
+    assert gap <= max(1e-10, 10 * self_sens)
+    assert rel_err(to_n(x), ud) <= 2 * rel_err(r.u, ud) + 1e-9

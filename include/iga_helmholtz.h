@@ -178,6 +178,30 @@ iga_status iga_solve(iga_ctx* ctx, const iga_c128* rhs, iga_c128* x, double tol,
 iga_status iga_solve_host(iga_ctx* ctx, const iga_c128* rhs_host, iga_c128* x_host, double tol,
                           int maxit, int* iters, double* res_hist, double* true_res);
 
+/* Allocation-free variant of iga_mgs, for callers that cannot call cudaMalloc
+   (for example code inside a framework whose caching allocator owns the device
+   memory, or a latency-critical loop that must not pay cudaMalloc's implicit
+   device synchronisation).  The paper has no counterpart: it is a property of
+   this library, not of the method.
+   Same sweep as iga_mgs, without a context: for i = 0..j, h[i] = v_i^H w,
+   w -= h[i] v_i; then h[j+1] = ||w||.  V (column i at V + i*ldv, n entries),
+   w (n, updated in place) and h (j+2 entries) are DEVICE pointers owned by the
+   caller, 16-byte aligned; work is enqueued on `stream`.
+   Scratch: the per-block partial sums live in one file-scope device array of
+   32 KiB (4096 doubles, enough for 1024 reduction blocks; the sweep uses two
+   blocks per SM).  Every GPU that loads the library holds that array until the
+   process exits.  The function allocates nothing and calls no allocating
+   library routine.  The first call on a device looks up the array's device
+   address (cudaGetSymbolAddress) with that device current; make that first
+   call before any stream capture.  All calls share the one array and it keeps
+   the last call's contents (every entry is written before it is read), so two
+   calls whose work overlaps on the GPU race: order them on one stream.
+   Errors: IGA_E_INVALID for NULL/misaligned pointers, n = 0, ldv < n, j < 0,
+   or a device whose reduction grid would exceed the 1024-block scratch;
+   IGA_E_CUDA if the symbol lookup or a launch fails. */
+iga_status iga_mgs_noalloc(const iga_c128* V, size_t ldv, size_t n, int j, iga_c128* w, iga_c128* h,
+                           void* stream);
+
 /* Measurement helper (no counterpart in the paper): launches 8 independent
    FMA chains per thread on 8 x SM-count blocks of 256 threads, in FP64
    (precision 0) or FP32 (1), on `stream`; *flops (HOST) receives the flop count

@@ -50,6 +50,7 @@ _SIG = {
     "iga_level_nel": (C.c_int, [_VP, C.c_int]),
     "iga_status_str": (C.c_char_p, [C.c_int]),
     "iga_launch_count": (C.c_ulonglong, []),
+    "iga_mgs_noalloc": (C.c_int, [_VP, C.c_size_t, C.c_size_t, C.c_int, _VP, _VP, _VP]),
     "iga_probe_fma": (C.c_int, [C.c_int, C.c_int, _VP, _VP, C.POINTER(C.c_double)]),
     "iga_last_error": (C.c_char_p, [_VP]),
     "iga_get_knots": (C.c_int, [_VP, C.c_int, _VP, C.c_int]),

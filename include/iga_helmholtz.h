@@ -72,6 +72,9 @@ typedef struct {
                               implies it)                                                 */
   int skip_deflation;      /* 1: operator / V-cycle context only (no Z, E); deflation and
                               solve entry points then return IGA_E_INVALID                 */
+  int host_loop;           /* 0 (default): the GMRES loop runs on the device as a CUDA
+                              graph with a WHILE conditional node; 1: the host launches
+                              each iteration and reads the convergence flag (profiling)   */
   void* stream;            /* cudaStream_t for all work of this context                   */
 } iga_params;
 

@@ -10,6 +10,7 @@
 static bool aligned16(const void* p) { return p && (((uintptr_t)p) & 15u) == 0; }
 static std::atomic<unsigned long long> g_launches{0};
 void iga_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void iga_add_launches(long long n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
 
 extern "C" {
 
@@ -31,6 +32,7 @@ void iga_default_params(iga_params* prm) {
   d.precision = 0;
   d.flexible = 0;
   d.skip_deflation = 0;
+  d.host_loop = 0;
   d.stream = nullptr;
   *prm = d;
 }
@@ -97,6 +99,7 @@ iga_status iga_setup(const iga_params* prm, iga_ctx** out) {
   for (int l = 0; l <= IGA_MAX_LINES; ++l) ctx->kf.k2[l] = l <= P.n_lines ? P.k_values[l] * P.k_values[l] : 0.0;
   ctx->k2const = P.k_values[0] * P.k_values[0];
   ctx->sig = make_double2(P.beta1, -P.beta2);
+  ctx->use_graph = P.host_loop == 0;
   iga_status s = IGA_OK;
   do {
     if (cudaGetDevice(&ctx->device) != cudaSuccess) { s = set_err(ctx, IGA_E_CUDA, "no CUDA device"); break; }
@@ -135,6 +138,9 @@ iga_status iga_setup(const iga_params* prm, iga_ctx** out) {
 void iga_destroy(iga_ctx* ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->st);
+  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+  if (ctx->graph) cudaGraphDestroy(ctx->graph);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   delete ctx;
 }
 

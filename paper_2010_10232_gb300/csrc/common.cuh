@@ -122,6 +122,7 @@ struct iga_ctx {
   double2* cw = nullptr;
   double2* ce1 = nullptr;            // refinement residual / correction
   double2* ce2 = nullptr;
+  int e_refine = 1;                  // iterative refinement steps of the FDM solve (0 or 1)
   // variable-k E (block tridiagonal, banded in y): see deflation.cu
   int eblk = 0, enb = 0, els = 0;   // block size (lines per block * mx), number of blocks, lines
   double2* eDinv = nullptr;          // [enb][bs][bs] inverse diagonal blocks D_I^{-1}
@@ -148,6 +149,19 @@ struct iga_ctx {
   double2* gy = nullptr;             // y[maxit]
   int* gflag = nullptr;              // [0] converged, [1] nonfinite, [2] breakdown
   int* hflag = nullptr;              // pinned host copy
+  // device-resident iteration (CUDA graph with a WHILE conditional node)
+  double2* kvec = nullptr;           // vcur, zcur, wnext (3 n)
+  int* kint = nullptr;               // [0] j, [1] barrier timeout
+  unsigned* kbar = nullptr;          // grid barrier state
+  int coop_blocks = 0;
+  bool use_graph = true;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  cudaGraphConditionalHandle gcond = 0;
+  bool graph_flex = false;
+  int graph_maxit = 0;
+  unsigned long long body_kernels = 0;
   double* hres = nullptr;            // pinned host copy of residual
   DevBuf bufs;
   std::string err;
@@ -160,6 +174,7 @@ struct iga_ctx {
 // Every kernel launch site calls this once per launch (process-wide counter,
 // read with iga_launch_count()).
 void iga_count_launch();
+void iga_add_launches(long long n);
 iga_status set_err(iga_ctx* c, iga_status s, const char* fmt, ...);
 template <typename T> inline T* dalloc(iga_ctx* c, size_t count) {
   void* p = nullptr;

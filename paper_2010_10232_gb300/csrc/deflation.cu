@@ -316,36 +316,52 @@ __global__ void k_axpy_c(double2* y, const double2* x, size_t n) {
 // R real m x m (row-major), X complex rows x cols.  TRANS: op(R) = R^T.
 // With DIVIDE the result is divided by lam_y[i] + lam_x[j] - k2 (lam_y = 0 in 1D).
 template <bool LEFT, bool TRANS, bool DIVIDE>
-__global__ void k_fdm_gemm(const double* R, const double2* X, double2* out, int rows, int cols,
-                           const double* lam_y, const double* lam_x, double k2) {
-  constexpr int TS = 16;
-  __shared__ double Rs[TS][TS + 1];
-  __shared__ double2 Xs[TS][TS + 1];
-  int ty = threadIdx.y, tx = threadIdx.x;
-  int i = blockIdx.y * TS + ty, j = blockIdx.x * TS + tx;
+__global__ void __launch_bounds__(128) k_fdm_gemm(const double* R, const double2* X, double2* out, int rows, int cols,
+                                                 const double* lam_y, const double* lam_x, double k2) {
+  // 8 x 16 output tile per block of 8 x 16 threads; K in steps of 16.
+  constexpr int TY = 8, TX = 16, TK = 16;
+  __shared__ double Rs[TK][TK + 1];
+  __shared__ double2 Xs[TK][TX + 1];
+  int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  int i = blockIdx.y * TY + ty, j = blockIdx.x * TX + tx;
   int K = LEFT ? rows : cols;
   double2 acc = make_double2(0.0, 0.0);
-  for (int k0 = 0; k0 < K; k0 += TS) {
+  for (int k0 = 0; k0 < K; k0 += TK) {
     if (LEFT) {
-      int ri = blockIdx.y * TS + ty, rk = k0 + tx;   // op(R)[ri][rk]
-      double v = 0.0;
-      if (ri < rows && rk < K) v = TRANS ? R[(size_t)rk * rows + ri] : R[(size_t)ri * rows + rk];
-      Rs[ty][tx] = v;
-      int xk = k0 + ty, xj = blockIdx.x * TS + tx;
-      Xs[ty][tx] = (xk < K && xj < cols) ? X[(size_t)xk * cols + xj] : make_double2(0.0, 0.0);
+      // Rs[r][kk] = op(R)[blockIdx.y*TY + r][k0 + kk] for r < TY
+      for (int t = threadIdx.x; t < TY * TK; t += 128) {
+        int r = t / TK, kk = t - r * TK;
+        int ri = blockIdx.y * TY + r, rk = k0 + kk;
+        double v = 0.0;
+        if (ri < rows && rk < K) v = TRANS ? R[(size_t)rk * rows + ri] : R[(size_t)ri * rows + rk];
+        Rs[r][kk] = v;
+      }
+      // Xs[kk][c] = X[k0 + kk][blockIdx.x*TX + c]
+      for (int t = threadIdx.x; t < TK * TX; t += 128) {
+        int kk = t / TX, c = t - kk * TX;
+        int xk = k0 + kk, xj = blockIdx.x * TX + c;
+        Xs[kk][c] = (xk < K && xj < cols) ? X[(size_t)xk * cols + xj] : make_double2(0.0, 0.0);
+      }
       __syncthreads();
 #pragma unroll
-      for (int kk = 0; kk < TS; ++kk) acc = cfma(Rs[ty][kk], Xs[kk][tx], acc);
+      for (int kk = 0; kk < TK; ++kk) acc = cfma(Rs[ty][kk], Xs[kk][tx], acc);
     } else {
-      int xi = blockIdx.y * TS + ty, xk = k0 + tx;
-      Xs[ty][tx] = (xi < rows && xk < K) ? X[(size_t)xi * cols + xk] : make_double2(0.0, 0.0);
-      int rk = k0 + ty, rj = blockIdx.x * TS + tx;   // op(R)[rk][rj]
-      double v = 0.0;
-      if (rk < K && rj < cols) v = TRANS ? R[(size_t)rj * cols + rk] : R[(size_t)rk * cols + rj];
-      Rs[ty][tx] = v;
+      // Xs[r][kk] = X[blockIdx.y*TY + r][k0 + kk] for r < TY ; Rs[kk][c] = op(R)[k0 + kk][blockIdx.x*TX + c]
+      for (int t = threadIdx.x; t < TY * TK; t += 128) {
+        int r = t / TK, kk = t - r * TK;
+        int xi = blockIdx.y * TY + r, xk = k0 + kk;
+        Xs[r][kk] = (xi < rows && xk < K) ? X[(size_t)xi * cols + xk] : make_double2(0.0, 0.0);
+      }
+      for (int t = threadIdx.x; t < TK * TX; t += 128) {
+        int kk = t / TX, c = t - kk * TX;
+        int rk = k0 + kk, rj = blockIdx.x * TX + c;
+        double v = 0.0;
+        if (rk < K && rj < cols) v = TRANS ? R[(size_t)rj * cols + rk] : R[(size_t)rk * cols + rj];
+        Rs[kk][c] = v;
+      }
       __syncthreads();
 #pragma unroll
-      for (int kk = 0; kk < TS; ++kk) acc = cfma(Rs[kk][tx], Xs[ty][kk], acc);
+      for (int kk = 0; kk < TK; ++kk) acc = cfma(Rs[kk][tx], Xs[ty][kk], acc);
     }
     __syncthreads();
   }
@@ -463,7 +479,7 @@ iga_status defl_z(iga_ctx* ctx, const double2* c, double2* x) {
 static iga_status fdm_solve(iga_ctx* ctx, const double2* t, double2* s) {
   const int mx = ctx->mx;
   const double k2 = ctx->k2const;
-  dim3 blk(16, 16);
+  dim3 blk(128);
   if (ctx->dim == 1) {
     // s = V ((V^T t) / (lambda - k^2)) with t as a 1 x m row: (t V) / d, then (.) V^T
     dim3 g(cdiv(mx, 16), 1);
@@ -472,7 +488,7 @@ static iga_status fdm_solve(iga_ctx* ctx, const double2* t, double2* s) {
     CKL();
     return IGA_OK;
   }
-  dim3 g(cdiv(mx, 16), cdiv(mx, 16));
+  dim3 g(cdiv(mx, 16), cdiv(mx, 8));
   // T1 = V^T T ; T2 = (T1 V) / D ; T3 = V T2 ; S = T3 V^T
   k_fdm_gemm<true, true, false><<<g, blk, 0, ctx->st>>>(ctx->fdmV, t, ctx->cw, mx, mx, nullptr, nullptr, 0.0); iga_count_launch();
   k_fdm_gemm<false, false, true><<<g, blk, 0, ctx->st>>>(ctx->fdmV, ctx->cw, s, mx, mx, ctx->fdmL, ctx->fdmL, k2); iga_count_launch();
@@ -482,12 +498,14 @@ static iga_status fdm_solve(iga_ctx* ctx, const double2* t, double2* s) {
   return IGA_OK;
 }
 
-// s = E^{-1} t.  Constant k: fast diagonalisation plus one step of iterative
-// refinement with the exact banded E (the coarse problem can be nearly
-// singular when lambda_i + lambda_j ~ k^2).  Variable k: block LU.
+// s = E^{-1} t.  Constant k: fast diagonalisation with Rayleigh-quotient
+// eigenvalues (about 1e-9 relative even where lambda_i + lambda_j ~ k^2 nearly
+// cancels); with refine = 1 one step of iterative refinement with the exact
+// banded E follows.  Variable k: block LU.
 iga_status defl_esolve(iga_ctx* ctx, const double2* t, double2* s) {
   if (ctx->vark) return block_E_solve(ctx, t, s);
   TRY(fdm_solve(ctx, t, s));
+  if (!ctx->e_refine) return IGA_OK;
   const int my = ctx->dim == 2 ? ctx->mx : 1;
   k_e_residual<<<cdiv(ctx->m, 256), 256, 0, ctx->st>>>(ctx->kc, ctx->mc, ctx->mx, my, (ctx->p + 4) / 2 + 1,
                                                        ctx->k2const, s, t, ctx->ce1); iga_count_launch();

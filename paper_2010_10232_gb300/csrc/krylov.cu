@@ -199,6 +199,128 @@ __global__ void k_add(const double2* a, const double2* b, double2* out, size_t n
   if (e < n) out[e] = a[e] + b[e];
 }
 
+// ------------------------------------------------------------------ device-resident iteration
+// Bounded grid barrier for a cooperative launch (all blocks co-resident).  A
+// barrier that waits longer than ~1 s sets *err and every block returns; the
+// host reports IGA_E_TIMEOUT.
+__device__ __forceinline__ bool grid_sync(unsigned* bar, unsigned nb, int* err) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = bar + 1;
+    volatile int* verr = err;
+    unsigned g = *vgen;
+    __threadfence();
+    unsigned arrived = atomicAdd(bar, 1u);
+    ok = 1;
+    if (arrived == nb - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      unsigned long long spins = 0;
+      while (*vgen == g) {
+        if (*verr || ++spins > (1ull << 24)) { atomicExch(err, 1); ok = 0; break; }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+struct ArnoldiArgs {
+  double2* V;          // basis, column i at V + i*ldv
+  size_t ldv, n;
+  double2* w;          // candidate vector; orthogonalised in place
+  double2* vcur;       // receives v_{j+1} (input of the next iteration)
+  double2* H;          // (maxit+1) x maxit, column-major, leading dimension ldh
+  int ldh, maxit;
+  GState gs;
+  int* jptr;           // current column j, advanced by this kernel
+  double* part;        // 2 x gridDim.x (re, im) partial sums
+  unsigned* bar;       // grid barrier {count, generation}
+  int* err;            // barrier timeout flag
+  cudaGraphConditionalHandle cond;
+  int use_cond;
+};
+
+// One Arnoldi step of column j = *jptr in a single cooperative launch:
+// modified Gram-Schmidt (i = 0..j: h_ij = v_i^H w, w -= h_ij v_i, one grid
+// barrier per coefficient), h_{j+1,j} = ||w||, v_{j+1} = w / h_{j+1,j}, the
+// Givens update of column j, j <- j + 1 and the loop condition.
+__global__ void __launch_bounds__(256) k_arnoldi_coop(ArnoldiArgs a) {
+  const int j = *a.jptr;
+  const unsigned nb = gridDim.x;
+  double2* hcol = a.H + (size_t)j * a.ldh;
+  double2 hp = make_double2(0.0, 0.0);
+  for (int i = 0; i <= j + 1; ++i) {
+    const double2* vprev = a.V + (size_t)(i > 0 ? i - 1 : 0) * a.ldv;
+    const double2* vi = a.V + (size_t)(i <= j ? i : 0) * a.ldv;
+    double sa = 0.0, sb = 0.0;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < a.n; e += (size_t)nb * blockDim.x) {
+      double2 we = a.w[e];
+      if (i > 0) {
+        we = we - cmul(hp, vprev[e]);
+        a.w[e] = we;
+      }
+      if (i <= j) {
+        double2 c = cconjmul(vi[e], we);
+        sa += c.x;
+        sb += c.y;
+      } else {
+        sa += we.x * we.x + we.y * we.y;
+      }
+    }
+    double2 s = block_sum2(sa, sb);
+    double* pb = a.part + (size_t)(i & 1) * 2 * nb;
+    if (threadIdx.x == 0) { pb[2 * blockIdx.x] = s.x; pb[2 * blockIdx.x + 1] = s.y; }
+    if (!grid_sync(a.bar, nb, a.err)) return;
+    hp = reduce_partials(pb, nb);
+    if (i <= j && blockIdx.x == 0 && threadIdx.x == 0) hcol[i] = hp;
+  }
+  double hn = sqrt(hp.x);
+  double inv = hn > 0.0 ? 1.0 / hn : 0.0;
+  double2* vnext = a.V + (size_t)(j + 1) * a.ldv;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < a.n; e += (size_t)nb * blockDim.x) {
+    double2 v = inv * a.w[e];
+    vnext[e] = v;
+    a.vcur[e] = v;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    hcol[j + 1] = make_double2(hn, 0.0);
+    givens_update(hcol, j, a.gs);
+    *a.jptr = j + 1;
+    unsigned go = (a.gs.flag[0] == 0 && a.gs.flag[1] == 0 && j + 1 < a.maxit) ? 1u : 0u;
+    if (a.use_cond) cudaGraphSetConditional(a.cond, go);
+  }
+}
+
+// z_j -> column j = *jptr of Zb
+__global__ void k_store_col(double2* Zb, size_t ldv, size_t n, const int* jptr, const double2* z) {
+  size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (e < n) Zb[(size_t)(*jptr) * ldv + e] = z[e];
+}
+// back substitution and combination with the device-side iteration count
+__global__ void k_backsolve_dev(const double2* H, int ldh, const double2* g, double2* y, const int* jptr) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int k = *jptr;
+  for (int r = k - 1; r >= 0; --r) {
+    double2 s = g[r];
+    for (int c = r + 1; c < k; ++c) s = s - cmul(H[(size_t)c * ldh + r], y[c]);
+    y[r] = cmul(s, cinv(H[(size_t)r * ldh + r]));
+  }
+}
+__global__ void k_combine_dev(const double2* V, size_t ldv, size_t n, const double2* y, const int* jptr, double2* x) {
+  size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  int k = *jptr;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int c = 0; c < k; ++c) acc = acc + cmul(y[c], V[(size_t)c * ldv + e]);
+  x[e] = acc;
+}
+
 // ------------------------------------------------------------------ host
 static int red_blocks(iga_ctx* ctx) { return 2 * ctx->num_sms; }
 
@@ -228,12 +350,30 @@ iga_status kry_mgs(iga_ctx* ctx, const double2* V, size_t ldv, int j, double2* w
   return IGA_OK;
 }
 
+static void drop_graph(iga_ctx* ctx) {
+  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+  if (ctx->graph) cudaGraphDestroy(ctx->graph);
+  ctx->gexec = nullptr;
+  ctx->graph = nullptr;
+}
+
 static iga_status ensure_krylov(iga_ctx* ctx, int maxit, bool flexible) {
   size_t n = ctx->lv[0].n;
+  if (!ctx->kvec) {
+    ctx->kvec = dalloc<double2>(ctx, 3 * n);        // vcur, zcur, wnext
+    ctx->kint = dalloc<int>(ctx, 4);                 // j, barrier err
+    ctx->kbar = dalloc<unsigned>(ctx, 2);
+    if (!ctx->kvec || !ctx->kint || !ctx->kbar) return set_err(ctx, IGA_E_OOM, "krylov vectors");
+    CK(cudaMemsetAsync(ctx->kbar, 0, 2 * sizeof(unsigned), ctx->st));
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_arnoldi_coop, 256, 0);
+    ctx->coop_blocks = std::max(1, std::min(occ, 2)) * ctx->num_sms;
+  }
   if (ctx->maxit_alloc >= maxit && (!flexible || ctx->Zb)) return IGA_OK;
+  drop_graph(ctx);
   int m = std::max(maxit, ctx->maxit_alloc);
   ctx->Vb = dalloc<double2>(ctx, n * (size_t)(m + 1));
-  if (flexible) ctx->Zb = dalloc<double2>(ctx, n * (size_t)m);
+  ctx->Zb = flexible || ctx->Zb ? dalloc<double2>(ctx, n * (size_t)m) : nullptr;
   ctx->H = dalloc<double2>(ctx, (size_t)(m + 1) * m);
   ctx->gstate = dalloc<double>(ctx, (size_t)m + (m + 1) + 4);
   ctx->gsn = dalloc<double2>(ctx, m);
@@ -257,15 +397,7 @@ static iga_status precond(iga_ctx* ctx, const double2* r, double2* z) {
   return IGA_OK;
 }
 
-iga_status kry_solve(iga_ctx* ctx, const double2* f, double2* x, double tol, int maxit, int* iters, double* hist,
-                     double* true_res) {
-  const bool flex = ctx->prm.precision != 0 || ctx->prm.flexible != 0;
-  TRY(ensure_krylov(ctx, maxit, flex));
-  cudaStream_t st = ctx->st;
-  const size_t n = ctx->lv[0].n;
-  const int ldh = ctx->maxit_alloc + 1;
-  const size_t ldv = n;
-  const int nb = red_blocks(ctx);
+static GState gstate_of(iga_ctx* ctx) {
   GState gs;
   gs.cs = ctx->gstate;
   gs.hist = ctx->gstate + ctx->maxit_alloc;
@@ -273,81 +405,178 @@ iga_status kry_solve(iga_ctx* ctx, const double2* f, double2* x, double tol, int
   gs.sn = ctx->gsn;
   gs.g = ctx->gg;
   gs.flag = ctx->gflag;
+  return gs;
+}
+
+static ArnoldiArgs arnoldi_args(iga_ctx* ctx, int maxit) {
+  ArnoldiArgs a;
+  a.V = ctx->Vb;
+  a.ldv = ctx->lv[0].n;
+  a.n = ctx->lv[0].n;
+  a.w = ctx->kvec + 2 * a.n;
+  a.vcur = ctx->kvec;
+  a.H = ctx->H;
+  a.ldh = ctx->maxit_alloc + 1;
+  a.maxit = maxit;
+  a.gs = gstate_of(ctx);
+  a.jptr = ctx->kint;
+  a.part = ctx->partials;
+  a.bar = ctx->kbar;
+  a.err = ctx->kint + 1;
+  a.cond = ctx->gcond;
+  a.use_cond = 0;
+  return a;
+}
+
+static iga_status launch_arnoldi(iga_ctx* ctx, ArnoldiArgs a) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(ctx->coop_blocks);
+  cfg.blockDim = dim3(256);
+  cfg.stream = ctx->st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  CK(cudaLaunchKernelEx(&cfg, k_arnoldi_coop, a));
+  iga_count_launch();
+  return IGA_OK;
+}
+
+// One iteration's work after v_j is in vcur: w = M~^{-1} P A v_j (left) or
+// z_j = M~^{-1} v_j, w = P A z_j (flexible), then the Arnoldi step.
+static iga_status iteration_body(iga_ctx* ctx, bool flex, ArnoldiArgs a) {
+  const size_t n = ctx->lv[0].n;
+  double2* vcur = ctx->kvec;
+  double2* zcur = ctx->kvec + n;
+  double2* wnext = ctx->kvec + 2 * n;
+  if (flex) {
+    TRY(precond(ctx, vcur, zcur));
+    k_store_col<<<cdiv(n, 256), 256, 0, ctx->st>>>(ctx->Zb, n, n, ctx->kint, zcur); iga_count_launch();
+    TRY(op_apply<double>(ctx, 0, OP_A, zcur, ctx->w1, nullptr, EPI_Y, nullptr, 0.0));
+    TRY(defl_apply(ctx, ctx->w1, wnext));
+  } else {
+    TRY(op_apply<double>(ctx, 0, OP_A, vcur, ctx->w1, nullptr, EPI_Y, nullptr, 0.0));
+    TRY(defl_apply(ctx, ctx->w1, ctx->w2));
+    TRY(precond(ctx, ctx->w2, wnext));
+  }
+  return launch_arnoldi(ctx, a);
+}
+
+// Build (once per workspace) the graph WHILE(cond) { iteration }.  Capture runs
+// on a private stream; ctx->st is restored afterwards.
+static iga_status build_loop_graph(iga_ctx* ctx, bool flex, int maxit) {
+  drop_graph(ctx);
+  if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+  CK(cudaGraphCreate(&ctx->graph, 0));
+  CK(cudaGraphConditionalHandleCreate(&ctx->gcond, ctx->graph, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = ctx->gcond;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  CK(cudaGraphAddNode(&node, ctx->graph, nullptr, nullptr, 0, &np));
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  cudaStream_t saved = ctx->st;
+  ctx->st = ctx->cap_stream;
+  unsigned long long before = iga_launch_count();
+  cudaError_t e = cudaStreamBeginCaptureToGraph(ctx->st, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) { ctx->st = saved; return set_err(ctx, IGA_E_CUDA, "capture: %s", cudaGetErrorString(e)); }
+  ArnoldiArgs a = arnoldi_args(ctx, maxit);
+  a.use_cond = 1;
+  iga_status s = iteration_body(ctx, flex, a);
+  cudaGraph_t cap = body;
+  cudaError_t e2 = cudaStreamEndCapture(ctx->st, &cap);
+  ctx->st = saved;
+  ctx->body_kernels = iga_launch_count() - before;
+  iga_add_launches(-(long long)ctx->body_kernels);   // capture does not execute anything
+  if (s != IGA_OK) return s;
+  if (e2 != cudaSuccess) return set_err(ctx, IGA_E_CUDA, "end capture: %s", cudaGetErrorString(e2));
+  CK(cudaGraphInstantiate(&ctx->gexec, ctx->graph, 0));
+  ctx->graph_flex = flex;
+  ctx->graph_maxit = maxit;
+  return IGA_OK;
+}
+
+iga_status kry_solve(iga_ctx* ctx, const double2* f, double2* x, double tol, int maxit, int* iters, double* hist,
+                     double* true_res) {
+  const bool flex = ctx->prm.precision != 0 || ctx->prm.flexible != 0;
+  TRY(ensure_krylov(ctx, maxit, flex));
+  cudaStream_t st = ctx->st;
+  const size_t n = ctx->lv[0].n;
+  const int ldh = ctx->maxit_alloc + 1;
+  const int nb = red_blocks(ctx);
+  GState gs = gstate_of(ctx);
   double tolv[1] = {tol};
   CK(cudaMemcpyAsync(gs.scal + 1, tolv, sizeof(double), cudaMemcpyHostToDevice, st));
   CK(cudaMemsetAsync(ctx->H, 0, sizeof(double2) * (size_t)ldh * ctx->maxit_alloc, st));
+  CK(cudaMemsetAsync(ctx->kint, 0, 4 * sizeof(int), st));
+  CK(cudaMemsetAsync(ctx->kbar, 0, 2 * sizeof(unsigned), st));
   double2* V = ctx->Vb;
-  // initial vector
+  // initial vector v0 = b / ||b||, b = P f (flexible) or M~^{-1} P f (left)
   if (flex) {
-    TRY(defl_apply(ctx, f, V));                       // b = P f
+    TRY(defl_apply(ctx, f, V));
   } else {
-    TRY(defl_apply(ctx, f, ctx->w0));                 // b = M~^{-1} P f
+    TRY(defl_apply(ctx, f, ctx->w0));
     TRY(precond(ctx, ctx->w0, V));
   }
   k_norm2_part<<<nb, IGA_RED_THREADS, 0, st>>>(V, n, ctx->partials); iga_count_launch();
   k_init_v0<<<nb, IGA_RED_THREADS, 0, st>>>(V, n, ctx->partials, gs); iga_count_launch();
   CKL();
-  int hflag[2] = {0, 0};
+  CK(cudaMemcpyAsync(ctx->kvec, V, sizeof(double2) * n, cudaMemcpyDeviceToDevice, st));
+  int hflag[4] = {0, 0, 0, 0};
   CK(cudaMemcpyAsync(hflag, gs.flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  int jdone = 0;
-  bool conv = hflag[0] != 0, nonfinite = hflag[1] != 0;
-  for (int j = 0; j < maxit && !conv && !nonfinite; ++j) {
-    double2* vj = V + (size_t)j * ldv;
-    double2* w = V + (size_t)(j + 1) * ldv;
-    if (flex) {
-      double2* zj = ctx->Zb + (size_t)j * ldv;
-      TRY(precond(ctx, vj, zj));
-      TRY(op_apply<double>(ctx, 0, OP_A, zj, ctx->w1, nullptr, EPI_Y, nullptr, 0.0));
-      TRY(defl_apply(ctx, ctx->w1, w));
+  if (!hflag[0] && !hflag[1]) {
+    if (ctx->use_graph) {
+      if (!ctx->gexec || ctx->graph_flex != flex || ctx->graph_maxit != maxit) {
+        iga_status s = build_loop_graph(ctx, flex, maxit);
+        if (s != IGA_OK) {                 // keep going without the graph
+          fprintf(stderr, "iga_solve: loop graph unavailable (%s); iterating from the host\n", ctx->err.c_str());
+          drop_graph(ctx);
+          ctx->use_graph = false;
+          cudaGetLastError();
+        }
+      }
+    }
+    if (ctx->use_graph) {
+      CK(cudaGraphLaunch(ctx->gexec, st));
     } else {
-      TRY(op_apply<double>(ctx, 0, OP_A, vj, ctx->w1, nullptr, EPI_Y, nullptr, 0.0));
-      TRY(defl_apply(ctx, ctx->w1, ctx->w2));
-      TRY(precond(ctx, ctx->w2, w));
+      ArnoldiArgs a = arnoldi_args(ctx, maxit);
+      for (int j = 0; j < maxit; ++j) {
+        TRY(iteration_body(ctx, flex, a));
+        CK(cudaMemcpyAsync(hflag, gs.flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(hflag + 2, ctx->kint, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (hflag[0] || hflag[1] || hflag[3]) break;
+      }
     }
-    double2* Hj = ctx->H + (size_t)j * ldh;
-    // MGS: h_ij for i <= j, then ||w||^2 partials
-    double* pa = ctx->partials;
-    double* pb = ctx->partials + 2 * nb;
-    for (int i = 0; i <= j + 1; ++i) {
-      const double* pin = (i & 1) ? pa : pb;
-      double* pout = (i & 1) ? pb : pa;
-      k_mgs_step<<<nb, IGA_RED_THREADS, 0, st>>>(V, ldv, n, i, j, w, pin, pout, Hj); iga_count_launch();
-    }
-    const double* plast = ((j + 1) & 1) ? pb : pa;
-    k_normalize_givens<<<nb, IGA_RED_THREADS, 0, st>>>(w, n, plast, Hj, j, gs, 1); iga_count_launch();
-    CKL();
-    CK(cudaMemcpyAsync(hflag, gs.flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    jdone = j + 1;
-    conv = hflag[0] != 0;
-    nonfinite = hflag[1] != 0;
   }
-  if (hist) CK(cudaMemcpyAsync(hist, gs.hist, sizeof(double) * (jdone + 1), cudaMemcpyDeviceToHost, st));
-  // y = R^{-1} g ; x^ = V y (or Z y)
-  if (jdone > 0) {
-    k_backsolve<<<1, 1, 0, st>>>(ctx->H, ldh, gs.g, ctx->gy, jdone); iga_count_launch();
-    k_combine<<<cdiv(n, 256), 256, 0, st>>>(flex ? ctx->Zb : V, ldv, n, ctx->gy, jdone, ctx->w0); iga_count_launch();
-  } else {
-    CK(cudaMemsetAsync(ctx->w0, 0, sizeof(double2) * n, st));
-  }
-  // u = x^ + Q (f - A x^)
+  // y = R^{-1} g ; x^ = V y (or Z y) ; u = x^ + Q (f - A x^)
+  k_backsolve_dev<<<1, 1, 0, st>>>(ctx->H, ldh, gs.g, ctx->gy, ctx->kint); iga_count_launch();
+  k_combine_dev<<<cdiv(n, 256), 256, 0, st>>>(flex ? ctx->Zb : V, n, n, ctx->gy, ctx->kint, ctx->w0); iga_count_launch();
   TRY(op_apply<double>(ctx, 0, OP_A, ctx->w0, ctx->w1, f, EPI_ZMINUS, nullptr, 0.0));
   TRY(defl_q(ctx, ctx->w1, ctx->w2));
   k_add<<<cdiv(n, 256), 256, 0, st>>>(ctx->w0, ctx->w2, x, n); iga_count_launch();
   CKL();
+  double* dn = gs.scal + 2;
   if (true_res) {
     TRY(op_apply<double>(ctx, 0, OP_A, x, ctx->w1, f, EPI_ZMINUS, nullptr, 0.0));
-    double* dn = gs.scal + 2;
     TRY(vec_norm(ctx, ctx->w1, n, dn));
     TRY(vec_norm(ctx, f, n, dn + 1));
-    double hn[2];
-    CK(cudaMemcpyAsync(hn, dn, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    *true_res = hn[1] > 0 ? hn[0] / hn[1] : 0.0;
   }
+  double hn[2] = {0.0, 0.0};
+  CK(cudaMemcpyAsync(hflag, gs.flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(hflag + 2, ctx->kint, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  if (true_res) CK(cudaMemcpyAsync(hn, dn, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  int jdone = hflag[2];
+  if (ctx->use_graph) iga_add_launches((long long)ctx->body_kernels * jdone);
+  if (hist) CK(cudaMemcpy(hist, gs.hist, sizeof(double) * (jdone + 1), cudaMemcpyDeviceToHost));
+  if (true_res) *true_res = hn[1] > 0 ? hn[0] / hn[1] : 0.0;
   if (iters) *iters = jdone;
-  if (nonfinite) return set_err(ctx, IGA_E_NONFINITE, "non-finite residual at iteration %d", jdone);
-  return conv ? IGA_OK : IGA_NOT_CONVERGED;
+  if (hflag[3]) return set_err(ctx, IGA_E_TIMEOUT, "grid barrier timed out in the Arnoldi step");
+  if (hflag[1]) return set_err(ctx, IGA_E_NONFINITE, "non-finite residual at iteration %d", jdone);
+  return hflag[0] ? IGA_OK : IGA_NOT_CONVERGED;
 }

@@ -98,19 +98,18 @@ __global__ void __launch_bounds__(256) k_kron1d(OpArgs<T> a) {
 }
 
 // ------------------------------------------------------------------ 2D constant k
-constexpr int KR_TX = 32, KR_TY = 16;
-
-template <int P, typename T>
+// Tile shapes (TX x TY outputs per 256-thread block): 32 x 16 for large grids,
+// 16 x 16 when the large tile would leave the SMs under-filled.
+template <int P, typename T, int TX, int TY>
 constexpr size_t kron2d_smem() {
   using C = typename cplx<T>::t;
-  return sizeof(C) * ((KR_TY + 2 * P) * (KR_TX + 2 * P) + 2 * (KR_TY + 2 * P) * KR_TX) +
-         sizeof(T) * (2 * KR_TX + 2 * KR_TY) * (2 * P + 1);
+  return sizeof(C) * ((TY + 2 * P) * (TX + 2 * P) + 2 * (TY + 2 * P) * TX) + sizeof(T) * (2 * TX + 2 * TY) * (2 * P + 1);
 }
 
-template <int P, typename T, int EPI>
+template <int P, typename T, int EPI, int TX, int TY>
 __global__ void __launch_bounds__(256) k_kron2d(OpArgs<T> a) {
   using C = typename cplx<T>::t;
-  constexpr int W = 2 * P + 1, TX = KR_TX, TY = KR_TY, SX = TX + 2 * P, SY = TY + 2 * P;
+  constexpr int W = 2 * P + 1, SX = TX + 2 * P, SY = TY + 2 * P;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* xs = (C*)smem_raw;
   C* us = xs + SY * SX;
@@ -347,14 +346,26 @@ static void launch_op(iga_ctx* ctx, const OpArgs<T>& a, int level) {
   if (ctx->dim == 1) {
     k_kron1d<P, T, EPI><<<cdiv(a.nx, 256), 256, 0, st>>>(a); iga_count_launch();
   } else if (!ctx->vark) {
-    constexpr size_t sm = kron2d_smem<P, T>();
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(k_kron2d<P, T, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      attr = true;
+    size_t big = (size_t)cdiv(a.nx, 32) * cdiv(a.ny, 16);
+    if (big >= (size_t)3 * ctx->num_sms) {
+      constexpr size_t sm = kron2d_smem<P, T, 32, 16>();
+      static bool attr = false;
+      if (!attr) {
+        cudaFuncSetAttribute(k_kron2d<P, T, EPI, 32, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        attr = true;
+      }
+      dim3 grid(cdiv(a.nx, 32), cdiv(a.ny, 16));
+      k_kron2d<P, T, EPI, 32, 16><<<grid, 256, sm, st>>>(a); iga_count_launch();
+    } else {
+      constexpr size_t sm = kron2d_smem<P, T, 16, 16>();
+      static bool attr = false;
+      if (!attr) {
+        cudaFuncSetAttribute(k_kron2d<P, T, EPI, 16, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        attr = true;
+      }
+      dim3 grid(cdiv(a.nx, 16), cdiv(a.ny, 16));
+      k_kron2d<P, T, EPI, 16, 16><<<grid, 256, sm, st>>>(a); iga_count_launch();
     }
-    dim3 grid(cdiv(a.nx, KR_TX), cdiv(a.ny, KR_TY));
-    k_kron2d<P, T, EPI><<<grid, 256, sm, st>>>(a); iga_count_launch();
   } else {
     constexpr size_t sm = elem2d_smem<P, T>();
     static bool attr = false;

@@ -3,6 +3,7 @@
     python -m paper_2010_10232_gb300.profile_cases apply   # FP64 constant-k apply, bench size
     python -m paper_2010_10232_gb300.profile_cases apply32 # FP32 M_beta Jacobi sweep, 4097^2 dofs
     python -m paper_2010_10232_gb300.profile_cases solve   # one bench solve
+    python -m paper_2010_10232_gb300.profile_cases solve_host  # same, iterations launched from the host
 
 Each case launches a handful of kernels on inputs of the bench problem so a
 capture (-k <kernel> -c <count>) ends in seconds.
@@ -29,8 +30,8 @@ def main(case: str) -> None:
         x = torch.randn(h.n, dtype=torch.complex128, device="cuda")
         z = h.vec()
         h.vcycle(x, z)
-    elif case == "solve":
-        h = Helmholtz(dim=2, p=3, n_el=320, kfield=200.0)
+    elif case in ("solve", "solve_host"):
+        h = Helmholtz(dim=2, p=3, n_el=320, kfield=200.0, host_loop=int(case == "solve_host"))
         f = h.point_source(0.5, 0.5)
         h.solve(f)
     else:

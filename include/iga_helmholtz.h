@@ -181,6 +181,68 @@ iga_status iga_solve(iga_ctx* ctx, const iga_c128* rhs, iga_c128* x, double tol,
 iga_status iga_solve_host(iga_ctx* ctx, const iga_c128* rhs_host, iga_c128* x_host, double tol,
                           int maxit, int* iters, double* res_hist, double* true_res);
 
+/* Operator tile shape chosen by the setup-time autotuner for `level` and
+   precision (0 FP64, 1 FP32): 0 = 32x16, 1 = 16x16, 2 = 32x8 outputs per block,
+   -1 = not tuned (heuristic), -2 = bad argument.  The autotuner times the three
+   shapes on each level with >= 64^2 dofs (constant k, 2D) and caches the
+   choice per (p, precision, n_x) for the process. */
+int iga_tile_choice(const iga_ctx* ctx, int level, int precision);
+
+/* Batched solves in one CUDA-graph launch (not in the paper; the batched form of
+   the method): instance b (context ctxs[b], each with its own k, p, mesh and
+   precision) solves nrhs[b] right-hand sides stored back to back at rhs[b]
+   (nrhs[b] * n_b complex128, DEVICE) into x[b] (same layout).  The chains of
+   one instance run in order, different instances run concurrently, and each
+   right-hand side stops on its own convergence test (tol, maxit as iga_solve).
+   iters and status (HOST, sum(nrhs) entries, instance-major; status may be
+   NULL) receive per right-hand side the iteration count and IGA_OK /
+   IGA_NOT_CONVERGED / error.  Contexts must be distinct, on one device, built
+   with deflation.  Work is launched on `stream`; the call synchronises.
+   Returns the worst per-right-hand-side status. */
+iga_status iga_solve_batched(iga_ctx* const* ctxs, int nb, const iga_c128* const* rhs, iga_c128* const* x,
+                             const int* nrhs, double tol, int maxit, int* iters, int* status, void* stream);
+
+/* ------------------------------------------------------------------ learned correction
+   Not in the paper: a 3x3 convolutional network (channels 3 -> 32 -> 32 -> 32 -> 2,
+   ReLU after the first three layers, BF16 weights/activations, FP32
+   accumulation on the tensor cores) that corrects the FP32 CSLP V-cycle inside
+   FGMRES: z = V(v) + gamma s NN(r~ / s), r~ = v - M_beta V(v), s = RMS(r~).
+   A correction with any non-finite entry is dropped (the plain V-cycle result
+   is used).  Input tensors are NHWC bf16 [B][H][W][16]: channels (Re r~ / s,
+   Im r~ / s, (k h)^2 at the dof's Greville point, 13 zeros); outputs and
+   targets FP32 [B][H][W][2].  Parameters: one flat FP32 vector, layer by layer
+   W[co][3][3][ci] then bias[co] (iga_net_num_params() floats). */
+typedef struct iga_net iga_net;
+int iga_net_num_params(void);
+/* He-initialised network (counter-based normal draws from `seed`). */
+iga_status iga_net_create(unsigned long long seed, iga_net** out);
+void iga_net_destroy(iga_net* net);
+const char* iga_net_last_error(const iga_net* net);
+/* HOST copies of the FP32 parameters (checkpoint / restore; set resets Adam). */
+iga_status iga_net_get_params(iga_net* net, float* host, int cap);
+iga_status iga_net_set_params(iga_net* net, const float* host, int count);
+/* y = NN(x) for B images of H x W (x: DEVICE bf16 NHWC-16, y: DEVICE FP32 NHWC-2). */
+iga_status iga_net_forward(iga_net* net, const void* x, float* y, int B, int H, int W, void* stream);
+/* Batch loss mean_b ||NN(x_b) - t_b||^2 / ||t_b||^2 and its gradient (grad_host:
+   HOST, iga_net_num_params() floats; loss_host: HOST; either may be NULL).
+   Synchronises. */
+iga_status iga_net_grad(iga_net* net, const void* x, const float* t, int B, int H, int W, float* grad_host,
+                        float* loss_host, void* stream);
+/* One Adam step (lr, beta 0.9 / 0.999, eps 1e-8) on the batch loss; loss_host
+   (HOST, may be NULL) receives the loss before the step. */
+iga_status iga_net_train_step(iga_net* net, const void* x, const float* t, int B, int H, int W, float lr,
+                              float* loss_host, void* stream);
+/* Attach (or detach with NULL) a network to a 2D context in precision 1. */
+iga_status iga_attach_net(iga_ctx* ctx, iga_net* net, double gamma);
+/* Training pair from a preconditioner input v (DEVICE, n complex128):
+   rt = v - M_beta V(v) and e ~ M_beta^{-1} rt by `cycles` FP32 V-cycles. */
+iga_status iga_precond_pair(iga_ctx* ctx, const iga_c128* v, iga_c128* rt, iga_c128* e, int cycles);
+/* Crop [y0, y0+Hc) x [x0, x0+Wc) of rt (and e) into a network input X (DEVICE
+   bf16 [Hc][Wc][16]) and target T = e / (RMS(rt) gamma) (DEVICE FP32
+   [Hc][Wc][2]; skipped when e or T is NULL). */
+iga_status iga_net_pack(iga_ctx* ctx, const iga_c128* rt, const iga_c128* e, int x0, int y0, int Hc, int Wc,
+                        void* X, float* T, double gamma);
+
 /* Allocation-free variant of iga_mgs, for callers that cannot call cudaMalloc
    (for example code inside a framework whose caching allocator owns the device
    memory, or a latency-critical loop that must not pay cudaMalloc's implicit

@@ -51,6 +51,22 @@ _SIG = {
     "iga_level_nel": (C.c_int, [_VP, C.c_int]),
     "iga_status_str": (C.c_char_p, [C.c_int]),
     "iga_launch_count": (C.c_ulonglong, []),
+    "iga_tile_choice": (C.c_int, [_VP, C.c_int, C.c_int]),
+    "iga_solve_batched": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                     C.POINTER(C.c_int), C.c_double, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                     _VP]),
+    "iga_net_num_params": (C.c_int, []),
+    "iga_net_create": (C.c_int, [C.c_ulonglong, C.POINTER(C.c_void_p)]),
+    "iga_net_destroy": (None, [_VP]),
+    "iga_net_last_error": (C.c_char_p, [_VP]),
+    "iga_net_get_params": (C.c_int, [_VP, _VP, C.c_int]),
+    "iga_net_set_params": (C.c_int, [_VP, _VP, C.c_int]),
+    "iga_net_forward": (C.c_int, [_VP, _VP, _VP, C.c_int, C.c_int, C.c_int, _VP]),
+    "iga_net_grad": (C.c_int, [_VP, _VP, _VP, C.c_int, C.c_int, C.c_int, _VP, _VP, _VP]),
+    "iga_net_train_step": (C.c_int, [_VP, _VP, _VP, C.c_int, C.c_int, C.c_int, C.c_float, _VP, _VP]),
+    "iga_attach_net": (C.c_int, [_VP, _VP, C.c_double]),
+    "iga_precond_pair": (C.c_int, [_VP, _VP, _VP, _VP, C.c_int]),
+    "iga_net_pack": (C.c_int, [_VP, _VP, _VP, C.c_int, C.c_int, C.c_int, C.c_int, _VP, _VP, C.c_double]),
     "iga_mgs_noalloc": (C.c_int, [_VP, C.c_size_t, C.c_size_t, C.c_int, _VP, _VP, _VP]),
     "iga_probe_fma": (C.c_int, [C.c_int, C.c_int, _VP, _VP, C.POINTER(C.c_double)]),
     "iga_last_error": (C.c_char_p, [_VP]),

@@ -100,6 +100,7 @@ iga_status iga_setup(const iga_params* prm, iga_ctx** out) {
   ctx->k2const = P.k_values[0] * P.k_values[0];
   ctx->sig = make_double2(P.beta1, -P.beta2);
   ctx->use_graph = P.host_loop == 0;
+  for (int l = 0; l < IGA_MAX_LEVELS; ++l) ctx->tile[l][0] = ctx->tile[l][1] = -1;
   iga_status s = IGA_OK;
   do {
     if (cudaGetDevice(&ctx->device) != cudaSuccess) { s = set_err(ctx, IGA_E_CUDA, "no CUDA device"); break; }
@@ -109,6 +110,7 @@ iga_status iga_setup(const iga_params* prm, iga_ctx** out) {
       for (int l = 0; l < ctx->L && s == IGA_OK; ++l) s = setup_vark_diag(ctx, l);
     if (s != IGA_OK) break;
     if ((s = alloc_level_vectors(ctx)) != IGA_OK) break;
+    if ((s = autotune_tiles(ctx)) != IGA_OK) break;
     if ((s = setup_coarse_inverse(ctx)) != IGA_OK) break;
     size_t n = ctx->lv[0].n;
     ctx->w0 = dalloc<double2>(ctx, n);
@@ -248,6 +250,7 @@ iga_status iga_vcycle_cslp(iga_ctx* ctx, const iga_c128* r, iga_c128* z) {
   size_t n = ctx->lv[0].n;
   launch_convert_d2f((const double2*)r, ctx->fin, n, ctx->st);
   TRY(mg_vcycle<float>(ctx, ctx->fin, ctx->fout));
+  if (ctx->net) TRY(net_correct(ctx, ctx->fin, ctx->fout));
   launch_convert_f2d(ctx->fout, (double2*)z, n, ctx->st);
   CKL();
   return IGA_OK;

@@ -90,6 +90,8 @@ struct LevelData {
   float2 *fb = nullptr, *fx = nullptr, *fy = nullptr, *fr = nullptr;
 };
 
+struct iga_net;
+
 struct DevBuf {   // tracked allocation list
   std::vector<void*> ptrs;
   ~DevBuf() { for (void* p : ptrs) cudaFree(p); }
@@ -103,6 +105,7 @@ struct iga_ctx {
   double k2const = 0.0;              // k^2 when constant
   double2 sig{};                     // beta1 - i beta2
   LevelData lv[IGA_MAX_LEVELS];
+  int tile[IGA_MAX_LEVELS][2];       // operator tile shape per level and precision (-1: heuristic)
   cudaStream_t st = nullptr;
   int device = 0;
   int num_sms = 148;
@@ -122,7 +125,12 @@ struct iga_ctx {
   double2* cw = nullptr;
   double2* ce1 = nullptr;            // refinement residual / correction
   double2* ce2 = nullptr;
-  int e_refine = 1;                  // iterative refinement steps of the FDM solve (0 or 1)
+  int e_refine = 2;                  // iterative refinement steps of the FDM coarse solve
+  float* fdmVf = nullptr;            // FP32 copy of the eigenvectors
+  double* kcb = nullptr;             // banded 1D coarse matrices (half width (p+4)/2)
+  double* mcb = nullptr;
+  float2* cwf = nullptr;             // FP32 transform scratch
+  float2* cwf2 = nullptr;
   // variable-k E (block tridiagonal, banded in y): see deflation.cu
   int eblk = 0, enb = 0, els = 0;   // block size (lines per block * mx), number of blocks, lines
   double2* eDinv = nullptr;          // [enb][bs][bs] inverse diagonal blocks D_I^{-1}
@@ -162,6 +170,13 @@ struct iga_ctx {
   bool graph_flex = false;
   int graph_maxit = 0;
   unsigned long long body_kernels = 0;
+  // learned correction of the FP32 V-cycle (precision 1 with a network attached)
+  iga_net* net = nullptr;
+  double net_gamma = 1.0;
+  double* net_rms = nullptr;
+  int* net_bad = nullptr;
+  int* brec = nullptr;               // batched solve: per right-hand side {iters, conv, nonfinite, timeout}
+  int brec_cap = 0;
   double* hres = nullptr;            // pinned host copy of residual
   DevBuf bufs;
   std::string err;
@@ -207,6 +222,10 @@ iga_status op_apply(iga_ctx* ctx, int level, int which, const typename cplx<T>::
                     typename cplx<T>::t* y, const typename cplx<T>::t* z, int epi,
                     const typename cplx<T>::t* b, double omega);
 iga_status setup_vark_diag(iga_ctx* ctx, int level);
+iga_status autotune_tiles(iga_ctx* ctx);
+// constant-coefficient tensor operator with explicit 1D bands (half width P)
+iga_status op_apply_bands(iga_ctx* ctx, int P, int nx, int ny, const double* K, const double* M, double2 c,
+                          const double2* x, double2* y, const double2* z, int epi);
 // op "which": 0 = A (c = -1), 1 = M_beta (c = -sigma)
 enum { OP_A = 0, OP_MB = 1 };
 // epilogues
@@ -228,6 +247,8 @@ iga_status defl_q(iga_ctx* ctx, const double2* x, double2* y);            // y =
 // ecoarse.cu (variable k)
 iga_status setup_block_E(iga_ctx* ctx);
 iga_status block_E_solve(iga_ctx* ctx, const double2* t, double2* s);
+// cnn.cu
+iga_status net_correct(iga_ctx* ctx, const float2* r, float2* z);
 // krylov.cu
 iga_status kry_mgs(iga_ctx* ctx, const double2* V, size_t ldv, int j, double2* w, double2* h);
 iga_status kry_solve(iga_ctx* ctx, const double2* f, double2* x, double tol, int maxit, int* iters,

@@ -159,19 +159,44 @@ __global__ void k_normalize_givens(double2* w, size_t n, const double* part, dou
   }
 }
 
-// initial vector: v0 = b / ||b||, g0 = beta, hist0 = 1
-__global__ void k_init_v0(double2* v, size_t n, const double* part, GState gs) {
+// initial vector: v0 = b / ||b||, g0 = beta, hist0 = 1; optionally sets the
+// loop condition of the following WHILE node (run only if beta is finite and
+// non-zero).
+__global__ void k_init_v0(double2* v, size_t n, const double* part, GState gs, double2* vcur,
+                          cudaGraphConditionalHandle cond, int use_cond) {
   double2 s = reduce_partials(part, gridDim.x);
   double beta = sqrt(s.x);
   double inv = beta > 0.0 ? 1.0 / beta : 0.0;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
-    v[e] = inv * v[e];
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    double2 u = inv * v[e];
+    v[e] = u;
+    if (vcur) vcur[e] = u;
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     gs.scal[0] = beta;
     gs.g[0] = make_double2(beta, 0.0);
     gs.hist[0] = 1.0;
     gs.flag[0] = (beta == 0.0) ? 1 : 0;
     gs.flag[1] = isfinite(beta) ? 0 : 1;
+    if (use_cond) cudaGraphSetConditional(cond, (beta > 0.0 && isfinite(beta)) ? 1u : 0u);
+  }
+}
+
+// per-solve state reset (kernel form so that it can live inside a graph)
+__global__ void k_solve_reset(double2* H, size_t nh, int* kint, unsigned* kbar, double* scal, double tol) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < nh) H[i] = make_double2(0.0, 0.0);
+  if (i < 4) kint[i] = 0;
+  if (i < 2) kbar[i] = 0u;
+  if (i == 0) scal[1] = tol;
+}
+// copy the iteration count and flags of a finished solve into slot `slot`
+__global__ void k_record(const int* kint, const int* flag, int* out, int slot) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    out[4 * slot + 0] = kint[0];
+    out[4 * slot + 1] = flag[0];
+    out[4 * slot + 2] = flag[1];
+    out[4 * slot + 3] = kint[1];
   }
 }
 
@@ -367,7 +392,11 @@ static iga_status ensure_krylov(iga_ctx* ctx, int maxit, bool flexible) {
     CK(cudaMemsetAsync(ctx->kbar, 0, 2 * sizeof(unsigned), ctx->st));
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_arnoldi_coop, 256, 0);
-    ctx->coop_blocks = std::max(1, std::min(occ, 2)) * ctx->num_sms;
+    // co-resident blocks for the cooperative Arnoldi step, sized to the problem
+    // (about 2048 entries per block) so that small batched instances leave room
+    // for each other
+    int cap = std::max(1, std::min(occ, 2)) * ctx->num_sms;
+    ctx->coop_blocks = (int)std::max<size_t>(1, std::min<size_t>(cap, cdiv(n, 2048)));
   }
   if (ctx->maxit_alloc >= maxit && (!flexible || ctx->Zb)) return IGA_OK;
   drop_graph(ctx);
@@ -392,6 +421,7 @@ static iga_status precond(iga_ctx* ctx, const double2* r, double2* z) {
   LevelData& L = ctx->lv[0];
   launch_convert_d2f(r, ctx->fin, L.n, ctx->st);
   TRY(mg_vcycle<float>(ctx, ctx->fin, ctx->fout));
+  if (ctx->net) TRY(net_correct(ctx, ctx->fin, ctx->fout));
   launch_convert_f2d(ctx->fout, z, L.n, ctx->st);
   CKL();
   return IGA_OK;
@@ -465,9 +495,12 @@ static iga_status iteration_body(iga_ctx* ctx, bool flex, ArnoldiArgs a) {
 
 // Build (once per workspace) the graph WHILE(cond) { iteration }.  Capture runs
 // on a private stream; ctx->st is restored afterwards.
+iga_status capture_body(iga_ctx* ctx, cudaGraph_t body, bool flex, int maxit, cudaGraphConditionalHandle cond,
+                        unsigned long long* nkern);
+
+// Build (once per workspace) the graph WHILE(cond) { iteration }.
 static iga_status build_loop_graph(iga_ctx* ctx, bool flex, int maxit) {
   drop_graph(ctx);
-  if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
   CK(cudaGraphCreate(&ctx->graph, 0));
   CK(cudaGraphConditionalHandleCreate(&ctx->gcond, ctx->graph, 1, cudaGraphCondAssignDefault));
   cudaGraphNodeParams np = {};
@@ -477,44 +510,24 @@ static iga_status build_loop_graph(iga_ctx* ctx, bool flex, int maxit) {
   np.conditional.size = 1;
   cudaGraphNode_t node;
   CK(cudaGraphAddNode(&node, ctx->graph, nullptr, nullptr, 0, &np));
-  cudaGraph_t body = np.conditional.phGraph_out[0];
-  cudaStream_t saved = ctx->st;
-  ctx->st = ctx->cap_stream;
-  unsigned long long before = iga_launch_count();
-  cudaError_t e = cudaStreamBeginCaptureToGraph(ctx->st, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
-  if (e != cudaSuccess) { ctx->st = saved; return set_err(ctx, IGA_E_CUDA, "capture: %s", cudaGetErrorString(e)); }
-  ArnoldiArgs a = arnoldi_args(ctx, maxit);
-  a.use_cond = 1;
-  iga_status s = iteration_body(ctx, flex, a);
-  cudaGraph_t cap = body;
-  cudaError_t e2 = cudaStreamEndCapture(ctx->st, &cap);
-  ctx->st = saved;
-  ctx->body_kernels = iga_launch_count() - before;
-  iga_add_launches(-(long long)ctx->body_kernels);   // capture does not execute anything
-  if (s != IGA_OK) return s;
-  if (e2 != cudaSuccess) return set_err(ctx, IGA_E_CUDA, "end capture: %s", cudaGetErrorString(e2));
+  TRY(capture_body(ctx, np.conditional.phGraph_out[0], flex, maxit, ctx->gcond, &ctx->body_kernels));
   CK(cudaGraphInstantiate(&ctx->gexec, ctx->graph, 0));
   ctx->graph_flex = flex;
   ctx->graph_maxit = maxit;
   return IGA_OK;
 }
 
-iga_status kry_solve(iga_ctx* ctx, const double2* f, double2* x, double tol, int maxit, int* iters, double* hist,
-                     double* true_res) {
-  const bool flex = ctx->prm.precision != 0 || ctx->prm.flexible != 0;
-  TRY(ensure_krylov(ctx, maxit, flex));
+// Phase 1 (kernels only): reset the solve state and form v0.
+iga_status solve_init(iga_ctx* ctx, const double2* f, double tol, bool flex, cudaGraphConditionalHandle cond,
+                      int use_cond) {
   cudaStream_t st = ctx->st;
   const size_t n = ctx->lv[0].n;
   const int ldh = ctx->maxit_alloc + 1;
   const int nb = red_blocks(ctx);
   GState gs = gstate_of(ctx);
-  double tolv[1] = {tol};
-  CK(cudaMemcpyAsync(gs.scal + 1, tolv, sizeof(double), cudaMemcpyHostToDevice, st));
-  CK(cudaMemsetAsync(ctx->H, 0, sizeof(double2) * (size_t)ldh * ctx->maxit_alloc, st));
-  CK(cudaMemsetAsync(ctx->kint, 0, 4 * sizeof(int), st));
-  CK(cudaMemsetAsync(ctx->kbar, 0, 2 * sizeof(unsigned), st));
+  size_t nh = (size_t)ldh * ctx->maxit_alloc;
+  k_solve_reset<<<cdiv(nh, 256), 256, 0, st>>>(ctx->H, nh, ctx->kint, ctx->kbar, gs.scal, tol); iga_count_launch();
   double2* V = ctx->Vb;
-  // initial vector v0 = b / ||b||, b = P f (flexible) or M~^{-1} P f (left)
   if (flex) {
     TRY(defl_apply(ctx, f, V));
   } else {
@@ -522,9 +535,65 @@ iga_status kry_solve(iga_ctx* ctx, const double2* f, double2* x, double tol, int
     TRY(precond(ctx, ctx->w0, V));
   }
   k_norm2_part<<<nb, IGA_RED_THREADS, 0, st>>>(V, n, ctx->partials); iga_count_launch();
-  k_init_v0<<<nb, IGA_RED_THREADS, 0, st>>>(V, n, ctx->partials, gs); iga_count_launch();
+  k_init_v0<<<nb, IGA_RED_THREADS, 0, st>>>(V, n, ctx->partials, gs, ctx->kvec, cond, use_cond); iga_count_launch();
   CKL();
-  CK(cudaMemcpyAsync(ctx->kvec, V, sizeof(double2) * n, cudaMemcpyDeviceToDevice, st));
+  return IGA_OK;
+}
+
+// Phase 3 (kernels only): x^ = V y (Z y), u = x^ + Q (f - A x^), optional
+// true-residual norms into scal[2], scal[3].
+iga_status solve_finish(iga_ctx* ctx, const double2* f, double2* x, bool flex, bool true_res) {
+  cudaStream_t st = ctx->st;
+  const size_t n = ctx->lv[0].n;
+  const int ldh = ctx->maxit_alloc + 1;
+  GState gs = gstate_of(ctx);
+  k_backsolve_dev<<<1, 1, 0, st>>>(ctx->H, ldh, gs.g, ctx->gy, ctx->kint); iga_count_launch();
+  k_combine_dev<<<cdiv(n, 256), 256, 0, st>>>(flex ? ctx->Zb : ctx->Vb, n, n, ctx->gy, ctx->kint, ctx->w0); iga_count_launch();
+  TRY(op_apply<double>(ctx, 0, OP_A, ctx->w0, ctx->w1, f, EPI_ZMINUS, nullptr, 0.0));
+  TRY(defl_q(ctx, ctx->w1, ctx->w2));
+  k_add<<<cdiv(n, 256), 256, 0, st>>>(ctx->w0, ctx->w2, x, n); iga_count_launch();
+  CKL();
+  if (true_res) {
+    TRY(op_apply<double>(ctx, 0, OP_A, x, ctx->w1, f, EPI_ZMINUS, nullptr, 0.0));
+    TRY(vec_norm(ctx, ctx->w1, n, gs.scal + 2));
+    TRY(vec_norm(ctx, f, n, gs.scal + 3));
+  }
+  return IGA_OK;
+}
+
+// Capture one iteration into `body` (the body graph of a WHILE node) with the
+// Arnoldi step driving `cond`.  Returns the number of kernels in the body.
+iga_status capture_body(iga_ctx* ctx, cudaGraph_t body, bool flex, int maxit, cudaGraphConditionalHandle cond,
+                        unsigned long long* nkern) {
+  if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+  cudaStream_t saved = ctx->st;
+  ctx->st = ctx->cap_stream;
+  unsigned long long before = iga_launch_count();
+  cudaError_t e = cudaStreamBeginCaptureToGraph(ctx->st, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) { ctx->st = saved; return set_err(ctx, IGA_E_CUDA, "capture: %s", cudaGetErrorString(e)); }
+  ArnoldiArgs a = arnoldi_args(ctx, maxit);
+  a.cond = cond;
+  a.use_cond = 1;
+  iga_status s = iteration_body(ctx, flex, a);
+  cudaGraph_t cap = body;
+  cudaError_t e2 = cudaStreamEndCapture(ctx->st, &cap);
+  ctx->st = saved;
+  *nkern = iga_launch_count() - before;
+  iga_add_launches(-(long long)*nkern);   // capture executes nothing
+  if (s != IGA_OK) return s;
+  if (e2 != cudaSuccess) return set_err(ctx, IGA_E_CUDA, "end capture: %s", cudaGetErrorString(e2));
+  return IGA_OK;
+}
+
+iga_status kry_prepare(iga_ctx* ctx, int maxit, bool flex) { return ensure_krylov(ctx, maxit, flex); }
+
+iga_status kry_solve(iga_ctx* ctx, const double2* f, double2* x, double tol, int maxit, int* iters, double* hist,
+                     double* true_res) {
+  const bool flex = ctx->prm.precision != 0 || ctx->prm.flexible != 0;
+  TRY(ensure_krylov(ctx, maxit, flex));
+  cudaStream_t st = ctx->st;
+  GState gs = gstate_of(ctx);
+  TRY(solve_init(ctx, f, tol, flex, 0, 0));
   int hflag[4] = {0, 0, 0, 0};
   CK(cudaMemcpyAsync(hflag, gs.flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -553,23 +622,11 @@ iga_status kry_solve(iga_ctx* ctx, const double2* f, double2* x, double tol, int
       }
     }
   }
-  // y = R^{-1} g ; x^ = V y (or Z y) ; u = x^ + Q (f - A x^)
-  k_backsolve_dev<<<1, 1, 0, st>>>(ctx->H, ldh, gs.g, ctx->gy, ctx->kint); iga_count_launch();
-  k_combine_dev<<<cdiv(n, 256), 256, 0, st>>>(flex ? ctx->Zb : V, n, n, ctx->gy, ctx->kint, ctx->w0); iga_count_launch();
-  TRY(op_apply<double>(ctx, 0, OP_A, ctx->w0, ctx->w1, f, EPI_ZMINUS, nullptr, 0.0));
-  TRY(defl_q(ctx, ctx->w1, ctx->w2));
-  k_add<<<cdiv(n, 256), 256, 0, st>>>(ctx->w0, ctx->w2, x, n); iga_count_launch();
-  CKL();
-  double* dn = gs.scal + 2;
-  if (true_res) {
-    TRY(op_apply<double>(ctx, 0, OP_A, x, ctx->w1, f, EPI_ZMINUS, nullptr, 0.0));
-    TRY(vec_norm(ctx, ctx->w1, n, dn));
-    TRY(vec_norm(ctx, f, n, dn + 1));
-  }
+  TRY(solve_finish(ctx, f, x, flex, true_res != nullptr));
   double hn[2] = {0.0, 0.0};
   CK(cudaMemcpyAsync(hflag, gs.flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(hflag + 2, ctx->kint, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
-  if (true_res) CK(cudaMemcpyAsync(hn, dn, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (true_res) CK(cudaMemcpyAsync(hn, gs.scal + 2, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   int jdone = hflag[2];
   if (ctx->use_graph) iga_add_launches((long long)ctx->body_kernels * jdone);

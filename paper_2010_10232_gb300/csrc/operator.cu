@@ -340,32 +340,32 @@ __global__ void k_vark_diag(int nx, int n_el, int p, const double* K, const doub
 }
 
 // ------------------------------------------------------------------ host dispatch
+template <int P, typename T, int EPI, int TX, int TY>
+static void launch_kron_tile(const OpArgs<T>& a, cudaStream_t st) {
+  constexpr size_t sm = kron2d_smem<P, T, TX, TY>();
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_kron2d<P, T, EPI, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    attr = true;
+  }
+  dim3 grid(cdiv(a.nx, TX), cdiv(a.ny, TY));
+  k_kron2d<P, T, EPI, TX, TY><<<grid, 256, sm, st>>>(a); iga_count_launch();
+}
+
 template <int P, typename T, int EPI>
 static void launch_op(iga_ctx* ctx, const OpArgs<T>& a, int level) {
   cudaStream_t st = ctx->st;
   if (ctx->dim == 1) {
     k_kron1d<P, T, EPI><<<cdiv(a.nx, 256), 256, 0, st>>>(a); iga_count_launch();
   } else if (!ctx->vark) {
-    size_t big = (size_t)cdiv(a.nx, 32) * cdiv(a.ny, 16);
-    if (big >= (size_t)3 * ctx->num_sms) {
-      constexpr size_t sm = kron2d_smem<P, T, 32, 16>();
-      static bool attr = false;
-      if (!attr) {
-        cudaFuncSetAttribute(k_kron2d<P, T, EPI, 32, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        attr = true;
-      }
-      dim3 grid(cdiv(a.nx, 32), cdiv(a.ny, 16));
-      k_kron2d<P, T, EPI, 32, 16><<<grid, 256, sm, st>>>(a); iga_count_launch();
-    } else {
-      constexpr size_t sm = kron2d_smem<P, T, 16, 16>();
-      static bool attr = false;
-      if (!attr) {
-        cudaFuncSetAttribute(k_kron2d<P, T, EPI, 16, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        attr = true;
-      }
-      dim3 grid(cdiv(a.nx, 16), cdiv(a.ny, 16));
-      k_kron2d<P, T, EPI, 16, 16><<<grid, 256, sm, st>>>(a); iga_count_launch();
+    int tile = ctx->tile[level][sizeof(T) == 8 ? 0 : 1];
+    if (tile < 0) {   // untuned: heuristic
+      size_t big = (size_t)cdiv(a.nx, 32) * cdiv(a.ny, 16);
+      tile = big >= (size_t)3 * ctx->num_sms ? 0 : 1;
     }
+    if (tile == 0) launch_kron_tile<P, T, EPI, 32, 16>(a, st);
+    else if (tile == 1) launch_kron_tile<P, T, EPI, 16, 16>(a, st);
+    else launch_kron_tile<P, T, EPI, 32, 8>(a, st);
   } else {
     constexpr size_t sm = elem2d_smem<P, T>();
     static bool attr = false;
@@ -450,4 +450,107 @@ iga_status setup_vark_diag(iga_ctx* ctx, int level) {
                                                    L.dinv, L.dinvf); iga_count_launch();
   CKL();
   return IGA_OK;
+}
+
+// Constant-coefficient tensor operator with explicit bands (used for the
+// deflation coarse matrix E, which has the same Kronecker structure as A).
+template <int P>
+static void launch_bands(iga_ctx* ctx, const OpArgs<double>& a, int epi) {
+  cudaStream_t st = ctx->st;
+  if (a.ny == 1) {
+    if (epi == EPI_Y) { k_kron1d<P, double, EPI_Y><<<cdiv(a.nx, 256), 256, 0, st>>>(a); iga_count_launch(); }
+    else { k_kron1d<P, double, EPI_ZMINUS><<<cdiv(a.nx, 256), 256, 0, st>>>(a); iga_count_launch(); }
+    return;
+  }
+  if (epi == EPI_Y) launch_kron_tile<P, double, EPI_Y, 16, 16>(a, st);
+  else launch_kron_tile<P, double, EPI_ZMINUS, 16, 16>(a, st);
+}
+
+iga_status op_apply_bands(iga_ctx* ctx, int P, int nx, int ny, const double* K, const double* M, double2 c,
+                          const double2* x, double2* y, const double2* z, int epi) {
+  OpArgs<double> a{};
+  a.nx = nx;
+  a.ny = ny;
+  a.K = K;
+  a.M = M;
+  a.c = c;
+  a.x = x;
+  a.y = y;
+  a.z = z;
+  switch (P) {
+    case 1: launch_bands<1>(ctx, a, epi); break;
+    case 2: launch_bands<2>(ctx, a, epi); break;
+    case 3: launch_bands<3>(ctx, a, epi); break;
+    case 4: launch_bands<4>(ctx, a, epi); break;
+    case 5: launch_bands<5>(ctx, a, epi); break;
+    default: return set_err(ctx, IGA_E_INVALID, "band width");
+  }
+  CKL();
+  return IGA_OK;
+}
+
+// ------------------------------------------------------------------ tile autotuner
+// For constant k in 2D the operator kernel has three tile shapes (32x16,
+// 16x16, 32x8 outputs per block).  At setup every level with at least 64^2
+// dofs times each shape on the level's own operator (CUDA events, 2 warm-up +
+// 5 timed launches) in FP64 and FP32 and keeps the fastest.  Results are
+// cached per (p, precision, n_x) for the whole process, so batched instances
+// of equal size are tuned once.
+#include <map>
+#include <mutex>
+#include <tuple>
+
+static std::map<std::tuple<int, int, int>, int> g_tile_cache;
+static std::mutex g_tile_mu;
+
+template <typename T>
+static iga_status tune_level(iga_ctx* ctx, int l, int slot) {
+  using C = typename cplx<T>::t;
+  LevelData& L = ctx->lv[l];
+  auto key = std::make_tuple(ctx->p, slot, L.nx);
+  {
+    std::lock_guard<std::mutex> lock(g_tile_mu);
+    auto it = g_tile_cache.find(key);
+    if (it != g_tile_cache.end()) { ctx->tile[l][slot] = it->second; return IGA_OK; }
+  }
+  C* x = (C*)(slot == 0 ? (void*)L.vb : (void*)L.fb);
+  C* y = (C*)(slot == 0 ? (void*)L.vx : (void*)L.fx);
+  CK(cudaMemsetAsync(x, 0, sizeof(C) * L.n, ctx->st));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_tile = 0;
+  for (int t = 0; t < 3; ++t) {
+    ctx->tile[l][slot] = t;
+    for (int w = 0; w < 2; ++w) TRY(op_apply<T>(ctx, l, OP_MB, x, y, nullptr, EPI_Y, nullptr, 0.0));
+    CK(cudaEventRecord(e0, ctx->st));
+    for (int r = 0; r < 5; ++r) TRY(op_apply<T>(ctx, l, OP_MB, x, y, nullptr, EPI_Y, nullptr, 0.0));
+    CK(cudaEventRecord(e1, ctx->st));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best) { best = ms; best_tile = t; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->tile[l][slot] = best_tile;
+  std::lock_guard<std::mutex> lock(g_tile_mu);
+  g_tile_cache[key] = best_tile;
+  return IGA_OK;
+}
+
+iga_status autotune_tiles(iga_ctx* ctx) {
+  if (ctx->dim != 2 || ctx->vark) return IGA_OK;
+  for (int l = 0; l < ctx->L; ++l) {
+    if (ctx->lv[l].nx < 64) continue;
+    TRY(tune_level<double>(ctx, l, 0));
+    TRY(tune_level<float>(ctx, l, 1));
+  }
+  return IGA_OK;
+}
+
+extern "C" int iga_tile_choice(const iga_ctx* ctx, int level, int precision) {
+  if (!ctx || level < 0 || level >= ctx->L || precision < 0 || precision > 1) return -2;
+  return ctx->tile[level][precision];
 }

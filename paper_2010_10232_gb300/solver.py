@@ -219,6 +219,35 @@ class Helmholtz:
         return x, iters.value, hist[:iters.value + 1], tr.value, st
 
 
+def solve_batched(contexts, rhs, x=None, tol=1e-7, maxit=100, stream=None):
+    """Solve every contexts[b] for the right-hand sides rhs[b] (tensor of shape
+    (nrhs_b, n_b), complex128, CUDA) in one graph launch.  Returns (x list,
+    iterations list of arrays, status list of arrays, overall status)."""
+    L = _ffi.lib()
+    nb = len(contexts)
+    rhs = [r.reshape(-1, c.n).contiguous() for r, c in zip(rhs, contexts)]
+    if x is None:
+        x = [torch.zeros_like(r) for r in rhs]
+    nr = [int(r.shape[0]) for r in rhs]
+    tot = sum(nr)
+    H = (C.c_void_p * nb)(*[c._h.value for c in contexts])
+    R = (C.c_void_p * nb)(*[_ptr(r) for r in rhs])
+    X = (C.c_void_p * nb)(*[_ptr(v) for v in x])
+    N = (C.c_int * nb)(*nr)
+    it = (C.c_int * tot)()
+    stt = (C.c_int * tot)()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    rc = L.iga_solve_batched(H, nb, R, X, N, float(tol), int(maxit), it, stt, C.c_void_p(s.cuda_stream))
+    if rc < 0:
+        raise IgaError(rc, contexts[0]._L.iga_last_error(contexts[0]._h).decode())
+    its, sts, k = [], [], 0
+    for n_r in nr:
+        its.append(np.array(it[k:k + n_r]))
+        sts.append(np.array(stt[k:k + n_r]))
+        k += n_r
+    return x, its, sts, rc
+
+
 def from_problem(pr, **kw) -> Helmholtz:
     """Build a context from a workloads.Problem-like description."""
     kf = pr.kfield

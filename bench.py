@@ -277,6 +277,7 @@ def gpu_arm(args):
     except Exception as e:       # report, do not hide
         big["error"] = str(e)[:200]
 
+    forms = {} if (args.no_forms or ws > 1) else other_forms(h, f, x, stream, flush, ws)
     if rank != 0:
         return
     cpu = None
@@ -307,11 +308,98 @@ def gpu_arm(args):
                      "probe_fma_tflops": probe, "launch_us": t_apply * 1e6,
                      "hbm_gbs": apply_bytes / t_apply / 1e9},
         "out_of_l2": dict(big, hbm_peak_gbs=peaks.get("hbm_gbs"), peak_source=src),
+        "forms": forms,
         "clocks": clk.summary(),
     }
     if cpu is not None:
         line["cpu_baseline"] = cpu
     print(json.dumps(line))
+
+
+def _time_solves(h, f, x, stream, flush, reps):
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for k in range(reps):
+        flush.fill_(k & 255)
+        ev[k][0].record(stream)
+        _, it, hist, tr, st = h.solve(f, x=x)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in ev) / reps, it, tr
+
+
+def other_forms(h64, f, x, stream, flush, ws):
+    """Mixed precision, learned correction and the batched 64-instance launch,
+    each with its error against the oracle's direct FP64 solution."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2010_10232_gb300.solver import from_problem, solve_batched
+    out = {}
+    pr = W.config2(k=K_WAVE, p=P_DEG)
+    ref = None
+    try:
+        from oracle.solver import Solver, rel_err      # error report only (CPU, untimed)
+        s_or = Solver(pr)
+        ref = s_or.direct(s_or.load())
+    except Exception as e:
+        out["oracle_error"] = str(e)[:200]
+    err = (lambda u: float(np.linalg.norm(u - ref) / np.linalg.norm(ref))) if ref is not None else (lambda u: None)
+    def tight(h):
+        """error of the same form solved to a relative residual of 1e-10"""
+        xt = h.vec()
+        _, it_t, _, tr_t, st_t = h.solve(f, x=xt, tol=1e-10, maxit=300)
+        return {"rel_err_vs_oracle_direct": err(xt.cpu().numpy()), "iterations": it_t, "status": st_t}
+
+    out["plain_fp64"] = {"rel_err_vs_oracle_direct": err(x.cpu().numpy()), "tol_1e-10": tight(h64)}
+    try:
+        hm = from_problem(pr, precision=1)
+        xm = hm.vec()
+        hm.solve(f, x=xm)
+        ms, it, tr = _time_solves(hm, f, xm, stream, flush, 5)
+        out["mixed_fp32_vcycle"] = {"ms": ms, "iterations": it, "true_res": tr,
+                                    "rel_err_vs_oracle_direct": err(xm.cpu().numpy()), "tol_1e-10": tight(hm)}
+        wpath = os.path.join(ROOT, "paper_2010_10232_gb300", "weights", "cslp_correction.npz")
+        if os.path.exists(wpath):
+            from paper_2010_10232_gb300.learned import Net
+            d = np.load(wpath)
+            net = Net(seed=0)
+            net.set_params(d["params"])
+            hm.attach(net, float(d["gamma"]))
+            hm.solve(f, x=xm)
+            ms, it, tr = _time_solves(hm, f, xm, stream, flush, 5)
+            out["learned_correction"] = {"ms": ms, "iterations": it, "true_res": tr,
+                                         "rel_err_vs_oracle_direct": err(xm.cpu().numpy()), "tol_1e-10": tight(hm)}
+            hm.attach(None)
+        del hm
+    except Exception as e:
+        out["mixed_error"] = str(e)[:200]
+    try:
+        inst = W.config4(64)
+        ctxs, rhs = [], []
+        for prb, nr in inst:
+            c = from_problem(prb, precision=1)
+            ctxs.append(c)
+            rhs.append(torch.stack([c.point_source(*s_) for s_ in prb.sources]))
+        solve_batched(ctxs, rhs)                    # warm-up (also builds every workspace)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.fill_(1)
+        e0.record(stream)
+        xs, its, sts, rc = solve_batched(ctxs, rhs)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tot = sum(len(r) for r in rhs)
+        ms = e0.elapsed_time(e1)
+        allit = np.concatenate(its)
+        out["batched_cfg4"] = {"instances": len(ctxs), "rhs": int(tot), "ms_total": ms,
+                               "ms_per_solve": ms / tot, "dofs": int(sum(c.n for c in ctxs)),
+                               "iterations_mean": float(allit.mean()), "iterations_max": int(allit.max()),
+                               "status": int(rc), "note": "one CUDA-graph launch, FP32 V-cycle, FP64 FGMRES"}
+        del ctxs, rhs, xs
+    except Exception as e:
+        out["batched_error"] = str(e)[:200]
+    return out
 
 
 def main():
@@ -321,6 +409,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-forms", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)

@@ -72,6 +72,10 @@ typedef struct {
                               implies it)                                                 */
   int skip_deflation;      /* 1: operator / V-cycle context only (no Z, E); deflation and
                               solve entry points then return IGA_E_INVALID                 */
+  int arnoldi;             /* 0 (default): modified Gram-Schmidt, all projections of an
+                              iteration in one cooperative launch (grid barriers);
+                              1: classical Gram-Schmidt with one reorthogonalisation
+                              (CGS2, barrier-free; batched solves always use it)        */
   int host_loop;           /* 0 (default): the GMRES loop runs on the device as a CUDA
                               graph with a WHILE conditional node; 1: the host launches
                               each iteration and reads the convergence flag (profiling)   */
@@ -197,7 +201,9 @@ int iga_tile_choice(const iga_ctx* ctx, int level, int precision);
    iters and status (HOST, sum(nrhs) entries, instance-major; status may be
    NULL) receive per right-hand side the iteration count and IGA_OK /
    IGA_NOT_CONVERGED / error.  Contexts must be distinct, on one device, built
-   with deflation.  Work is launched on `stream`; the call synchronises.
+   with deflation.  Arnoldi runs as CGS2 (barrier-free) in this entry point so
+   that the instances' kernels can overlap.  Work is launched on `stream`; the
+   call synchronises.
    Returns the worst per-right-hand-side status. */
 iga_status iga_solve_batched(iga_ctx* const* ctxs, int nb, const iga_c128* const* rhs, iga_c128* const* x,
                              const int* nrhs, double tol, int maxit, int* iters, int* status, void* stream);
@@ -234,8 +240,9 @@ iga_status iga_net_train_step(iga_net* net, const void* x, const float* t, int B
                               float* loss_host, void* stream);
 /* Attach (or detach with NULL) a network to a 2D context in precision 1. */
 iga_status iga_attach_net(iga_ctx* ctx, iga_net* net, double gamma);
-/* Training pair from a preconditioner input v (DEVICE, n complex128):
-   rt = v - M_beta V(v) and e ~ M_beta^{-1} rt by `cycles` FP32 V-cycles. */
+/* Training pair from a preconditioner input v (DEVICE, n complex128) by the
+   error propagation of the FP32 V-cycle V: e = V(v), then `cycles` times
+   e <- e - V(M_beta e); rt = M_beta e (so e = M_beta^{-1} rt exactly). */
 iga_status iga_precond_pair(iga_ctx* ctx, const iga_c128* v, iga_c128* rt, iga_c128* e, int cycles);
 /* Crop [y0, y0+Hc) x [x0, x0+Wc) of rt (and e) into a network input X (DEVICE
    bf16 [Hc][Wc][16]) and target T = e / (RMS(rt) gamma) (DEVICE FP32

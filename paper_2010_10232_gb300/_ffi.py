@@ -34,6 +34,7 @@ class IgaParams(C.Structure):
         ("precision", C.c_int),
         ("flexible", C.c_int),
         ("skip_deflation", C.c_int),
+        ("arnoldi", C.c_int),
         ("host_loop", C.c_int),
         ("stream", C.c_void_p),
     ]

@@ -33,6 +33,7 @@ void iga_default_params(iga_params* prm) {
   d.flexible = 0;
   d.skip_deflation = 0;
   d.host_loop = 0;
+  d.arnoldi = 0;
   d.stream = nullptr;
   *prm = d;
 }
@@ -83,6 +84,7 @@ iga_status iga_setup(const iga_params* prm, iga_ctx** out) {
   if (P.n_lines < 0 || P.n_lines > IGA_MAX_LINES || (P.n_lines > 0 && P.dim != 2)) return IGA_E_INVALID;
   if (!(P.omega > 0.0) || P.nu_pre < 0 || P.nu_post < 0 || P.n_vcycles < 1) return IGA_E_INVALID;
   if (P.precision < 0 || P.precision > 1) return IGA_E_INVALID;
+  if (P.arnoldi < 0 || P.arnoldi > 1) return IGA_E_INVALID;
   for (int l = 0; l <= P.n_lines; ++l)
     if (!std::isfinite(P.k_values[l]) || P.k_values[l] < 0.0) return IGA_E_INVALID;
   iga_ctx* ctx = new (std::nothrow) iga_ctx();
@@ -100,6 +102,7 @@ iga_status iga_setup(const iga_params* prm, iga_ctx** out) {
   ctx->k2const = P.k_values[0] * P.k_values[0];
   ctx->sig = make_double2(P.beta1, -P.beta2);
   ctx->use_graph = P.host_loop == 0;
+  ctx->arnoldi_cgs = P.arnoldi == 1;
   for (int l = 0; l < IGA_MAX_LEVELS; ++l) ctx->tile[l][0] = ctx->tile[l][1] = -1;
   iga_status s = IGA_OK;
   do {

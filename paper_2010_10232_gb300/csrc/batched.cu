@@ -80,6 +80,13 @@ extern "C" iga_status iga_solve_batched(iga_ctx* const* ctxs, int nb, const iga_
   iga_ctx* ctx = ctxs[0];   // error reporting and the record buffer
   for (int b = 0; b < nb; ++b) {
     bool flex = ctxs[b]->prm.precision != 0 || ctxs[b]->prm.flexible != 0;
+    if (!ctxs[b]->arnoldi_cgs) {       // the single-solve graph (if any) used the other Arnoldi form
+      ctxs[b]->arnoldi_cgs = true;
+      if (ctxs[b]->gexec) cudaGraphExecDestroy(ctxs[b]->gexec);
+      if (ctxs[b]->graph) cudaGraphDestroy(ctxs[b]->graph);
+      ctxs[b]->gexec = nullptr;
+      ctxs[b]->graph = nullptr;
+    }
     iga_status s = kry_prepare(ctxs[b], maxit, flex);
     if (s != IGA_OK) return s;
   }

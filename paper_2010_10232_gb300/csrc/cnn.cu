@@ -567,19 +567,44 @@ __global__ void k_net_target(const double2* e, int nx, int ny, int x0, int y0, i
   T[2 * i + 1] = b;
 }
 
-// RMS of a complex vector into *out (one block; used once per application)
+__global__ void k_sub_f2(float2* a, const float2* b, size_t n) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < n) a[i] = a[i] - b[i];
+}
+
+// RMS of a complex vector: per-block partial sums of |r_i|^2 into out[2 + b],
+// then one block adds them in a fixed order into out[0].  out holds
+// 2 + IGA_RMS_BLOCKS doubles.
+constexpr int IGA_RMS_BLOCKS = 256;
 template <typename C>
-__global__ void k_rms(const C* r, size_t n, double* out) {
+__global__ void k_rms_part(const C* r, size_t n, double* out) {
   __shared__ double s[256];
   double a = 0.0;
-  for (size_t i = threadIdx.x; i < n; i += blockDim.x) a += (double)r[i].x * r[i].x + (double)r[i].y * r[i].y;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    a += (double)r[i].x * r[i].x + (double)r[i].y * r[i].y;
   s[threadIdx.x] = a;
   __syncthreads();
   for (int k = 128; k > 0; k >>= 1) {
     if (threadIdx.x < k) s[threadIdx.x] += s[threadIdx.x + k];
     __syncthreads();
   }
-  if (threadIdx.x == 0) *out = sqrt(s[0] / (double)n);
+  if (threadIdx.x == 0) out[2 + blockIdx.x] = s[0];
+}
+__global__ void k_rms_finish(size_t n, int nb, double* out) {
+  __shared__ double s[256];
+  s[threadIdx.x] = threadIdx.x < nb ? out[2 + threadIdx.x] : 0.0;
+  __syncthreads();
+  for (int k = 128; k > 0; k >>= 1) {
+    if (threadIdx.x < k) s[threadIdx.x] += s[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = sqrt(s[0] / (double)n);
+}
+template <typename C>
+static void launch_rms(const C* r, size_t n, double* out, cudaStream_t st) {
+  int nb = (int)std::max<size_t>(1, std::min<size_t>(IGA_RMS_BLOCKS, cdiv(n, 2048)));
+  k_rms_part<C><<<nb, 256, 0, st>>>(r, n, out); iga_count_launch();
+  k_rms_finish<<<1, 256, 0, st>>>(n, nb, out); iga_count_launch();
 }
 
 // z += gamma * s * y  if every output is finite (else z stays the plain V-cycle result)
@@ -603,7 +628,7 @@ iga_status net_correct(iga_ctx* ctx, const float2* r, float2* z) {
   TRY(net_workspace(n, 1, H, W));
   float2* rt = L.fr;
   TRY(op_apply<float>(ctx, 0, OP_MB, z, rt, r, EPI_ZMINUS, nullptr, 0.0));
-  k_rms<float2><<<1, 256, 0, st>>>(rt, L.n, ctx->net_rms); iga_count_launch();
+  launch_rms<float2>(rt, L.n, ctx->net_rms, st);
   k_net_pack<float2><<<cdiv(L.n, 256), 256, 0, st>>>(rt, W, H, 0, 0, H, W, L.knots, ctx->p, L.n_el, ctx->kf,
                                                       ctx->net_rms, n->act[0]); iga_count_launch();
   net_forward(n, 1, H, W, st);
@@ -623,7 +648,7 @@ iga_status iga_attach_net(iga_ctx* ctx, iga_net* net, double gamma) {
   if (net && (ctx->prm.precision != 1 || ctx->dim != 2))
     return set_err(ctx, IGA_E_INVALID, "the learned correction needs a 2D context in precision 1");
   if (!ctx->net_rms) {
-    ctx->net_rms = dalloc<double>(ctx, 2);
+    ctx->net_rms = dalloc<double>(ctx, 2 + IGA_RMS_BLOCKS);
     ctx->net_bad = dalloc<int>(ctx, 1);
     if (!ctx->net_rms || !ctx->net_bad) return set_err(ctx, IGA_E_OOM, "net scalars");
   }
@@ -641,23 +666,29 @@ iga_status iga_attach_net(iga_ctx* ctx, iga_net* net, double gamma) {
   return IGA_OK;
 }
 
-// Training pair from a preconditioner input v (DEVICE, n complex128):
-// z = V(v) (FP32 V-cycle), rt = v - M_beta z and e ~ M_beta^{-1} rt by `cycles`
-// further FP32 V-cycles (rt, e: DEVICE complex128).
+// Training pair from a preconditioner input v (DEVICE, n complex128), built
+// from the error propagation of the FP32 V-cycle V (no inverse needed):
+// e_0 = V(v), then `cycles` times e <- e - V(M_beta e); rt = M_beta e.  The
+// network's task NN(rt) ~ e is then exactly the inference-time task (the error
+// M_beta^{-1} rt left by a V-cycle).  rt, e: DEVICE complex128.
 iga_status iga_precond_pair(iga_ctx* ctx, const iga_c128* v, iga_c128* rt, iga_c128* e, int cycles) {
   if (!ctx || !v || !rt || !e || cycles < 1) return IGA_E_INVALID;
   LevelData& L = ctx->lv[0];
   size_t n = L.n;
-  launch_convert_d2f((const double2*)v, ctx->fin, n, ctx->st);
-  TRY(mg_vcycle<float>(ctx, ctx->fin, ctx->fout));
-  TRY(op_apply<float>(ctx, 0, OP_MB, ctx->fout, L.fr, ctx->fin, EPI_ZMINUS, nullptr, 0.0));   // fr = v - M z
-  launch_convert_f2d(L.fr, (double2*)rt, n, ctx->st);
-  int saved = ctx->prm.n_vcycles;
-  ctx->prm.n_vcycles = cycles;
-  iga_status s = mg_vcycle<float>(ctx, L.fr, ctx->fout);
-  ctx->prm.n_vcycles = saved;
-  TRY(s);
-  launch_convert_f2d(ctx->fout, (double2*)e, n, ctx->st);
+  cudaStream_t st = ctx->st;
+  launch_convert_d2f((const double2*)v, ctx->fin, n, st);
+  TRY(mg_vcycle<float>(ctx, ctx->fin, ctx->fout));            // e_0 in fout
+  float2* ecur = ctx->fout;
+  float2* r = ctx->fin;
+  float2* z = L.fr;
+  for (int c = 0; c < cycles; ++c) {
+    TRY(op_apply<float>(ctx, 0, OP_MB, ecur, r, nullptr, EPI_Y, nullptr, 0.0));   // r = M e
+    TRY(mg_vcycle<float>(ctx, r, z));                                              // z = V(r)
+    k_sub_f2<<<cdiv(n, 256), 256, 0, st>>>(ecur, z, n); iga_count_launch();        // e -= z
+  }
+  TRY(op_apply<float>(ctx, 0, OP_MB, ecur, r, nullptr, EPI_Y, nullptr, 0.0));     // rt = M e
+  launch_convert_f2d(r, (double2*)rt, n, st);
+  launch_convert_f2d(ecur, (double2*)e, n, st);
   CKL();
   return IGA_OK;
 }
@@ -670,11 +701,11 @@ iga_status iga_net_pack(iga_ctx* ctx, const iga_c128* rt, const iga_c128* e, int
   if (!ctx || !rt || !X || Hc < 1 || Wc < 1 || x0 < 0 || y0 < 0 || ctx->dim != 2) return IGA_E_INVALID;
   LevelData& L = ctx->lv[0];
   if (!ctx->net_rms) {
-    ctx->net_rms = dalloc<double>(ctx, 2);
+    ctx->net_rms = dalloc<double>(ctx, 2 + IGA_RMS_BLOCKS);
     ctx->net_bad = dalloc<int>(ctx, 1);
     if (!ctx->net_rms || !ctx->net_bad) return set_err(ctx, IGA_E_OOM, "net scalars");
   }
-  k_rms<double2><<<1, 256, 0, ctx->st>>>((const double2*)rt, L.n, ctx->net_rms); iga_count_launch();
+  launch_rms<double2>((const double2*)rt, L.n, ctx->net_rms, ctx->st);
   size_t px = (size_t)Hc * Wc;
   k_net_pack<double2><<<cdiv(px, 256), 256, 0, ctx->st>>>((const double2*)rt, L.nx, L.ny, x0, y0, Hc, Wc, L.knots,
                                                           ctx->p, L.n_el, ctx->kf, ctx->net_rms, (bf16*)X); iga_count_launch();

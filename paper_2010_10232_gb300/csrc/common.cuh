@@ -127,6 +127,7 @@ struct iga_ctx {
   double2* ce2 = nullptr;
   int e_refine = 2;                  // iterative refinement steps of the FDM coarse solve
   float* fdmVf = nullptr;            // FP32 copy of the eigenvectors
+  float* fdmVtf = nullptr;           // and of their transpose
   double* kcb = nullptr;             // banded 1D coarse matrices (half width (p+4)/2)
   double* mcb = nullptr;
   float2* cwf = nullptr;             // FP32 transform scratch
@@ -162,6 +163,10 @@ struct iga_ctx {
   int* kint = nullptr;               // [0] j, [1] barrier timeout
   unsigned* kbar = nullptr;          // grid barrier state
   int coop_blocks = 0;
+  bool arnoldi_cgs = false;          // CGS2 Arnoldi (no grid barrier) instead of cooperative MGS
+  int cgs_blocks = 0;
+  double* cgs_part = nullptr;        // [cgs_blocks][2 (maxit+1)] partial projections
+  double2* cgs_h = nullptr;          // current projections
   bool use_graph = true;
   cudaStream_t cap_stream = nullptr;
   cudaGraph_t graph = nullptr;

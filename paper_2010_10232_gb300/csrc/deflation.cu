@@ -281,97 +281,9 @@ __global__ void k_rayleigh(const double* V, const double* Kc, const double* Mc, 
   lam[k] = num / den;
 }
 
-// r = t - E s with E = Mc (x) Kc + Kc (x) Mc - k^2 Mc (x) Mc (2D) or Kc - k^2 Mc
-// (1D), using the banded 1D coarse matrices (half bandwidth bw).
-__global__ void k_e_residual(const double* Kc, const double* Mc, int mx, int my, int bw, double k2,
-                             const double2* s, const double2* t, double2* r) {
-  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (i >= (size_t)mx * my) return;
-  int iy = (int)(i / mx), ix = (int)(i - (size_t)iy * mx);
-  double2 acc = make_double2(0.0, 0.0);
-  if (my == 1) {
-    for (int b = max(0, ix - bw); b <= min(mx - 1, ix + bw); ++b)
-      acc = cfma(Kc[(size_t)ix * mx + b] - k2 * Mc[(size_t)ix * mx + b], s[b], acc);
-  } else {
-    for (int a = max(0, iy - bw); a <= min(my - 1, iy + bw); ++a) {
-      double my_ = Mc[(size_t)iy * mx + a], ky_ = Kc[(size_t)iy * mx + a];
-      double2 rk = make_double2(0.0, 0.0), rm = make_double2(0.0, 0.0);
-      for (int b = max(0, ix - bw); b <= min(mx - 1, ix + bw); ++b) {
-        double2 v = s[(size_t)a * mx + b];
-        rk = cfma(Kc[(size_t)ix * mx + b], v, rk);
-        rm = cfma(Mc[(size_t)ix * mx + b], v, rm);
-      }
-      acc = acc + my_ * rk + (ky_ - k2 * my_) * rm;
-    }
-  }
-  r[i] = t[i] - acc;
-}
 __global__ void k_axpy_c(double2* y, const double2* x, size_t n) {
   size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (i < n) y[i] = y[i] + x[i];
-}
-
-// ------------------------------------------------------------------ FDM apply GEMMs
-// out[i][j] = sum_k op(R)[i][k] X[k][j]  (LEFT)   or  sum_k X[i][k] op(R)[k][j]  (RIGHT)
-// R real m x m (row-major), X complex rows x cols.  TRANS: op(R) = R^T.
-// With DIVIDE the result is divided by lam_y[i] + lam_x[j] - k2 (lam_y = 0 in 1D).
-template <bool LEFT, bool TRANS, bool DIVIDE>
-__global__ void __launch_bounds__(128) k_fdm_gemm(const double* R, const double2* X, double2* out, int rows, int cols,
-                                                 const double* lam_y, const double* lam_x, double k2) {
-  // 8 x 16 output tile per block of 8 x 16 threads; K in steps of 16.
-  constexpr int TY = 8, TX = 16, TK = 16;
-  __shared__ double Rs[TK][TK + 1];
-  __shared__ double2 Xs[TK][TX + 1];
-  int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  int i = blockIdx.y * TY + ty, j = blockIdx.x * TX + tx;
-  int K = LEFT ? rows : cols;
-  double2 acc = make_double2(0.0, 0.0);
-  for (int k0 = 0; k0 < K; k0 += TK) {
-    if (LEFT) {
-      // Rs[r][kk] = op(R)[blockIdx.y*TY + r][k0 + kk] for r < TY
-      for (int t = threadIdx.x; t < TY * TK; t += 128) {
-        int r = t / TK, kk = t - r * TK;
-        int ri = blockIdx.y * TY + r, rk = k0 + kk;
-        double v = 0.0;
-        if (ri < rows && rk < K) v = TRANS ? R[(size_t)rk * rows + ri] : R[(size_t)ri * rows + rk];
-        Rs[r][kk] = v;
-      }
-      // Xs[kk][c] = X[k0 + kk][blockIdx.x*TX + c]
-      for (int t = threadIdx.x; t < TK * TX; t += 128) {
-        int kk = t / TX, c = t - kk * TX;
-        int xk = k0 + kk, xj = blockIdx.x * TX + c;
-        Xs[kk][c] = (xk < K && xj < cols) ? X[(size_t)xk * cols + xj] : make_double2(0.0, 0.0);
-      }
-      __syncthreads();
-#pragma unroll
-      for (int kk = 0; kk < TK; ++kk) acc = cfma(Rs[ty][kk], Xs[kk][tx], acc);
-    } else {
-      // Xs[r][kk] = X[blockIdx.y*TY + r][k0 + kk] for r < TY ; Rs[kk][c] = op(R)[k0 + kk][blockIdx.x*TX + c]
-      for (int t = threadIdx.x; t < TY * TK; t += 128) {
-        int r = t / TK, kk = t - r * TK;
-        int xi = blockIdx.y * TY + r, xk = k0 + kk;
-        Xs[r][kk] = (xi < rows && xk < K) ? X[(size_t)xi * cols + xk] : make_double2(0.0, 0.0);
-      }
-      for (int t = threadIdx.x; t < TK * TX; t += 128) {
-        int kk = t / TX, c = t - kk * TX;
-        int rk = k0 + kk, rj = blockIdx.x * TX + c;
-        double v = 0.0;
-        if (rk < K && rj < cols) v = TRANS ? R[(size_t)rj * cols + rk] : R[(size_t)rk * cols + rj];
-        Rs[kk][c] = v;
-      }
-      __syncthreads();
-#pragma unroll
-      for (int kk = 0; kk < TK; ++kk) acc = cfma(Rs[kk][tx], Xs[ty][kk], acc);
-    }
-    __syncthreads();
-  }
-  if (i < rows && j < cols) {
-    if (DIVIDE) {
-      double d = (lam_y ? lam_y[i] : 0.0) + lam_x[j] - k2;
-      acc = make_double2(acc.x / d, acc.y / d);
-    }
-    out[(size_t)i * cols + j] = acc;
-  }
 }
 
 // FP32 variant of the FDM transform for the refined coarse solve: X is double2
@@ -382,49 +294,50 @@ __device__ __forceinline__ float2 ld_f2(const float2* p) { return *p; }
 __device__ __forceinline__ void st_c(double2* p, float2 v) { *p = tod(v); }
 __device__ __forceinline__ void st_c(float2* p, float2 v) { *p = v; }
 
-template <bool LEFT, bool TRANS, bool DIVIDE, typename XT, typename OT>
+// out = R X (LEFT) or X R (RIGHT) with R a row-major m x m FP32 matrix (V or
+// V^T, both stored), so every operand tile is read with unit stride.
+template <bool LEFT, bool DIVIDE, typename XT, typename OT>
 __global__ void __launch_bounds__(128) k_fdm_gemm32(const float* R, const XT* X, OT* out, int rows, int cols,
                                                    const double* lam_y, const double* lam_x, double k2) {
-  constexpr int TY = 8, TX = 16, TK = 16;
-  __shared__ float Rs[TK][TK + 1];
-  __shared__ float2 Xs[TK][TX + 1];
+  constexpr int TY = 8, TX = 16, TK = 64;
+  // LEFT: Rs[TY][TK] and Xs[TK][TX]; RIGHT: Xs[TY][TK] and Rs[TK][TX]
+  __shared__ float Rsm[TK * (TX + 1)];
+  __shared__ float2 Xsm[TK * (TX + 1)];
   int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   int i = blockIdx.y * TY + ty, j = blockIdx.x * TX + tx;
   int K = LEFT ? rows : cols;
   float2 acc = make_float2(0.f, 0.f);
   for (int k0 = 0; k0 < K; k0 += TK) {
     if (LEFT) {
+      // Rs[r][kk] = R[row0 + r][k0 + kk]  (kk fastest: coalesced)
       for (int t = threadIdx.x; t < TY * TK; t += 128) {
         int r = t / TK, kk = t - r * TK;
         int ri = blockIdx.y * TY + r, rk = k0 + kk;
-        float v = 0.f;
-        if (ri < rows && rk < K) v = TRANS ? R[(size_t)rk * rows + ri] : R[(size_t)ri * rows + rk];
-        Rs[r][kk] = v;
+        Rsm[r * (TK + 1) + kk] = (ri < rows && rk < K) ? R[(size_t)ri * rows + rk] : 0.f;
       }
       for (int t = threadIdx.x; t < TK * TX; t += 128) {
         int kk = t / TX, c = t - kk * TX;
         int xk = k0 + kk, xj = blockIdx.x * TX + c;
-        Xs[kk][c] = (xk < K && xj < cols) ? ld_f2(X + (size_t)xk * cols + xj) : make_float2(0.f, 0.f);
+        Xsm[kk * (TX + 1) + c] = (xk < K && xj < cols) ? ld_f2(X + (size_t)xk * cols + xj) : make_float2(0.f, 0.f);
       }
       __syncthreads();
 #pragma unroll
-      for (int kk = 0; kk < TK; ++kk) acc = cfma(Rs[ty][kk], Xs[kk][tx], acc);
+      for (int kk = 0; kk < TK; ++kk) acc = cfma(Rsm[ty * (TK + 1) + kk], Xsm[kk * (TX + 1) + tx], acc);
     } else {
       for (int t = threadIdx.x; t < TY * TK; t += 128) {
         int r = t / TK, kk = t - r * TK;
         int xi = blockIdx.y * TY + r, xk = k0 + kk;
-        Xs[r][kk] = (xi < rows && xk < K) ? ld_f2(X + (size_t)xi * cols + xk) : make_float2(0.f, 0.f);
+        Xsm[r * (TK + 1) + kk] = (xi < rows && xk < K) ? ld_f2(X + (size_t)xi * cols + xk) : make_float2(0.f, 0.f);
       }
+      // Rs[kk][c] = R[k0 + kk][col0 + c]  (c fastest: coalesced)
       for (int t = threadIdx.x; t < TK * TX; t += 128) {
         int kk = t / TX, c = t - kk * TX;
         int rk = k0 + kk, rj = blockIdx.x * TX + c;
-        float v = 0.f;
-        if (rk < K && rj < cols) v = TRANS ? R[(size_t)rj * cols + rk] : R[(size_t)rk * cols + rj];
-        Rs[kk][c] = v;
+        Rsm[kk * (TX + 1) + c] = (rk < K && rj < cols) ? R[(size_t)rk * cols + rj] : 0.f;
       }
       __syncthreads();
 #pragma unroll
-      for (int kk = 0; kk < TK; ++kk) acc = cfma(Rs[kk][tx], Xs[ty][kk], acc);
+      for (int kk = 0; kk < TK; ++kk) acc = cfma(Rsm[kk * (TX + 1) + tx], Xsm[ty * (TK + 1) + kk], acc);
     }
     __syncthreads();
   }
@@ -435,6 +348,11 @@ __global__ void __launch_bounds__(128) k_fdm_gemm32(const float* R, const XT* X,
     }
     st_c(out + (size_t)i * cols + j, acc);
   }
+}
+
+__global__ void k_transpose_f(const float* A, float* B, int n) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < n * n) { int i = idx / n, j = idx - i * n; B[(size_t)j * n + i] = A[idx]; }
 }
 
 // band extraction of a dense (banded) matrix: B[i][d + bw] = A[i][i + d]
@@ -507,13 +425,16 @@ static iga_status fdm_setup(iga_ctx* ctx) {
   k_trsm_lower_t<<<cdiv(n, 64), 64, 0, st>>>(Lm, W, ctx->fdmV, n); iga_count_launch();
   k_rayleigh<<<cdiv(n, 64), 64, 0, st>>>(ctx->fdmV, ctx->kc, ctx->mc, n, (ctx->p + 4) / 2 + 1, ctx->fdmL); iga_count_launch();
   ctx->fdmVf = dalloc<float>(ctx, (size_t)n * n);
+  ctx->fdmVtf = dalloc<float>(ctx, (size_t)n * n);
   const int bw = (ctx->p + 4) / 2;
   ctx->kcb = dalloc<double>(ctx, (size_t)n * (2 * bw + 1));
   ctx->mcb = dalloc<double>(ctx, (size_t)n * (2 * bw + 1));
   ctx->cwf = dalloc<float2>(ctx, ctx->m);
   ctx->cwf2 = dalloc<float2>(ctx, ctx->m);
-  if (!ctx->fdmVf || !ctx->kcb || !ctx->mcb || !ctx->cwf || !ctx->cwf2) return set_err(ctx, IGA_E_OOM, "fdm32 alloc");
+  if (!ctx->fdmVf || !ctx->fdmVtf || !ctx->kcb || !ctx->mcb || !ctx->cwf || !ctx->cwf2)
+    return set_err(ctx, IGA_E_OOM, "fdm32 alloc");
   k_d2f_vec<<<cdiv((size_t)n * n, 256), 256, 0, st>>>(ctx->fdmV, ctx->fdmVf, (size_t)n * n); iga_count_launch();
+  k_transpose_f<<<cdiv((size_t)n * n, 256), 256, 0, st>>>(ctx->fdmVf, ctx->fdmVtf, n); iga_count_launch();
   k_dense_to_band<<<cdiv((size_t)n * (2 * bw + 1), 128), 128, 0, st>>>(ctx->kc, n, bw, ctx->kcb); iga_count_launch();
   k_dense_to_band<<<cdiv((size_t)n * (2 * bw + 1), 128), 128, 0, st>>>(ctx->mc, n, bw, ctx->mcb); iga_count_launch();
   CKL();
@@ -563,25 +484,37 @@ iga_status defl_z(iga_ctx* ctx, const double2* c, double2* x) {
 
 // s ~ E^{-1} t by fast diagonalisation with FP32 transforms (constant k); the
 // FP32 intermediates live in cwf, cwf2.
-static iga_status fdm_solve32(iga_ctx* ctx, const double2* t, double2* s) {
+static iga_status fdm_solve32(iga_ctx* ctx, const double2* t, double2* s, bool accumulate = false) {
   const int mx = ctx->mx;
   const double k2 = ctx->k2const;
+  const float* V = ctx->fdmVf;
+  const float* Vt = ctx->fdmVtf;
   dim3 blk(128);
   if (ctx->dim == 1) {
+    // s^T = ((t^T V) / d) V^T with t as a 1 x m row
     dim3 g(cdiv(mx, 16), 1);
-    k_fdm_gemm32<false, false, true, double2, float2><<<g, blk, 0, ctx->st>>>(ctx->fdmVf, t, ctx->cwf, 1, mx, nullptr, ctx->fdmL, k2); iga_count_launch();
-    k_fdm_gemm32<false, true, false, float2, double2><<<g, blk, 0, ctx->st>>>(ctx->fdmVf, ctx->cwf, s, 1, mx, nullptr, nullptr, 0.0); iga_count_launch();
+    k_fdm_gemm32<false, true, double2, float2><<<g, blk, 0, ctx->st>>>(V, t, ctx->cwf, 1, mx, nullptr, ctx->fdmL, k2); iga_count_launch();
+    if (accumulate) {
+      k_fdm_gemm32<false, false, float2, double2><<<g, blk, 0, ctx->st>>>(Vt, ctx->cwf, ctx->ce2, 1, mx, nullptr, nullptr, 0.0); iga_count_launch();
+      k_axpy_c<<<cdiv(mx, 256), 256, 0, ctx->st>>>(s, ctx->ce2, mx); iga_count_launch();
+    } else {
+      k_fdm_gemm32<false, false, float2, double2><<<g, blk, 0, ctx->st>>>(Vt, ctx->cwf, s, 1, mx, nullptr, nullptr, 0.0); iga_count_launch();
+    }
     CKL();
     return IGA_OK;
   }
-  dim3 g(cdiv(mx, 16), cdiv(mx, 8));
-  // T1 = V^T T ; T2 = (T1 V) / D ; T3 = V T2 ; S = T3 V^T
-  k_fdm_gemm32<true, true, false, double2, float2><<<g, blk, 0, ctx->st>>>(ctx->fdmVf, t, ctx->cwf, mx, mx, nullptr, nullptr, 0.0); iga_count_launch();
-  k_fdm_gemm32<false, false, true, float2, float2><<<g, blk, 0, ctx->st>>>(ctx->fdmVf, ctx->cwf, ctx->cwf2, mx, mx, ctx->fdmL, ctx->fdmL, k2); iga_count_launch();
-  k_fdm_gemm32<true, false, false, float2, float2><<<g, blk, 0, ctx->st>>>(ctx->fdmVf, ctx->cwf2, ctx->cwf, mx, mx, nullptr, nullptr, 0.0); iga_count_launch();
-  k_fdm_gemm32<false, true, false, float2, double2><<<g, blk, 0, ctx->st>>>(ctx->fdmVf, ctx->cwf, s, mx, mx, nullptr, nullptr, 0.0); iga_count_launch();
-  CKL();
-  return IGA_OK;
+  {
+    // four GEMMs with a 64-deep K tile (T1 = V^T T; T2 = T1 V / D; T3 = V T2; S = T3 V^T)
+    dim3 g(cdiv(mx, 16), cdiv(mx, 8));
+    double2* dst = accumulate ? ctx->ce2 : s;
+    k_fdm_gemm32<true, false, double2, float2><<<g, blk, 0, ctx->st>>>(Vt, t, ctx->cwf, mx, mx, nullptr, nullptr, 0.0); iga_count_launch();
+    k_fdm_gemm32<false, true, float2, float2><<<g, blk, 0, ctx->st>>>(V, ctx->cwf, ctx->cwf2, mx, mx, ctx->fdmL, ctx->fdmL, k2); iga_count_launch();
+    k_fdm_gemm32<true, false, float2, float2><<<g, blk, 0, ctx->st>>>(V, ctx->cwf2, ctx->cwf, mx, mx, nullptr, nullptr, 0.0); iga_count_launch();
+    k_fdm_gemm32<false, false, float2, double2><<<g, blk, 0, ctx->st>>>(Vt, ctx->cwf, dst, mx, mx, nullptr, nullptr, 0.0); iga_count_launch();
+    if (accumulate) { k_axpy_c<<<cdiv(ctx->m, 256), 256, 0, ctx->st>>>(s, ctx->ce2, ctx->m); iga_count_launch(); }
+    CKL();
+    return IGA_OK;
+  }
 }
 
 // s = E^{-1} t.  Constant k: fast diagonalisation with FP32 transforms and
@@ -598,8 +531,7 @@ iga_status defl_esolve(iga_ctx* ctx, const double2* t, double2* s) {
   for (int it = 0; it < ctx->e_refine; ++it) {
     TRY(op_apply_bands(ctx, bw, ctx->mx, my, ctx->kcb, ctx->mcb, make_double2(-ctx->k2const, 0.0), s, ctx->ce1, t,
                        EPI_ZMINUS));
-    TRY(fdm_solve32(ctx, ctx->ce1, ctx->ce2));
-    k_axpy_c<<<cdiv(ctx->m, 256), 256, 0, ctx->st>>>(s, ctx->ce2, ctx->m); iga_count_launch();
+    TRY(fdm_solve32(ctx, ctx->ce1, s, true));          // s += FDM(r)
   }
   CKL();
   return IGA_OK;

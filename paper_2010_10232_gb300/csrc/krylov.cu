@@ -322,6 +322,100 @@ __global__ void __launch_bounds__(256) k_arnoldi_coop(ArnoldiArgs a) {
   }
 }
 
+// ------------------------------------------------------------------ CGS2 Arnoldi (no grid barrier)
+// Classical Gram-Schmidt with one reorthogonalisation: h = V^H w (all j+1
+// projections in one pass), w -= V h, twice; H[:, j] = h1 + h2.  Launch count
+// is fixed (independent of j), and no kernel waits on another block, so
+// concurrent solves in one graph can overlap.
+constexpr int CGS_CH = 8;
+
+// part[blk][2 i .. 2 i + 1] = block partial of v_i^H w, i <= j
+__global__ void __launch_bounds__(256) k_cgs_dots(const double2* V, size_t ldv, size_t n, const int* jptr,
+                                                  const double2* w, double* part, int stride) {
+  const int j = *jptr;
+  for (int i0 = 0; i0 <= j; i0 += CGS_CH) {
+    double ar[CGS_CH], ai[CGS_CH];
+#pragma unroll
+    for (int c = 0; c < CGS_CH; ++c) ar[c] = ai[c] = 0.0;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+      double2 we = w[e];
+#pragma unroll
+      for (int c = 0; c < CGS_CH; ++c) {
+        if (i0 + c <= j) {
+          double2 t = cconjmul(V[(size_t)(i0 + c) * ldv + e], we);
+          ar[c] += t.x;
+          ai[c] += t.y;
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < CGS_CH; ++c) {
+      if (i0 + c > j) break;
+      double2 s = block_sum2(ar[c], ai[c]);
+      if (threadIdx.x == 0) {
+        part[(size_t)blockIdx.x * stride + 2 * (i0 + c)] = s.x;
+        part[(size_t)blockIdx.x * stride + 2 * (i0 + c) + 1] = s.y;
+      }
+    }
+  }
+}
+// h_i = sum over blocks (fixed order); block i handles coefficient i.  With
+// hcol, the pass-1 values are stored (first) or added (second pass).
+__global__ void k_cgs_reduce(const double* part, int nb, int stride, const int* jptr, double2* h, double2* H, int ldh,
+                             int second) {
+  const int i = blockIdx.x;
+  if (i > *jptr) return;
+  double a = 0.0, b = 0.0;
+  for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+    a += part[(size_t)t * stride + 2 * i];
+    b += part[(size_t)t * stride + 2 * i + 1];
+  }
+  double2 s = block_sum2(a, b);
+  if (threadIdx.x == 0) {
+    h[i] = s;
+    double2* hc = H + (size_t)(*jptr) * ldh;
+    hc[i] = second ? hc[i] + s : s;
+  }
+}
+// w -= sum_{i <= j} h_i v_i
+__global__ void k_cgs_update(const double2* V, size_t ldv, size_t n, const int* jptr, const double2* h, double2* w) {
+  size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const int j = *jptr;
+  double2 we = w[e];
+  for (int i = 0; i <= j; ++i) we = we - cmul(h[i], V[(size_t)i * ldv + e]);
+  w[e] = we;
+}
+// normalise w into V[:, j+1] and vcur (every block re-reduces ||w||^2)
+__global__ void k_cgs_normalize(double2* V, size_t ldv, size_t n, const double2* w, double2* vcur, const double* part,
+                                const int* jptr) {
+  const int j = *jptr;
+  double2 s = reduce_partials(part, gridDim.x);
+  double hn = sqrt(s.x);
+  double inv = hn > 0.0 ? 1.0 / hn : 0.0;
+  double2* vnext = V + (size_t)(j + 1) * ldv;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    double2 v = inv * w[e];
+    vnext[e] = v;
+    vcur[e] = v;
+  }
+}
+// H[j+1][j] = ||w||, Givens update of column j, j <- j + 1, loop condition.  A
+// launch of its own (one block) because every block of the normalisation reads j.
+__global__ void k_cgs_advance(double2* H, int ldh, int maxit, const double* part, int nb, GState gs, int* jptr,
+                              cudaGraphConditionalHandle cond, int use_cond) {
+  double2 s = reduce_partials(part, nb);
+  if (threadIdx.x == 0) {
+    const int j = *jptr;
+    double2* hcol = H + (size_t)j * ldh;
+    hcol[j + 1] = make_double2(sqrt(s.x), 0.0);
+    givens_update(hcol, j, gs);
+    *jptr = j + 1;
+    unsigned go = (gs.flag[0] == 0 && gs.flag[1] == 0 && j + 1 < maxit) ? 1u : 0u;
+    if (use_cond) cudaGraphSetConditional(cond, go);
+  }
+}
+
 // z_j -> column j = *jptr of Zb
 __global__ void k_store_col(double2* Zb, size_t ldv, size_t n, const int* jptr, const double2* z) {
   size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
@@ -409,6 +503,10 @@ static iga_status ensure_krylov(iga_ctx* ctx, int maxit, bool flexible) {
   ctx->gg = dalloc<double2>(ctx, m + 1);
   ctx->gy = dalloc<double2>(ctx, m);
   ctx->gflag = dalloc<int>(ctx, 4);
+  ctx->cgs_blocks = (int)std::max<size_t>(1, std::min<size_t>(2 * ctx->num_sms, cdiv(n, 1024)));
+  ctx->cgs_part = dalloc<double>(ctx, (size_t)ctx->cgs_blocks * 2 * (m + 1) + 16);
+  ctx->cgs_h = dalloc<double2>(ctx, m + 1);
+  if (!ctx->cgs_part || !ctx->cgs_h) return set_err(ctx, IGA_E_OOM, "cgs workspace");
   if (!ctx->Vb || (flexible && !ctx->Zb) || !ctx->H || !ctx->gstate || !ctx->gsn || !ctx->gg || !ctx->gy || !ctx->gflag)
     return set_err(ctx, IGA_E_OOM, "krylov workspace (n=%zu, maxit=%d)", n, m);
   ctx->maxit_alloc = m;
@@ -458,7 +556,27 @@ static ArnoldiArgs arnoldi_args(iga_ctx* ctx, int maxit) {
   return a;
 }
 
+static iga_status launch_arnoldi_cgs(iga_ctx* ctx, ArnoldiArgs a) {
+  cudaStream_t st = ctx->st;
+  const int nb = ctx->cgs_blocks;
+  const int stride = 2 * (ctx->maxit_alloc + 1);
+  double* part = ctx->cgs_part;
+  double2* h = ctx->cgs_h;
+  for (int pass = 0; pass < 2; ++pass) {
+    k_cgs_dots<<<nb, 256, 0, st>>>(a.V, a.ldv, a.n, a.jptr, a.w, part, stride); iga_count_launch();
+    k_cgs_reduce<<<a.maxit + 1, 256, 0, st>>>(part, nb, stride, a.jptr, h, a.H, a.ldh, pass); iga_count_launch();
+    k_cgs_update<<<cdiv(a.n, 256), 256, 0, st>>>(a.V, a.ldv, a.n, a.jptr, h, a.w); iga_count_launch();
+  }
+  k_norm2_part<<<nb, IGA_RED_THREADS, 0, st>>>(a.w, a.n, part); iga_count_launch();
+  k_cgs_normalize<<<nb, IGA_RED_THREADS, 0, st>>>(a.V, a.ldv, a.n, a.w, a.vcur, part, a.jptr); iga_count_launch();
+  k_cgs_advance<<<1, IGA_RED_THREADS, 0, st>>>(a.H, a.ldh, a.maxit, part, nb, a.gs, a.jptr, a.cond, a.use_cond);
+  iga_count_launch();
+  CKL();
+  return IGA_OK;
+}
+
 static iga_status launch_arnoldi(iga_ctx* ctx, ArnoldiArgs a) {
+  if (ctx->arnoldi_cgs) return launch_arnoldi_cgs(ctx, a);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(ctx->coop_blocks);
   cfg.blockDim = dim3(256);

@@ -34,9 +34,14 @@ __global__ void k_jacobi0(int nx, int ny, int p, const T* K, const T* M, typenam
 }
 
 // coarse = P^T fine  (2D: tensor product of the 1D restriction rows)
+// With xc != nullptr the same kernel also performs the coarse level's first
+// damped Jacobi sweep from zero, xc = omega D_c^{-1} c (D_c from the coarse 1D
+// band diagonals, or dinv for variable k).
 template <typename T>
 __global__ void k_restrict(int nxf, int nyf, int nxc, int nyc, int wR, const T* Rw, const int* Rlo,
-                           const typename cplx<T>::t* f, typename cplx<T>::t* c) {
+                           const typename cplx<T>::t* f, typename cplx<T>::t* c, typename cplx<T>::t* xc, int p,
+                           const T* Kc, const T* Mc, typename cplx<T>::t cm, const typename cplx<T>::t* dinv,
+                           T omega) {
   using C = typename cplx<T>::t;
   size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (j >= (size_t)nxc * nyc) return;
@@ -65,6 +70,24 @@ __global__ void k_restrict(int nxf, int nyf, int nxc, int nyc, int wR, const T* 
     }
   }
   c[j] = acc;
+  if (xc) {
+    C di;
+    if (dinv) {
+      di = dinv[j];
+    } else {
+      int W = 2 * p + 1;
+      T kx = Kc[(size_t)jx * W + p], mx = Mc[(size_t)jx * W + p];
+      C d;
+      if (nyc == 1) {
+        d = mkc(kx, (T)0) + mx * cm;
+      } else {
+        T ky = Kc[(size_t)jy * W + p], my = Mc[(size_t)jy * W + p];
+        d = my * (mkc(kx, (T)0) + mx * cm) + mkc(ky * mx, (T)0);
+      }
+      di = cinv(d);
+    }
+    xc[j] = omega * cmul(di, acc);
+  }
 }
 
 // fine += P coarse
@@ -264,7 +287,26 @@ template <typename T>
 iga_status mg_restrict(iga_ctx* ctx, int l, const typename cplx<T>::t* f, typename cplx<T>::t* c) {
   LevelData& F = ctx->lv[l];
   LevelData& Cc = ctx->lv[l + 1];
-  k_restrict<T><<<cdiv(Cc.n, 256), 256, 0, ctx->st>>>(F.nx, F.ny, Cc.nx, Cc.ny, F.wR, LvBuf<T>::Rw(F), F.Rlo, f, c); iga_count_launch();
+  k_restrict<T><<<cdiv(Cc.n, 256), 256, 0, ctx->st>>>(F.nx, F.ny, Cc.nx, Cc.ny, F.wR, LvBuf<T>::Rw(F), F.Rlo, f, c,
+                                                     nullptr, 0, nullptr, nullptr, czero<typename cplx<T>::t>(),
+                                                     nullptr, (T)0); iga_count_launch();
+  CKL();
+  return IGA_OK;
+}
+
+// c = P^T f and xc = omega D_c^{-1} c (the coarse level's first Jacobi sweep)
+template <typename T>
+static iga_status mg_restrict_j0(iga_ctx* ctx, int l, const typename cplx<T>::t* f, typename cplx<T>::t* c,
+                                 typename cplx<T>::t* xc) {
+  using C = typename cplx<T>::t;
+  LevelData& F = ctx->lv[l];
+  LevelData& Cc = ctx->lv[l + 1];
+  double2 cm = make_double2(-ctx->sig.x, -ctx->sig.y);
+  if (!ctx->vark) cm = ctx->k2const * cm;
+  const C* dinv = (ctx->vark && ctx->dim == 2) ? LvBuf<T>::dinv(Cc) : nullptr;
+  k_restrict<T><<<cdiv(Cc.n, 256), 256, 0, ctx->st>>>(F.nx, F.ny, Cc.nx, Cc.ny, F.wR, LvBuf<T>::Rw(F), F.Rlo, f, c, xc,
+                                                     ctx->p, LvBuf<T>::K(Cc), LvBuf<T>::M(Cc), cconv<C>(cm), dinv,
+                                                     (T)ctx->prm.omega); iga_count_launch();
   CKL();
   return IGA_OK;
 }
@@ -288,9 +330,19 @@ iga_status mg_coarse(iga_ctx* ctx, const typename cplx<T>::t* b, typename cplx<T
 
 // One V-cycle on level l for M_beta x = b from x = 0.  The result is written to
 // `out`; `alt` is a second level-sized buffer used for Jacobi ping-pong.
+// Buffer (out or alt) in which level l's pre-smoothing starts, so that the
+// last post-sweep lands in `out`.
+static int start_buffer(iga_ctx* ctx) {
+  const int nu1 = ctx->prm.nu_pre, nu2 = ctx->prm.nu_post;
+  const int before_post = nu2 & 1;
+  return (nu1 >= 1) ? (before_post ^ ((nu1 - 1) & 1)) : before_post;
+}
+
+// pre_done: the first Jacobi sweep (from zero) was already written into the
+// start buffer by the parent's fused restriction.
 template <typename T>
 static iga_status vcycle_level(iga_ctx* ctx, int l, const typename cplx<T>::t* b, typename cplx<T>::t* out,
-                               typename cplx<T>::t* alt) {
+                               typename cplx<T>::t* alt, bool pre_done = false) {
   using C = typename cplx<T>::t;
   LevelData& L = ctx->lv[l];
   if (l == ctx->L - 1) return mg_coarse<T>(ctx, b, out);
@@ -299,10 +351,9 @@ static iga_status vcycle_level(iga_ctx* ctx, int l, const typename cplx<T>::t* b
   // Choose the buffer the pre-smoother starts in so that, after the nu2
   // post-sweeps (each flips the buffer), the result lands in `out`.
   C* bufs[2] = {out, alt};
-  const int before_post = nu2 & 1;
-  int cur = (nu1 >= 1) ? (before_post ^ ((nu1 - 1) & 1)) : before_post;
+  int cur = start_buffer(ctx);
   if (nu1 >= 1) {
-    TRY(mg_jacobi0<T>(ctx, l, b, bufs[cur]));
+    if (!pre_done) TRY(mg_jacobi0<T>(ctx, l, b, bufs[cur]));
     for (int s = 1; s < nu1; ++s) {
       TRY(op_apply<T>(ctx, l, OP_MB, bufs[cur], bufs[cur ^ 1], nullptr, EPI_JACOBI, b, om));
       cur ^= 1;
@@ -317,8 +368,14 @@ static iga_status vcycle_level(iga_ctx* ctx, int l, const typename cplx<T>::t* b
     CK(cudaMemcpyAsync(r, b, sizeof(C) * L.n, cudaMemcpyDeviceToDevice, ctx->st));
   }
   LevelData& Cl = ctx->lv[l + 1];
-  TRY(mg_restrict<T>(ctx, l, r, LvBuf<T>::b(Cl)));
-  TRY(vcycle_level<T>(ctx, l + 1, LvBuf<T>::b(Cl), LvBuf<T>::x(Cl), LvBuf<T>::y(Cl)));
+  if (nu1 >= 1 && l + 1 < ctx->L - 1) {
+    C* cstart = start_buffer(ctx) ? LvBuf<T>::y(Cl) : LvBuf<T>::x(Cl);
+    TRY(mg_restrict_j0<T>(ctx, l, r, LvBuf<T>::b(Cl), cstart));
+    TRY(vcycle_level<T>(ctx, l + 1, LvBuf<T>::b(Cl), LvBuf<T>::x(Cl), LvBuf<T>::y(Cl), true));
+  } else {
+    TRY(mg_restrict<T>(ctx, l, r, LvBuf<T>::b(Cl)));
+    TRY(vcycle_level<T>(ctx, l + 1, LvBuf<T>::b(Cl), LvBuf<T>::x(Cl), LvBuf<T>::y(Cl)));
+  }
   TRY(mg_prolong_add<T>(ctx, l, LvBuf<T>::x(Cl), bufs[cur]));
   for (int s = 0; s < nu2; ++s) {
     TRY(op_apply<T>(ctx, l, OP_MB, bufs[cur], bufs[cur ^ 1], nullptr, EPI_JACOBI, b, om));

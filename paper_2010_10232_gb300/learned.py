@@ -111,8 +111,8 @@ def preconditioner_inputs(h: Helmholtz, f: torch.Tensor, count: int):
 
 def make_pairs(h: Helmholtz, vectors, crops_per_vector: int, crop: int, gamma: float, cycles: int, rng):
     """Training samples (X bf16 (N, crop, crop, 16), T f32 (N, crop, crop, 2)) from
-    preconditioner inputs: r~ = v - M_beta V(v), e = M_beta^{-1} r~ (by `cycles`
-    V-cycles), random crops."""
+    preconditioner inputs: e = (I - V M_beta)^cycles V(v), r~ = M_beta e (so
+    e = M_beta^{-1} r~ exactly), random crops."""
     L = h._L
     nx = h.level_nx(0)
     Xs, Ts = [], []
@@ -132,7 +132,7 @@ def make_pairs(h: Helmholtz, vectors, crops_per_vector: int, crop: int, gamma: f
     return torch.stack(Xs), torch.stack(Ts)
 
 
-def target_scale(h: Helmholtz, v: torch.Tensor, cycles: int = 20) -> float:
+def target_scale(h: Helmholtz, v: torch.Tensor, cycles: int = 1) -> float:
     """RMS(e) / RMS(r~) for one preconditioner input: the normalisation that makes
     the network's targets O(1)."""
     rt, e = h.vec(), h.vec()

@@ -26,7 +26,7 @@ def _instances():
 
 def test_batched_matches_single_solves():
     inst = _instances()
-    ctxs = [from_problem(pr, precision=prec) for pr, prec in inst]
+    ctxs = [from_problem(pr, precision=prec, arnoldi=1) for pr, prec in inst]
     rhs = []
     for (pr, _), h in zip(inst, ctxs):
         rhs.append(torch.stack([h.point_source(*s) for s in pr.sources]))
@@ -76,3 +76,19 @@ def test_autotuner_choices():
             else:
                 assert c == -1
     assert L.iga_tile_choice(h._h, 99, 0) == -2
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_cgs2_arnoldi_matches_mgs_and_oracle(precision):
+    """The barrier-free CGS2 Arnoldi (used by the batched launch) gives the same
+    iterations as modified Gram-Schmidt and the oracle's solution."""
+    pr = W.small_2d(n_el=64, p=3, k=40.0)
+    s = Solver(pr)
+    f = s.load()
+    ud = s.direct(f)
+    fd = torch.from_numpy(f).cuda()
+    x0, it0, *_ = from_problem(pr, precision=precision).solve(fd, tol=1e-9, maxit=120)
+    x1, it1, hist, tr, st = from_problem(pr, precision=precision, arnoldi=1).solve(fd, tol=1e-9, maxit=120)
+    assert st == 0 and abs(it1 - it0) <= 1
+    assert rel_err(x1.cpu().numpy(), ud) <= 1e-6
+    assert rel_err(x1.cpu().numpy(), x0.cpu().numpy()) <= 1e-6

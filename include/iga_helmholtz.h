@@ -72,10 +72,16 @@ typedef struct {
                               implies it)                                                 */
   int skip_deflation;      /* 1: operator / V-cycle context only (no Z, E); deflation and
                               solve entry points then return IGA_E_INVALID                 */
-  int arnoldi;             /* 0 (default): modified Gram-Schmidt, all projections of an
+  int arnoldi;             /* 0: modified Gram-Schmidt, all projections of an
                               iteration in one cooperative launch (grid barriers);
-                              1: classical Gram-Schmidt with one reorthogonalisation
-                              (CGS2, barrier-free; batched solves always use it)        */
+                              1 (default): classical Gram-Schmidt with one
+                              reorthogonalisation (CGS2, barrier-free, a fixed number
+                              of launches per iteration; batched solves always use it) */
+  int fused_vcycle;        /* 1 (default): in 2D with constant k and nu_pre = nu_post = 1,
+                              each V-cycle level runs as two fused kernels (residual +
+                              restriction; prolongation + post-smoothing), the
+                              pre-smoothing sweep being recomputed where needed;
+                              0: one kernel per operation                               */
   int host_loop;           /* 0 (default): the GMRES loop runs on the device as a CUDA
                               graph with a WHILE conditional node; 1: the host launches
                               each iteration and reads the convergence flag (profiling)   */

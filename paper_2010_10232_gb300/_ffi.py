@@ -35,6 +35,7 @@ class IgaParams(C.Structure):
         ("flexible", C.c_int),
         ("skip_deflation", C.c_int),
         ("arnoldi", C.c_int),
+        ("fused_vcycle", C.c_int),
         ("host_loop", C.c_int),
         ("stream", C.c_void_p),
     ]

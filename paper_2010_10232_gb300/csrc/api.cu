@@ -33,7 +33,8 @@ void iga_default_params(iga_params* prm) {
   d.flexible = 0;
   d.skip_deflation = 0;
   d.host_loop = 0;
-  d.arnoldi = 0;
+  d.arnoldi = 1;
+  d.fused_vcycle = 1;
   d.stream = nullptr;
   *prm = d;
 }
@@ -85,6 +86,7 @@ iga_status iga_setup(const iga_params* prm, iga_ctx** out) {
   if (!(P.omega > 0.0) || P.nu_pre < 0 || P.nu_post < 0 || P.n_vcycles < 1) return IGA_E_INVALID;
   if (P.precision < 0 || P.precision > 1) return IGA_E_INVALID;
   if (P.arnoldi < 0 || P.arnoldi > 1) return IGA_E_INVALID;
+  if (P.fused_vcycle < 0 || P.fused_vcycle > 1) return IGA_E_INVALID;
   for (int l = 0; l <= P.n_lines; ++l)
     if (!std::isfinite(P.k_values[l]) || P.k_values[l] < 0.0) return IGA_E_INVALID;
   iga_ctx* ctx = new (std::nothrow) iga_ctx();
@@ -112,9 +114,11 @@ iga_status iga_setup(const iga_params* prm, iga_ctx** out) {
     if (ctx->vark && ctx->dim == 2)
       for (int l = 0; l < ctx->L && s == IGA_OK; ++l) s = setup_vark_diag(ctx, l);
     if (s != IGA_OK) break;
+    if ((s = setup_const_dinv(ctx)) != IGA_OK) break;
     if ((s = alloc_level_vectors(ctx)) != IGA_OK) break;
     if ((s = autotune_tiles(ctx)) != IGA_OK) break;
     if ((s = setup_coarse_inverse(ctx)) != IGA_OK) break;
+    if ((s = setup_fused_vcycle(ctx)) != IGA_OK) break;
     size_t n = ctx->lv[0].n;
     ctx->w0 = dalloc<double2>(ctx, n);
     ctx->w1 = dalloc<double2>(ctx, n);

@@ -82,6 +82,7 @@ struct LevelData {
   double* Rw = nullptr; int* Rlo = nullptr;   // coarse row j: fine rows Rlo[j] .. +wR
   float* Pwf = nullptr; float* Rwf = nullptr;
   float* k2qf = nullptr;                      // (unused unless variable k) reserved
+  int vc_fmax = 0, vc_cmax = 0;               // fused V-cycle: fine footprint / coarse patch bounds
   // variable k: inverse diagonal of M_beta
   double2* dinv = nullptr;
   float2* dinvf = nullptr;
@@ -128,6 +129,7 @@ struct iga_ctx {
   int e_refine = 2;                  // iterative refinement steps of the FDM coarse solve
   float* fdmVf = nullptr;            // FP32 copy of the eigenvectors
   float* fdmVtf = nullptr;           // and of their transpose
+  float* fdmDinv = nullptr;          // FP32 reciprocal denominators (formed in FP64)
   double* kcb = nullptr;             // banded 1D coarse matrices (half width (p+4)/2)
   double* mcb = nullptr;
   float2* cwf = nullptr;             // FP32 transform scratch
@@ -163,6 +165,7 @@ struct iga_ctx {
   int* kint = nullptr;               // [0] j, [1] barrier timeout
   unsigned* kbar = nullptr;          // grid barrier state
   int coop_blocks = 0;
+  bool vc_fused = false;             // V-cycle by the fused level kernels
   bool arnoldi_cgs = false;          // CGS2 Arnoldi (no grid barrier) instead of cooperative MGS
   int cgs_blocks = 0;
   double* cgs_part = nullptr;        // [cgs_blocks][2 (maxit+1)] partial projections
@@ -189,6 +192,7 @@ struct iga_ctx {
 
 #define IGA_RED_BLOCKS 296
 #define IGA_RED_THREADS 256
+#define IGA_MAX_COARSEST 2048      // largest coarsest-level system inverted densely at setup
 
 // ------------------------------------------------------------------ host helpers
 // Every kernel launch site calls this once per launch (process-wide counter,
@@ -240,6 +244,9 @@ template <typename T> iga_status mg_vcycle(iga_ctx* ctx, const typename cplx<T>:
 template <typename T> iga_status mg_restrict(iga_ctx* ctx, int l, const typename cplx<T>::t* f, typename cplx<T>::t* c);
 template <typename T> iga_status mg_prolong_add(iga_ctx* ctx, int l, const typename cplx<T>::t* c, typename cplx<T>::t* f);
 template <typename T> iga_status mg_coarse(iga_ctx* ctx, const typename cplx<T>::t* b, typename cplx<T>::t* x);
+template <typename T> iga_status mg_vcycle_fused(iga_ctx* ctx, const typename cplx<T>::t* r, typename cplx<T>::t* z);
+iga_status setup_fused_vcycle(iga_ctx* ctx);
+iga_status setup_const_dinv(iga_ctx* ctx);
 template <typename T> iga_status mg_jacobi0(iga_ctx* ctx, int l, const typename cplx<T>::t* b, typename cplx<T>::t* x);
 iga_status setup_coarse_inverse(iga_ctx* ctx);
 // deflation.cu

@@ -16,6 +16,7 @@
 #include "common.cuh"
 #include <cmath>
 
+
 // ------------------------------------------------------------------ Z, Z^T
 __device__ __forceinline__ double zt_w(int a, double eps) {   // a in -2..2
   const double w[5] = {1.0 / 8.0, 4.0 / 8.0, 0.0, 4.0 / 8.0, 1.0 / 8.0};
@@ -281,10 +282,6 @@ __global__ void k_rayleigh(const double* V, const double* Kc, const double* Mc, 
   lam[k] = num / den;
 }
 
-__global__ void k_axpy_c(double2* y, const double2* x, size_t n) {
-  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (i < n) y[i] = y[i] + x[i];
-}
 
 // FP32 variant of the FDM transform for the refined coarse solve: X is double2
 // (first pass) or float2, the output float2 or double2, V in FP32, products
@@ -295,59 +292,110 @@ __device__ __forceinline__ void st_c(double2* p, float2 v) { *p = tod(v); }
 __device__ __forceinline__ void st_c(float2* p, float2 v) { *p = v; }
 
 // out = R X (LEFT) or X R (RIGHT) with R a row-major m x m FP32 matrix (V or
-// V^T, both stored), so every operand tile is read with unit stride.
-template <bool LEFT, bool DIVIDE, typename XT, typename OT>
+// V^T, both stored), so every operand tile is read with unit stride.  The
+// K extent of both operand panels is staged in shared memory in stages of TK
+// (the whole K for short panels: one round of loads).  ACC: out (FP64) += result.
+constexpr int FDM_TY = 8, FDM_TX = 16, FDM_TK = 192;
+__host__ __device__ inline size_t fdm_gemm_smem(int tk) {
+  return sizeof(float2) * ((size_t)FDM_TY * (tk + 1) + (size_t)tk * (FDM_TX + 1));
+}
+
+template <bool LEFT, bool DIVIDE, bool ACC, typename XT, typename OT>
 __global__ void __launch_bounds__(128) k_fdm_gemm32(const float* R, const XT* X, OT* out, int rows, int cols,
-                                                   const double* lam_y, const double* lam_x, double k2) {
-  constexpr int TY = 8, TX = 16, TK = 64;
-  // LEFT: Rs[TY][TK] and Xs[TK][TX]; RIGHT: Xs[TY][TK] and Rs[TK][TX]
-  __shared__ float Rsm[TK * (TX + 1)];
-  __shared__ float2 Xsm[TK * (TX + 1)];
+                                                   const float* dinv, int TK) {
+  constexpr int TY = FDM_TY, TX = FDM_TX;
+  extern __shared__ __align__(16) unsigned char fsm[];
+  // LEFT: Rs[TY][TK+1] and Xs[TK][TX+1]; RIGHT: Xs[TY][TK+1] and Rs[TK][TX+1]
+  float2* Xsm = reinterpret_cast<float2*>(fsm);
+  float* Rsm = reinterpret_cast<float*>(Xsm + (LEFT ? (size_t)TK * (TX + 1) : (size_t)TY * (TK + 1)));
   int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   int i = blockIdx.y * TY + ty, j = blockIdx.x * TX + tx;
   int K = LEFT ? rows : cols;
   float2 acc = make_float2(0.f, 0.f);
   for (int k0 = 0; k0 < K; k0 += TK) {
+    const int kc = min(TK, K - k0);
     if (LEFT) {
       // Rs[r][kk] = R[row0 + r][k0 + kk]  (kk fastest: coalesced)
-      for (int t = threadIdx.x; t < TY * TK; t += 128) {
-        int r = t / TK, kk = t - r * TK;
-        int ri = blockIdx.y * TY + r, rk = k0 + kk;
-        Rsm[r * (TK + 1) + kk] = (ri < rows && rk < K) ? R[(size_t)ri * rows + rk] : 0.f;
+#pragma unroll 4
+      for (int t = threadIdx.x; t < TY * kc; t += 128) {
+        int r = t / kc, kk = t - r * kc;
+        int ri = blockIdx.y * TY + r;
+        Rsm[r * (TK + 1) + kk] = ri < rows ? R[(size_t)ri * rows + k0 + kk] : 0.f;
       }
-      for (int t = threadIdx.x; t < TK * TX; t += 128) {
+#pragma unroll 4
+      for (int t = threadIdx.x; t < kc * TX; t += 128) {
         int kk = t / TX, c = t - kk * TX;
-        int xk = k0 + kk, xj = blockIdx.x * TX + c;
-        Xsm[kk * (TX + 1) + c] = (xk < K && xj < cols) ? ld_f2(X + (size_t)xk * cols + xj) : make_float2(0.f, 0.f);
+        int xj = blockIdx.x * TX + c;
+        Xsm[kk * (TX + 1) + c] = xj < cols ? ld_f2(X + (size_t)(k0 + kk) * cols + xj) : make_float2(0.f, 0.f);
       }
       __syncthreads();
-#pragma unroll
-      for (int kk = 0; kk < TK; ++kk) acc = cfma(Rsm[ty * (TK + 1) + kk], Xsm[kk * (TX + 1) + tx], acc);
+#pragma unroll 8
+      for (int kk = 0; kk < kc; ++kk) acc = cfma(Rsm[ty * (TK + 1) + kk], Xsm[kk * (TX + 1) + tx], acc);
     } else {
-      for (int t = threadIdx.x; t < TY * TK; t += 128) {
-        int r = t / TK, kk = t - r * TK;
-        int xi = blockIdx.y * TY + r, xk = k0 + kk;
-        Xsm[r * (TK + 1) + kk] = (xi < rows && xk < K) ? ld_f2(X + (size_t)xi * cols + xk) : make_float2(0.f, 0.f);
+#pragma unroll 4
+      for (int t = threadIdx.x; t < TY * kc; t += 128) {
+        int r = t / kc, kk = t - r * kc;
+        int xi = blockIdx.y * TY + r;
+        Xsm[r * (TK + 1) + kk] = xi < rows ? ld_f2(X + (size_t)xi * cols + k0 + kk) : make_float2(0.f, 0.f);
       }
       // Rs[kk][c] = R[k0 + kk][col0 + c]  (c fastest: coalesced)
-      for (int t = threadIdx.x; t < TK * TX; t += 128) {
+#pragma unroll 4
+      for (int t = threadIdx.x; t < kc * TX; t += 128) {
         int kk = t / TX, c = t - kk * TX;
-        int rk = k0 + kk, rj = blockIdx.x * TX + c;
-        Rsm[kk * (TX + 1) + c] = (rk < K && rj < cols) ? R[(size_t)rk * cols + rj] : 0.f;
+        int rj = blockIdx.x * TX + c;
+        Rsm[kk * (TX + 1) + c] = rj < cols ? R[(size_t)(k0 + kk) * cols + rj] : 0.f;
       }
       __syncthreads();
-#pragma unroll
-      for (int kk = 0; kk < TK; ++kk) acc = cfma(Rsm[kk * (TX + 1) + tx], Xsm[ty * (TK + 1) + kk], acc);
+#pragma unroll 8
+      for (int kk = 0; kk < kc; ++kk) acc = cfma(Rsm[kk * (TX + 1) + tx], Xsm[ty * (TK + 1) + kk], acc);
     }
     __syncthreads();
   }
   if (i < rows && j < cols) {
-    if (DIVIDE) {
-      double d = (lam_y ? lam_y[i] : 0.0) + lam_x[j] - k2;
-      acc = make_float2((float)((double)acc.x / d), (float)((double)acc.y / d));
+    if (DIVIDE) acc = dinv[(size_t)i * cols + j] * acc;
+    if constexpr (ACC) {
+      OT* o = out + (size_t)i * cols + j;
+      *o = *o + tod(acc);
+    } else {
+      st_c(out + (size_t)i * cols + j, acc);
     }
-    st_c(out + (size_t)i * cols + j, acc);
   }
+}
+
+template <bool LEFT, bool DIVIDE, bool ACC, typename XT, typename OT>
+static void launch_fdm_gemm(iga_ctx* ctx, const float* R, const XT* X, OT* out, int rows, int cols,
+                            const float* dinv) {
+  // the whole K extent in one stage up to 192 (one round of loads); longer
+  // panels in 64-deep stages (fewer loads in flight per thread per stage)
+  const int K = LEFT ? rows : cols;
+  const int tk = K <= 192 ? K : 64;
+  dim3 g(cdiv(cols, FDM_TX), cdiv(rows, FDM_TY));
+  k_fdm_gemm32<LEFT, DIVIDE, ACC, XT, OT><<<g, 128, fdm_gemm_smem(tk), ctx->st>>>(R, X, out, rows, cols, dinv, tk);
+  iga_count_launch();
+}
+
+// one-time: allow the whole-K panels above 48 KB of shared memory
+static iga_status fdm_gemm_attrs(iga_ctx* ctx) {
+  const int sm = (int)fdm_gemm_smem(FDM_TK);
+  CK(cudaFuncSetAttribute(k_fdm_gemm32<false, true, false, double2, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  CK(cudaFuncSetAttribute(k_fdm_gemm32<false, false, false, float2, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  CK(cudaFuncSetAttribute(k_fdm_gemm32<false, false, true, float2, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  CK(cudaFuncSetAttribute(k_fdm_gemm32<true, false, false, double2, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  CK(cudaFuncSetAttribute(k_fdm_gemm32<false, true, false, float2, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  CK(cudaFuncSetAttribute(k_fdm_gemm32<true, false, false, float2, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  return IGA_OK;
+}
+
+// dinv[i][j] = 1 / (lambda_i + lambda_j - k^2) (2D) or 1 / (lambda_j - k^2) (1D):
+// the sum is formed in FP64 (it nearly cancels for modes close to k^2), the
+// reciprocal is rounded once to FP32.
+__global__ void k_fdm_dinv(const double* lam, int n, int dim, double k2, float* dinv) {
+  size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  size_t tot = dim == 2 ? (size_t)n * n : (size_t)n;
+  if (idx >= tot) return;
+  int i = (int)(idx / n), j = (int)(idx - (size_t)i * n);
+  double d = (dim == 2 ? lam[i] : 0.0) + lam[j] - k2;
+  dinv[idx] = (float)(1.0 / d);
 }
 
 __global__ void k_transpose_f(const float* A, float* B, int n) {
@@ -431,8 +479,11 @@ static iga_status fdm_setup(iga_ctx* ctx) {
   ctx->mcb = dalloc<double>(ctx, (size_t)n * (2 * bw + 1));
   ctx->cwf = dalloc<float2>(ctx, ctx->m);
   ctx->cwf2 = dalloc<float2>(ctx, ctx->m);
-  if (!ctx->fdmVf || !ctx->fdmVtf || !ctx->kcb || !ctx->mcb || !ctx->cwf || !ctx->cwf2)
+  ctx->fdmDinv = dalloc<float>(ctx, ctx->m);
+  if (!ctx->fdmVf || !ctx->fdmVtf || !ctx->kcb || !ctx->mcb || !ctx->cwf || !ctx->cwf2 || !ctx->fdmDinv)
     return set_err(ctx, IGA_E_OOM, "fdm32 alloc");
+  k_fdm_dinv<<<cdiv(ctx->m, 256), 256, 0, st>>>(ctx->fdmL, n, ctx->dim, ctx->k2const, ctx->fdmDinv); iga_count_launch();
+  TRY(fdm_gemm_attrs(ctx));
   k_d2f_vec<<<cdiv((size_t)n * n, 256), 256, 0, st>>>(ctx->fdmV, ctx->fdmVf, (size_t)n * n); iga_count_launch();
   k_transpose_f<<<cdiv((size_t)n * n, 256), 256, 0, st>>>(ctx->fdmVf, ctx->fdmVtf, n); iga_count_launch();
   k_dense_to_band<<<cdiv((size_t)n * (2 * bw + 1), 128), 128, 0, st>>>(ctx->kc, n, bw, ctx->kcb); iga_count_launch();
@@ -486,35 +537,23 @@ iga_status defl_z(iga_ctx* ctx, const double2* c, double2* x) {
 // FP32 intermediates live in cwf, cwf2.
 static iga_status fdm_solve32(iga_ctx* ctx, const double2* t, double2* s, bool accumulate = false) {
   const int mx = ctx->mx;
-  const double k2 = ctx->k2const;
   const float* V = ctx->fdmVf;
   const float* Vt = ctx->fdmVtf;
-  dim3 blk(128);
   if (ctx->dim == 1) {
     // s^T = ((t^T V) / d) V^T with t as a 1 x m row
-    dim3 g(cdiv(mx, 16), 1);
-    k_fdm_gemm32<false, true, double2, float2><<<g, blk, 0, ctx->st>>>(V, t, ctx->cwf, 1, mx, nullptr, ctx->fdmL, k2); iga_count_launch();
-    if (accumulate) {
-      k_fdm_gemm32<false, false, float2, double2><<<g, blk, 0, ctx->st>>>(Vt, ctx->cwf, ctx->ce2, 1, mx, nullptr, nullptr, 0.0); iga_count_launch();
-      k_axpy_c<<<cdiv(mx, 256), 256, 0, ctx->st>>>(s, ctx->ce2, mx); iga_count_launch();
-    } else {
-      k_fdm_gemm32<false, false, float2, double2><<<g, blk, 0, ctx->st>>>(Vt, ctx->cwf, s, 1, mx, nullptr, nullptr, 0.0); iga_count_launch();
-    }
-    CKL();
-    return IGA_OK;
+    launch_fdm_gemm<false, true, false>(ctx, V, t, ctx->cwf, 1, mx, ctx->fdmDinv);
+    if (accumulate) launch_fdm_gemm<false, false, true>(ctx, Vt, ctx->cwf, s, 1, mx, nullptr);
+    else launch_fdm_gemm<false, false, false>(ctx, Vt, ctx->cwf, s, 1, mx, nullptr);
+  } else {
+    // T1 = V^T T; T2 = T1 V / D; T3 = V T2; S = T3 V^T (or s += S)
+    launch_fdm_gemm<true, false, false>(ctx, Vt, t, ctx->cwf, mx, mx, nullptr);
+    launch_fdm_gemm<false, true, false>(ctx, V, ctx->cwf, ctx->cwf2, mx, mx, ctx->fdmDinv);
+    launch_fdm_gemm<true, false, false>(ctx, V, ctx->cwf2, ctx->cwf, mx, mx, nullptr);
+    if (accumulate) launch_fdm_gemm<false, false, true>(ctx, Vt, ctx->cwf, s, mx, mx, nullptr);
+    else launch_fdm_gemm<false, false, false>(ctx, Vt, ctx->cwf, s, mx, mx, nullptr);
   }
-  {
-    // four GEMMs with a 64-deep K tile (T1 = V^T T; T2 = T1 V / D; T3 = V T2; S = T3 V^T)
-    dim3 g(cdiv(mx, 16), cdiv(mx, 8));
-    double2* dst = accumulate ? ctx->ce2 : s;
-    k_fdm_gemm32<true, false, double2, float2><<<g, blk, 0, ctx->st>>>(Vt, t, ctx->cwf, mx, mx, nullptr, nullptr, 0.0); iga_count_launch();
-    k_fdm_gemm32<false, true, float2, float2><<<g, blk, 0, ctx->st>>>(V, ctx->cwf, ctx->cwf2, mx, mx, ctx->fdmL, ctx->fdmL, k2); iga_count_launch();
-    k_fdm_gemm32<true, false, float2, float2><<<g, blk, 0, ctx->st>>>(V, ctx->cwf2, ctx->cwf, mx, mx, nullptr, nullptr, 0.0); iga_count_launch();
-    k_fdm_gemm32<false, false, float2, double2><<<g, blk, 0, ctx->st>>>(Vt, ctx->cwf, dst, mx, mx, nullptr, nullptr, 0.0); iga_count_launch();
-    if (accumulate) { k_axpy_c<<<cdiv(ctx->m, 256), 256, 0, ctx->st>>>(s, ctx->ce2, ctx->m); iga_count_launch(); }
-    CKL();
-    return IGA_OK;
-  }
+  CKL();
+  return IGA_OK;
 }
 
 // s = E^{-1} t.  Constant k: fast diagonalisation with FP32 transforms and

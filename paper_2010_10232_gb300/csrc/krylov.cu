@@ -503,7 +503,8 @@ static iga_status ensure_krylov(iga_ctx* ctx, int maxit, bool flexible) {
   ctx->gg = dalloc<double2>(ctx, m + 1);
   ctx->gy = dalloc<double2>(ctx, m);
   ctx->gflag = dalloc<int>(ctx, 4);
-  ctx->cgs_blocks = (int)std::max<size_t>(1, std::min<size_t>(2 * ctx->num_sms, cdiv(n, 1024)));
+  // FP64-bound passes: cover every SM where n allows
+  ctx->cgs_blocks = (int)std::max<size_t>(1, std::min<size_t>(2 * ctx->num_sms, cdiv(n, 256)));
   ctx->cgs_part = dalloc<double>(ctx, (size_t)ctx->cgs_blocks * 2 * (m + 1) + 16);
   ctx->cgs_h = dalloc<double2>(ctx, m + 1);
   if (!ctx->cgs_part || !ctx->cgs_h) return set_err(ctx, IGA_E_OOM, "cgs workspace");

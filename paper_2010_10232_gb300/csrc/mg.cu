@@ -220,6 +220,11 @@ iga_status setup_coarse_inverse(iga_ctx* ctx) {
   LevelData& L = ctx->lv[l];
   int n = L.n;
   ctx->nc = n;
+  // one block inverts the coarsest matrix (a row of it in shared memory)
+  if (n > IGA_MAX_COARSEST)
+    return set_err(ctx, IGA_E_INVALID,
+                   "coarsest level has %d dofs (> %d): n_el must halve to a coarsest mesh of at most ~%d "
+                   "elements per direction", n, IGA_MAX_COARSEST, 40);
   double2* cols = dalloc<double2>(ctx, (size_t)n * n);   // row j = M_beta e_j
   double2* A = dalloc<double2>(ctx, (size_t)n * n);
   double2* e = dalloc<double2>(ctx, n);
@@ -270,13 +275,22 @@ template <> struct LvBuf<float> {
   static const float2* cinv(iga_ctx* c) { return c->cinvf; }
 };
 
+// D^{-1} for the Jacobi sweeps where it is kept in memory: every 2D FP64 level
+// (FP64 division is slow), FP32 only with variable k; else formed on the fly
+template <typename T>
+static const typename cplx<T>::t* jac_dinv(iga_ctx* ctx, LevelData& L) {
+  if (ctx->dim != 2) return nullptr;
+  if (sizeof(T) == 8 || ctx->vark) return LvBuf<T>::dinv(L);
+  return nullptr;
+}
+
 template <typename T>
 iga_status mg_jacobi0(iga_ctx* ctx, int l, const typename cplx<T>::t* b, typename cplx<T>::t* x) {
   using C = typename cplx<T>::t;
   LevelData& L = ctx->lv[l];
   double2 cm = make_double2(-ctx->sig.x, -ctx->sig.y);
   if (!ctx->vark) cm = ctx->k2const * cm;
-  const C* dinv = (ctx->vark && ctx->dim == 2) ? LvBuf<T>::dinv(L) : nullptr;
+  const C* dinv = jac_dinv<T>(ctx, L);
   k_jacobi0<T><<<cdiv(L.n, 256), 256, 0, ctx->st>>>(L.nx, L.ny, ctx->p, LvBuf<T>::K(L), LvBuf<T>::M(L),
                                                     cconv<C>(cm), dinv, b, x, (T)ctx->prm.omega); iga_count_launch();
   CKL();
@@ -303,7 +317,7 @@ static iga_status mg_restrict_j0(iga_ctx* ctx, int l, const typename cplx<T>::t*
   LevelData& Cc = ctx->lv[l + 1];
   double2 cm = make_double2(-ctx->sig.x, -ctx->sig.y);
   if (!ctx->vark) cm = ctx->k2const * cm;
-  const C* dinv = (ctx->vark && ctx->dim == 2) ? LvBuf<T>::dinv(Cc) : nullptr;
+  const C* dinv = jac_dinv<T>(ctx, Cc);
   k_restrict<T><<<cdiv(Cc.n, 256), 256, 0, ctx->st>>>(F.nx, F.ny, Cc.nx, Cc.ny, F.wR, LvBuf<T>::Rw(F), F.Rlo, f, c, xc,
                                                      ctx->p, LvBuf<T>::K(Cc), LvBuf<T>::M(Cc), cconv<C>(cm), dinv,
                                                      (T)ctx->prm.omega); iga_count_launch();
@@ -387,16 +401,27 @@ static iga_status vcycle_level(iga_ctx* ctx, int l, const typename cplx<T>::t* b
 
 // z = n_vcycles V-cycles applied to r on the finest level (stationary
 // iteration z <- z + V(r - M_beta z) from z = 0).
+// one V-cycle from zero on the finest level: the fused level kernels where they
+// apply (2D, constant k, one pre- and one post-sweep, FP32), else operation by
+// operation
+// (in FP64 the halo recomputation costs more FP64 work than the saved
+// launches are worth)
+template <typename T>
+static iga_status vcycle0(iga_ctx* ctx, const typename cplx<T>::t* b, typename cplx<T>::t* out) {
+  if (ctx->vc_fused && sizeof(T) == 4) return mg_vcycle_fused<T>(ctx, b, out);
+  return vcycle_level<T>(ctx, 0, b, out, LvBuf<T>::y(ctx->lv[0]));
+}
+
 template <typename T>
 iga_status mg_vcycle(iga_ctx* ctx, const typename cplx<T>::t* r, typename cplx<T>::t* z) {
   using C = typename cplx<T>::t;
   LevelData& L = ctx->lv[0];
-  TRY(vcycle_level<T>(ctx, 0, r, z, LvBuf<T>::y(L)));
+  TRY(vcycle0<T>(ctx, r, z));
   for (int c = 1; c < ctx->prm.n_vcycles; ++c) {
     C* res = LvBuf<T>::b(L);
     C* e = LvBuf<T>::x(L);
     TRY(op_apply<T>(ctx, 0, OP_MB, z, res, r, EPI_ZMINUS, nullptr, 0.0));
-    TRY(vcycle_level<T>(ctx, 0, res, e, LvBuf<T>::y(L)));
+    TRY(vcycle0<T>(ctx, res, e));
     k_axpy1<C><<<cdiv(L.n, 256), 256, 0, ctx->st>>>(z, e, L.n); iga_count_launch();
     CKL();
   }
@@ -408,4 +433,5 @@ template iga_status mg_vcycle<float>(iga_ctx*, const float2*, float2*);
 template iga_status mg_restrict<double>(iga_ctx*, int, const double2*, double2*);
 template iga_status mg_prolong_add<double>(iga_ctx*, int, const double2*, double2*);
 template iga_status mg_coarse<double>(iga_ctx*, const double2*, double2*);
+template iga_status mg_coarse<float>(iga_ctx*, const float2*, float2*);
 template iga_status mg_jacobi0<double>(iga_ctx*, int, const double2*, double2*);

@@ -418,9 +418,9 @@ iga_status op_apply(iga_ctx* ctx, int level, int which, const typename cplx<T>::
   a.x = x;
   a.y = y;
   a.z = (epi == EPI_JACOBI) ? b : z;
-  a.dinv = nullptr;
-  if (epi == EPI_JACOBI && ctx->vark && ctx->dim == 2) {
-    if constexpr (dbl) a.dinv = (const C*)L.dinv; else a.dinv = (const C*)L.dinvf;
+  a.dinv = nullptr;     // D^{-1} from memory: 2D FP64 levels, FP32 with variable k
+  if (epi == EPI_JACOBI && ctx->dim == 2) {
+    if constexpr (dbl) a.dinv = (const C*)L.dinv; else if (ctx->vark) a.dinv = (const C*)L.dinvf;
   }
   a.omega = (T)omega;
   switch (ctx->p) {

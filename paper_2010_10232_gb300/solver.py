@@ -37,7 +37,8 @@ class Helmholtz:
     a*x + b*y + c >= 0)."""
 
     def __init__(self, dim=2, p=3, n_el=32, kfield=10.0, beta=(1.0, 0.5), eps=0.0, nu_pre=1, nu_post=1,
-                 omega=0.6, n_vcycles=1, precision=0, flexible=0, skip_deflation=0, host_loop=0, arnoldi=0, stream=None):
+                 omega=0.6, n_vcycles=1, precision=0, flexible=0, skip_deflation=0, host_loop=0, arnoldi=None,
+                 fused_vcycle=1, stream=None):
         self._L = _ffi.lib()
         prm = _ffi.IgaParams()
         self._L.iga_default_params(C.byref(prm))
@@ -64,7 +65,9 @@ class Helmholtz:
         prm.flexible = int(flexible)
         prm.skip_deflation = int(skip_deflation)
         prm.host_loop = int(host_loop)
-        prm.arnoldi = int(arnoldi)
+        if arnoldi is not None:
+            prm.arnoldi = int(arnoldi)
+        prm.fused_vcycle = int(fused_vcycle)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream

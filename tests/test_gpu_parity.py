@@ -374,3 +374,62 @@ def test_full_size_solve(cfg2_full):
     assert st == 0 and abs(it - r.iters) <= 1
     assert gap <= max(1e-10, 10 * self_sens)
     assert rel_err(to_n(x), ud) <= 2 * rel_err(r.u, ud) + 1e-9
+
+
+@pytest.mark.parametrize("n_el,p", [(40, 3), (46, 3), (64, 2), (96, 5), (152, 3)])
+def test_esolve_fdm_sizes(n_el, p):
+    """E^{-1} t by the refined FP32 fast diagonalisation against the oracle's
+    sparse LU (odd m_x, m_x not a multiple of the GEMM tiles, p = 2..5)."""
+    pr = W.small_2d(n_el=n_el, p=p, k=0.55 * n_el)
+    h = from_problem(pr)
+    s = Solver(pr)
+    t = rvec(h.m, 95)
+    assert rel_err(to_n(h.esolve(to_t(t))), s.defl.lu.solve(t)) <= 1e-10
+
+
+def test_coarsest_level_too_large_is_rejected():
+    """n_el = 150 halves once (75 is odd): the 76^2-dof coarsest level is refused
+    by the setup with IGA_E_INVALID instead of a failing launch."""
+    with pytest.raises(IgaError) as ei:
+        Helmholtz(dim=2, p=3, n_el=150, kfield=50.0)
+    assert "INVALID" in str(ei.value)
+
+
+@pytest.mark.slow
+def test_esolve_large_coarse_grid_residual():
+    """m_x = 312 (four output rows per block in the two-launch pass): too large
+    for the oracle's sparse LU in test time, so the device result is checked by
+    its residual against the oracle's Galerkin matrix E = Z^T A Z."""
+    n_el, p = 624, 3
+    pr = W.small_2d(n_el=n_el, p=p, k=0.55 * n_el)
+    h = from_problem(pr)
+    d = asm.Discretization(2, p, n_el, pr.kfield)
+    Z = dfl.z_matrix(2, d.n_x, pr.eps)
+    E = (Z.T @ d.A @ Z).tocsr()
+    t = rvec(h.m, 96)
+    s = to_n(h.esolve(to_t(t)))
+    assert np.linalg.norm(t - E @ s) <= 1e-11 * np.linalg.norm(t)
+
+
+@pytest.mark.parametrize("n_el,p,cycles", [(32, 1, 1), (48, 2, 1), (40, 3, 2), (40, 4, 1), (24, 5, 1), (256, 3, 1)])
+def test_vcycle_fused_levels(n_el, p, cycles):
+    """The fused level kernels (residual + restriction, prolongation + post-sweep,
+    pre-sweep recomputed) against the oracle's V-cycle and the per-operation
+    kernels, FP64 and FP32."""
+    pr = W.small_2d(n_el=n_el, p=p, k=0.6 * n_el)
+    pr.n_vcycles = cycles
+    hier = mg.MGHierarchy(2, p, n_el, pr.kfield, 1.0, 0.5)
+    r = rvec(pr.n_x ** 2, 83)
+    ref = hier.apply(r, cycles)
+    for prec in (0, 1):
+        hf = from_problem(pr, precision=prec, skip_deflation=1, fused_vcycle=1)
+        hu = from_problem(pr, precision=prec, skip_deflation=1, fused_vcycle=0)
+        ef = rel_err(to_n(hf.vcycle(to_t(r))), ref)
+        eu = rel_err(to_n(hu.vcycle(to_t(r))), ref)
+        if prec == 0:
+            assert ef <= 1e-11 and eu <= 1e-11
+        else:
+            # FP32: the fused kernels are as accurate as the per-operation
+            # kernels (both carry the FP32 rounding of the V-cycle, which
+            # grows with p), and both stay within 1e-3 of the FP64 result
+            assert ef <= max(2.0 * eu, 1e-5) and ef <= 1e-3, (ef, eu)

@@ -397,6 +397,38 @@ def other_forms(h64, f, x, stream, flush, ws):
                                "iterations_mean": float(allit.mean()), "iterations_max": int(allit.max()),
                                "status": int(rc), "note": "one CUDA-graph launch, FP32 V-cycle, FP64 FGMRES"}
         del ctxs, rhs, xs
+        # the same method unbatched, and the plain FP64 form, on every 8th
+        # instance (all its right-hand sides): one solve call after another
+        sub = inst[::8]
+        ctxs32 = [from_problem(prb, precision=1) for prb, _ in sub]
+        ctxs64 = [from_problem(prb, precision=0) for prb, _ in sub]
+        rhs = [torch.stack([c.point_source(*s_) for s_ in prb.sources]) for c, (prb, _) in zip(ctxs32, sub)]
+        nsub = sum(len(r) for r in rhs)
+
+        def timed(fn):
+            fn()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            return a.elapsed_time(b)
+
+        def seq(cs):
+            def run():
+                for c, r in zip(cs, rhs):
+                    x_ = c.vec()
+                    for j in range(r.shape[0]):
+                        c.solve(r[j], x=x_)
+            return run
+        out["batched_vs_sequential"] = {
+            "instances": len(sub), "rhs": int(nsub),
+            "batched_ms": timed(lambda: solve_batched(ctxs32, rhs)),
+            "sequential_same_method_ms": timed(seq(ctxs32)),
+            "sequential_plain_fp64_ms": timed(seq(ctxs64)),
+            "note": "every 8th instance of the 64, all of its right-hand sides"}
+        del ctxs32, ctxs64, rhs
     except Exception as e:
         out["batched_error"] = str(e)[:200]
     return out

@@ -170,6 +170,7 @@ struct iga_ctx {
   int cgs_blocks = 0;
   double* cgs_part = nullptr;        // [cgs_blocks][2 (maxit+1)] partial projections
   double2* cgs_h = nullptr;          // current projections
+  unsigned* cgs_ticket = nullptr;    // finished-block counter of the normalisation
   bool use_graph = true;
   cudaStream_t cap_stream = nullptr;
   cudaGraph_t graph = nullptr;

@@ -324,49 +324,100 @@ __global__ void __launch_bounds__(256) k_arnoldi_coop(ArnoldiArgs a) {
 
 // ------------------------------------------------------------------ CGS2 Arnoldi (no grid barrier)
 // Classical Gram-Schmidt with one reorthogonalisation: h = V^H w (all j+1
-// projections in one pass), w -= V h, twice; H[:, j] = h1 + h2.  Launch count
-// is fixed (independent of j), and no kernel waits on another block, so
-// concurrent solves in one graph can overlap.
-constexpr int CGS_CH = 8;
+// projections in one pass), w -= V h, twice; H[:, j] = h1 + h2.  Six launches
+// per iteration whatever j is, and no kernel waits on another block, so
+// concurrent solves in one graph can overlap:
+//   dots(w) | reduce | update + dots(w) | reduce | update + ||w||^2 | normalise (+ Givens in the last block)
+// FP64 on this part retires one warp instruction per 64 cycles per SM
+// sub-partition, so the reductions are arranged to issue few FP64 adds.
+constexpr int CGS_T = 128;      // threads per block (4 warps)
+constexpr int CGS_CH = 8;       // projections accumulated per sweep
 
-// part[blk][2 i .. 2 i + 1] = block partial of v_i^H w, i <= j
-__global__ void __launch_bounds__(256) k_cgs_dots(const double2* V, size_t ldv, size_t n, const int* jptr,
-                                                  const double2* w, double* part, int stride) {
+// Sum 16 per-thread values (8 complex partial sums, re in v[0..7], im in
+// v[8..15]) over a warp with a halving butterfly: 16 FP64 adds per warp instead
+// of 80 for one shuffle tree per value.  Afterwards lane L holds the total of
+// value bfly_index(L) (lanes L and L^1 hold the same).
+__device__ __forceinline__ int bfly_index(int lane) {
+  return ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+}
+__device__ __forceinline__ double warp_bfly16(double* v, int lane) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const bool up = lane & 16;
+    double keep = up ? v[8 + k] : v[k], send = up ? v[k] : v[8 + k];
+    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const bool up = lane & 8;
+    double keep = up ? v[4 + k] : v[k], send = up ? v[k] : v[4 + k];
+    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const bool up = lane & 4;
+    double keep = up ? v[2 + k] : v[k], send = up ? v[k] : v[2 + k];
+    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  {
+    const bool up = lane & 2;
+    double keep = up ? v[1] : v[0], send = up ? v[0] : v[1];
+    v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+  }
+  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+// Block partials of v_i^H w for i = i0 .. i0 + 7 (i <= j) -> part[blk][2 i .. 2 i + 1]
+__device__ __forceinline__ void cgs_store_partials(double* v, int i0, int j, double* part, int stride) {
+  __shared__ double red[CGS_T / 32][16];
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const double s = warp_bfly16(v, lane);
+  if ((lane & 1) == 0) red[wp][bfly_index(lane)] = s;
+  __syncthreads();
+  if (threadIdx.x < 16) {
+    double t = 0.0;
+#pragma unroll
+    for (int q = 0; q < CGS_T / 32; ++q) t += red[q][threadIdx.x];
+    const int c = threadIdx.x & 7, i = i0 + c;
+    if (i <= j) part[(size_t)blockIdx.x * stride + 2 * i + (threadIdx.x >> 3)] = t;
+  }
+  __syncthreads();
+}
+
+// conj(v) w accumulated with FMAs: re += vx wx + vy wy, im += vx wy - vy wx
+__device__ __forceinline__ void cacc_conj(double* v, int c, double2 a, double2 b) {
+  v[c] = fma(a.x, b.x, v[c]);
+  v[c] = fma(a.y, b.y, v[c]);
+  v[8 + c] = fma(a.x, b.y, v[8 + c]);
+  v[8 + c] = fma(-a.y, b.x, v[8 + c]);
+}
+
+// pass 1: partial projections of w
+__global__ void __launch_bounds__(CGS_T) k_cgs_dots(const double2* V, size_t ldv, size_t n, const int* jptr,
+                                                    const double2* w, double* part, int stride) {
   const int j = *jptr;
   for (int i0 = 0; i0 <= j; i0 += CGS_CH) {
-    double ar[CGS_CH], ai[CGS_CH];
+    double v[16];
 #pragma unroll
-    for (int c = 0; c < CGS_CH; ++c) ar[c] = ai[c] = 0.0;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-      double2 we = w[e];
+    for (int c = 0; c < 16; ++c) v[c] = 0.0;
+    for (size_t e = blockIdx.x * (size_t)CGS_T + threadIdx.x; e < n; e += (size_t)gridDim.x * CGS_T) {
+      const double2 we = w[e];
 #pragma unroll
-      for (int c = 0; c < CGS_CH; ++c) {
-        if (i0 + c <= j) {
-          double2 t = cconjmul(V[(size_t)(i0 + c) * ldv + e], we);
-          ar[c] += t.x;
-          ai[c] += t.y;
-        }
-      }
+      for (int c = 0; c < CGS_CH; ++c)
+        if (i0 + c <= j) cacc_conj(v, c, V[(size_t)(i0 + c) * ldv + e], we);
     }
-#pragma unroll
-    for (int c = 0; c < CGS_CH; ++c) {
-      if (i0 + c > j) break;
-      double2 s = block_sum2(ar[c], ai[c]);
-      if (threadIdx.x == 0) {
-        part[(size_t)blockIdx.x * stride + 2 * (i0 + c)] = s.x;
-        part[(size_t)blockIdx.x * stride + 2 * (i0 + c) + 1] = s.y;
-      }
-    }
+    cgs_store_partials(v, i0, j, part, stride);
   }
 }
-// h_i = sum over blocks (fixed order); block i handles coefficient i.  With
-// hcol, the pass-1 values are stored (first) or added (second pass).
-__global__ void k_cgs_reduce(const double* part, int nb, int stride, const int* jptr, double2* h, double2* H, int ldh,
-                             int second) {
+
+// h_i = sum over blocks in a fixed order (one block per coefficient); the
+// first pass stores H[:, j] = h, the second adds to it
+__global__ void __launch_bounds__(CGS_T) k_cgs_reduce(const double* part, int nb, int stride, const int* jptr,
+                                                      double2* h, double2* H, int ldh, int second) {
   const int i = blockIdx.x;
   if (i > *jptr) return;
   double a = 0.0, b = 0.0;
-  for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+  for (int t = threadIdx.x; t < nb; t += CGS_T) {
     a += part[(size_t)t * stride + 2 * i];
     b += part[(size_t)t * stride + 2 * i + 1];
   }
@@ -377,38 +428,74 @@ __global__ void k_cgs_reduce(const double* part, int nb, int stride, const int* 
     hc[i] = second ? hc[i] + s : s;
   }
 }
-// w -= sum_{i <= j} h_i v_i
-__global__ void k_cgs_update(const double2* V, size_t ldv, size_t n, const int* jptr, const double2* h, double2* w) {
-  size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (e >= n) return;
+
+// w -= sum_{i <= j} h_i v_i, then (NORM) partial ||w||^2 or (else) the second
+// pass's partial projections of the updated w, over the same elements
+template <bool NORM>
+__global__ void __launch_bounds__(CGS_T) k_cgs_update(const double2* V, size_t ldv, size_t n, const int* jptr,
+                                                      const double2* h, double2* w, double* part, int stride) {
   const int j = *jptr;
-  double2 we = w[e];
-  for (int i = 0; i <= j; ++i) we = we - cmul(h[i], V[(size_t)i * ldv + e]);
-  w[e] = we;
+  double nrm = 0.0;
+  for (size_t e = blockIdx.x * (size_t)CGS_T + threadIdx.x; e < n; e += (size_t)gridDim.x * CGS_T) {
+    double2 we = w[e];
+    for (int i = 0; i <= j; ++i) {
+      const double2 hv = h[i], vv = V[(size_t)i * ldv + e];
+      we.x = fma(-hv.x, vv.x, fma(hv.y, vv.y, we.x));
+      we.y = fma(-hv.x, vv.y, fma(-hv.y, vv.x, we.y));
+    }
+    w[e] = we;
+    if (NORM) nrm = fma(we.x, we.x, fma(we.y, we.y, nrm));
+  }
+  if (NORM) {
+    double2 s = block_sum2(nrm, 0.0);
+    if (threadIdx.x == 0) { part[2 * blockIdx.x] = s.x; part[2 * blockIdx.x + 1] = 0.0; }
+    return;
+  }
+  __syncthreads();      // every thread's w is written before it is read back below
+  for (int i0 = 0; i0 <= j; i0 += CGS_CH) {
+    double v[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) v[c] = 0.0;
+    for (size_t e = blockIdx.x * (size_t)CGS_T + threadIdx.x; e < n; e += (size_t)gridDim.x * CGS_T) {
+      const double2 we = w[e];
+#pragma unroll
+      for (int c = 0; c < CGS_CH; ++c)
+        if (i0 + c <= j) cacc_conj(v, c, V[(size_t)(i0 + c) * ldv + e], we);
+    }
+    cgs_store_partials(v, i0, j, part, stride);
+  }
 }
-// normalise w into V[:, j+1] and vcur (every block re-reduces ||w||^2)
-__global__ void k_cgs_normalize(double2* V, size_t ldv, size_t n, const double2* w, double2* vcur, const double* part,
-                                const int* jptr) {
+
+// v_{j+1} = w / ||w|| into V[:, j+1] and vcur (every block re-reduces ||w||^2).
+// The block that finishes last (ticket counter, no waiting) then sets
+// H[j+1][j] = ||w||, applies the Givens update of column j, advances j and
+// sets the loop condition: by then every block has read j.
+__global__ void __launch_bounds__(CGS_T) k_cgs_normalize(double2* V, size_t ldv, size_t n, const double2* w,
+                                                         double2* vcur, const double* part, int* jptr,
+                                                         unsigned* ticket, double2* H, int ldh, int maxit, GState gs,
+                                                         cudaGraphConditionalHandle cond, int use_cond) {
+  __shared__ bool last;
   const int j = *jptr;
   double2 s = reduce_partials(part, gridDim.x);
-  double hn = sqrt(s.x);
-  double inv = hn > 0.0 ? 1.0 / hn : 0.0;
+  const double hn = sqrt(s.x);
+  const double inv = hn > 0.0 ? 1.0 / hn : 0.0;
   double2* vnext = V + (size_t)(j + 1) * ldv;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+  for (size_t e = blockIdx.x * (size_t)CGS_T + threadIdx.x; e < n; e += (size_t)gridDim.x * CGS_T) {
     double2 v = inv * w[e];
     vnext[e] = v;
     vcur[e] = v;
   }
-}
-// H[j+1][j] = ||w||, Givens update of column j, j <- j + 1, loop condition.  A
-// launch of its own (one block) because every block of the normalisation reads j.
-__global__ void k_cgs_advance(double2* H, int ldh, int maxit, const double* part, int nb, GState gs, int* jptr,
-                              cudaGraphConditionalHandle cond, int use_cond) {
-  double2 s = reduce_partials(part, nb);
+  __syncthreads();
   if (threadIdx.x == 0) {
-    const int j = *jptr;
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    *ticket = 0u;
     double2* hcol = H + (size_t)j * ldh;
-    hcol[j + 1] = make_double2(sqrt(s.x), 0.0);
+    hcol[j + 1] = make_double2(hn, 0.0);
     givens_update(hcol, j, gs);
     *jptr = j + 1;
     unsigned go = (gs.flag[0] == 0 && gs.flag[1] == 0 && j + 1 < maxit) ? 1u : 0u;
@@ -503,11 +590,15 @@ static iga_status ensure_krylov(iga_ctx* ctx, int maxit, bool flexible) {
   ctx->gg = dalloc<double2>(ctx, m + 1);
   ctx->gy = dalloc<double2>(ctx, m);
   ctx->gflag = dalloc<int>(ctx, 4);
-  // FP64-bound passes: cover every SM where n allows
-  ctx->cgs_blocks = (int)std::max<size_t>(1, std::min<size_t>(2 * ctx->num_sms, cdiv(n, 256)));
+  // FP64-bound passes: two 4-warp blocks per SM where n allows
+  ctx->cgs_blocks = (int)std::max<size_t>(1, std::min<size_t>(2 * ctx->num_sms, cdiv(n, 128)));
   ctx->cgs_part = dalloc<double>(ctx, (size_t)ctx->cgs_blocks * 2 * (m + 1) + 16);
   ctx->cgs_h = dalloc<double2>(ctx, m + 1);
-  if (!ctx->cgs_part || !ctx->cgs_h) return set_err(ctx, IGA_E_OOM, "cgs workspace");
+  if (!ctx->cgs_ticket) {
+    ctx->cgs_ticket = dalloc<unsigned>(ctx, 1);
+    if (ctx->cgs_ticket) CK(cudaMemset(ctx->cgs_ticket, 0, sizeof(unsigned)));
+  }
+  if (!ctx->cgs_part || !ctx->cgs_h || !ctx->cgs_ticket) return set_err(ctx, IGA_E_OOM, "cgs workspace");
   if (!ctx->Vb || (flexible && !ctx->Zb) || !ctx->H || !ctx->gstate || !ctx->gsn || !ctx->gg || !ctx->gy || !ctx->gflag)
     return set_err(ctx, IGA_E_OOM, "krylov workspace (n=%zu, maxit=%d)", n, m);
   ctx->maxit_alloc = m;
@@ -563,15 +654,13 @@ static iga_status launch_arnoldi_cgs(iga_ctx* ctx, ArnoldiArgs a) {
   const int stride = 2 * (ctx->maxit_alloc + 1);
   double* part = ctx->cgs_part;
   double2* h = ctx->cgs_h;
-  for (int pass = 0; pass < 2; ++pass) {
-    k_cgs_dots<<<nb, 256, 0, st>>>(a.V, a.ldv, a.n, a.jptr, a.w, part, stride); iga_count_launch();
-    k_cgs_reduce<<<a.maxit + 1, 256, 0, st>>>(part, nb, stride, a.jptr, h, a.H, a.ldh, pass); iga_count_launch();
-    k_cgs_update<<<cdiv(a.n, 256), 256, 0, st>>>(a.V, a.ldv, a.n, a.jptr, h, a.w); iga_count_launch();
-  }
-  k_norm2_part<<<nb, IGA_RED_THREADS, 0, st>>>(a.w, a.n, part); iga_count_launch();
-  k_cgs_normalize<<<nb, IGA_RED_THREADS, 0, st>>>(a.V, a.ldv, a.n, a.w, a.vcur, part, a.jptr); iga_count_launch();
-  k_cgs_advance<<<1, IGA_RED_THREADS, 0, st>>>(a.H, a.ldh, a.maxit, part, nb, a.gs, a.jptr, a.cond, a.use_cond);
-  iga_count_launch();
+  k_cgs_dots<<<nb, CGS_T, 0, st>>>(a.V, a.ldv, a.n, a.jptr, a.w, part, stride); iga_count_launch();
+  k_cgs_reduce<<<a.maxit + 1, CGS_T, 0, st>>>(part, nb, stride, a.jptr, h, a.H, a.ldh, 0); iga_count_launch();
+  k_cgs_update<false><<<nb, CGS_T, 0, st>>>(a.V, a.ldv, a.n, a.jptr, h, a.w, part, stride); iga_count_launch();
+  k_cgs_reduce<<<a.maxit + 1, CGS_T, 0, st>>>(part, nb, stride, a.jptr, h, a.H, a.ldh, 1); iga_count_launch();
+  k_cgs_update<true><<<nb, CGS_T, 0, st>>>(a.V, a.ldv, a.n, a.jptr, h, a.w, part, stride); iga_count_launch();
+  k_cgs_normalize<<<nb, CGS_T, 0, st>>>(a.V, a.ldv, a.n, a.w, a.vcur, part, a.jptr, ctx->cgs_ticket, a.H, a.ldh,
+                                        a.maxit, a.gs, a.cond, a.use_cond); iga_count_launch();
   CKL();
   return IGA_OK;
 }
@@ -646,6 +735,7 @@ iga_status solve_init(iga_ctx* ctx, const double2* f, double tol, bool flex, cud
   GState gs = gstate_of(ctx);
   size_t nh = (size_t)ldh * ctx->maxit_alloc;
   k_solve_reset<<<cdiv(nh, 256), 256, 0, st>>>(ctx->H, nh, ctx->kint, ctx->kbar, gs.scal, tol); iga_count_launch();
+  if (ctx->cgs_ticket) CK(cudaMemsetAsync(ctx->cgs_ticket, 0, sizeof(unsigned), st));
   double2* V = ctx->Vb;
   if (flex) {
     TRY(defl_apply(ctx, f, V));

@@ -300,6 +300,26 @@ __host__ __device__ inline size_t fdm_gemm_smem(int tk) {
   return sizeof(float2) * ((size_t)FDM_TY * (tk + 1) + (size_t)tk * (FDM_TX + 1));
 }
 
+// stage n elements of a panel into shared memory, issuing FDM_LPT independent
+// loads per thread before any store (one round of L2 latency per batch)
+constexpr int FDM_LPT = 16;
+template <typename S, typename D, typename F>
+__device__ __forceinline__ void stage_panel(int total, D* dst, F src_at) {
+  for (int base = 0; base < total; base += 128 * FDM_LPT) {
+    D v[FDM_LPT];
+#pragma unroll
+    for (int q = 0; q < FDM_LPT; ++q) {
+      const int t = base + q * 128 + (int)threadIdx.x;
+      v[q] = t < total ? src_at(t) : D{};
+    }
+#pragma unroll
+    for (int q = 0; q < FDM_LPT; ++q) {
+      const int t = base + q * 128 + (int)threadIdx.x;
+      if (t < total) dst[t] = v[q];
+    }
+  }
+}
+
 template <bool LEFT, bool DIVIDE, bool ACC, typename XT, typename OT>
 __global__ void __launch_bounds__(128) k_fdm_gemm32(const float* R, const XT* X, OT* out, int rows, int cols,
                                                    const float* dinv, int TK) {
@@ -310,44 +330,37 @@ __global__ void __launch_bounds__(128) k_fdm_gemm32(const float* R, const XT* X,
   float* Rsm = reinterpret_cast<float*>(Xsm + (LEFT ? (size_t)TK * (TX + 1) : (size_t)TY * (TK + 1)));
   int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   int i = blockIdx.y * TY + ty, j = blockIdx.x * TX + tx;
+  const int row0 = blockIdx.y * TY, col0 = blockIdx.x * TX;
   int K = LEFT ? rows : cols;
   float2 acc = make_float2(0.f, 0.f);
   for (int k0 = 0; k0 < K; k0 += TK) {
     const int kc = min(TK, K - k0);
     if (LEFT) {
-      // Rs[r][kk] = R[row0 + r][k0 + kk]  (kk fastest: coalesced)
-#pragma unroll 4
-      for (int t = threadIdx.x; t < TY * kc; t += 128) {
+      // Rs[r][kk] = R[row0 + r][k0 + kk]; Xs[kk][c] = X[k0 + kk][col0 + c]  (coalesced)
+      stage_panel<float, float>(TY * kc, Rsm, [&](int t) {
         int r = t / kc, kk = t - r * kc;
-        int ri = blockIdx.y * TY + r;
-        Rsm[r * (TK + 1) + kk] = ri < rows ? R[(size_t)ri * rows + k0 + kk] : 0.f;
-      }
-#pragma unroll 4
-      for (int t = threadIdx.x; t < kc * TX; t += 128) {
+        return row0 + r < rows ? R[(size_t)(row0 + r) * rows + k0 + kk] : 0.f;
+      });
+      stage_panel<float2, float2>(kc * TX, Xsm, [&](int t) {
         int kk = t / TX, c = t - kk * TX;
-        int xj = blockIdx.x * TX + c;
-        Xsm[kk * (TX + 1) + c] = xj < cols ? ld_f2(X + (size_t)(k0 + kk) * cols + xj) : make_float2(0.f, 0.f);
-      }
+        return col0 + c < cols ? ld_f2(X + (size_t)(k0 + kk) * cols + col0 + c) : make_float2(0.f, 0.f);
+      });
       __syncthreads();
 #pragma unroll 8
-      for (int kk = 0; kk < kc; ++kk) acc = cfma(Rsm[ty * (TK + 1) + kk], Xsm[kk * (TX + 1) + tx], acc);
+      for (int kk = 0; kk < kc; ++kk) acc = cfma(Rsm[ty * kc + kk], Xsm[kk * TX + tx], acc);
     } else {
-#pragma unroll 4
-      for (int t = threadIdx.x; t < TY * kc; t += 128) {
+      stage_panel<float2, float2>(TY * kc, Xsm, [&](int t) {
         int r = t / kc, kk = t - r * kc;
-        int xi = blockIdx.y * TY + r;
-        Xsm[r * (TK + 1) + kk] = xi < rows ? ld_f2(X + (size_t)xi * cols + k0 + kk) : make_float2(0.f, 0.f);
-      }
+        return row0 + r < rows ? ld_f2(X + (size_t)(row0 + r) * cols + k0 + kk) : make_float2(0.f, 0.f);
+      });
       // Rs[kk][c] = R[k0 + kk][col0 + c]  (c fastest: coalesced)
-#pragma unroll 4
-      for (int t = threadIdx.x; t < kc * TX; t += 128) {
+      stage_panel<float, float>(kc * TX, Rsm, [&](int t) {
         int kk = t / TX, c = t - kk * TX;
-        int rj = blockIdx.x * TX + c;
-        Rsm[kk * (TX + 1) + c] = rj < cols ? R[(size_t)(k0 + kk) * cols + rj] : 0.f;
-      }
+        return col0 + c < cols ? R[(size_t)(k0 + kk) * cols + col0 + c] : 0.f;
+      });
       __syncthreads();
 #pragma unroll 8
-      for (int kk = 0; kk < kc; ++kk) acc = cfma(Rsm[kk * (TX + 1) + tx], Xsm[ty * (TK + 1) + kk], acc);
+      for (int kk = 0; kk < kc; ++kk) acc = cfma(Rsm[kk * TX + tx], Xsm[ty * kc + kk], acc);
     }
     __syncthreads();
   }

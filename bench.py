@@ -24,6 +24,9 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# dram__bytes_read.sum + dram__bytes_write.sum of k_kron2d<3, double, EPI_Y, 32, 8> applying A
+# at n = 321^2 (one ncu capture, L2 cold); the algorithmic bytes are 16 B in + 16 B out per dof
+APPLY_DRAM_BYTES = 1695232
 K_WAVE, P_DEG, N_EL = 200.0, 3, 320
 METRIC = "2D solve time to 1e-7 rel. residual + iterations; apply/V-cycle HBM GB/s vs peak"
 WORKLOAD = f"MP2-A constant k={int(K_WAVE)}, p={P_DEG}, {N_EL}x{N_EL} elements, centre point source"
@@ -302,7 +305,9 @@ def gpu_arm(args):
         "gpu_launches": int(launches),
         "roofline": {"kernel": "k_kron2d<3,double,EPI_Y> (apply A)", "bound": "alu",
                      "achieved": achieved_gflops / 1e3, "peak": fp64_nominal, "unit": "TFLOP/s",
-                     "frac": achieved_gflops / 1e3 / fp64_nominal, "traffic": None,
+                     "frac": achieved_gflops / 1e3 / fp64_nominal, "traffic": APPLY_DRAM_BYTES,
+                     "traffic_note": "DRAM bytes read + written per launch, one ncu capture at this size "
+                                     "(cold L2; the output stays in L2, so about the x read)",
                      "algorithmic": f"{flops_dof} flop/dof x {h.n} dofs per launch",
                      "peak_source": "nominal FP64 of the profiling recipe",
                      "probe_fma_tflops": probe, "launch_us": t_apply * 1e6,

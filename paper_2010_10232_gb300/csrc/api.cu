@@ -115,6 +115,7 @@ iga_status iga_setup(const iga_params* prm, iga_ctx** out) {
       for (int l = 0; l < ctx->L && s == IGA_OK; ++l) s = setup_vark_diag(ctx, l);
     if (s != IGA_OK) break;
     if ((s = setup_const_dinv(ctx)) != IGA_OK) break;
+    if ((s = setup_tiled_transfers(ctx)) != IGA_OK) break;
     if ((s = alloc_level_vectors(ctx)) != IGA_OK) break;
     if ((s = autotune_tiles(ctx)) != IGA_OK) break;
     if ((s = setup_coarse_inverse(ctx)) != IGA_OK) break;

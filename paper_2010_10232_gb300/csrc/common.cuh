@@ -83,6 +83,7 @@ struct LevelData {
   float* Pwf = nullptr; float* Rwf = nullptr;
   float* k2qf = nullptr;                      // (unused unless variable k) reserved
   int vc_fmax = 0, vc_cmax = 0;               // fused V-cycle: fine footprint / coarse patch bounds
+  int tr_fmax = 0, tp_cmax = 0;               // tiled 2D transfers (0: per-point kernels)
   // variable k: inverse diagonal of M_beta
   double2* dinv = nullptr;
   float2* dinvf = nullptr;
@@ -248,6 +249,7 @@ template <typename T> iga_status mg_coarse(iga_ctx* ctx, const typename cplx<T>:
 template <typename T> iga_status mg_vcycle_fused(iga_ctx* ctx, const typename cplx<T>::t* r, typename cplx<T>::t* z);
 iga_status setup_fused_vcycle(iga_ctx* ctx);
 iga_status setup_const_dinv(iga_ctx* ctx);
+iga_status setup_tiled_transfers(iga_ctx* ctx);
 template <typename T> iga_status mg_jacobi0(iga_ctx* ctx, int l, const typename cplx<T>::t* b, typename cplx<T>::t* x);
 iga_status setup_coarse_inverse(iga_ctx* ctx);
 // deflation.cu

@@ -4,6 +4,8 @@
 // p = 1 case is the paper's linear interpolation; restriction is its
 // transpose.  The coarsest level is solved with a dense inverse built at setup.
 #include "common.cuh"
+#include <algorithm>
+#include <vector>
 
 // ------------------------------------------------------------------ kernels
 // First Jacobi sweep from x = 0:  x = omega D^{-1} b.
@@ -122,6 +124,166 @@ __global__ void k_prolong_add(int nxf, int nyf, int nxc, int nyc, int wP, const 
     }
   }
   f[i] = f[i] + acc;
+}
+
+// ------------------------------------------------------------------ tiled 2D transfers
+// Separable tensor-product transfers through shared memory: each pass runs
+// one 1D window (p + 3 or p/2 + 3 taps) per output instead of the 2D window,
+// so a thread's dependent chain is a few FMAs (FP64 retires one warp
+// instruction per 64 cycles per SM sub-partition on this part).
+constexpr int TR_CT = 16;            // coarse tile of the restriction
+constexpr int TP_TX = 32, TP_TY = 8; // fine tile of the prolongation
+
+template <typename C, typename T>
+__host__ __device__ inline size_t tr_smem(int fmax, int wR) {
+  return sizeof(C) * ((size_t)fmax * fmax + (size_t)fmax * TR_CT) + sizeof(T) * 2 * TR_CT * wR + sizeof(int) * 2 * TR_CT;
+}
+
+// c = R f on a coarse TR_CT^2 tile; with xc also xc = omega D_c^{-1} c
+template <typename T>
+__global__ void __launch_bounds__(256) k_restrict_tiled(int nxf, int nyf, int nxc, int nyc, int wR, const T* Rw,
+                                                        const int* Rlo, int fmax, const typename cplx<T>::t* f,
+                                                        typename cplx<T>::t* c, typename cplx<T>::t* xc,
+                                                        const typename cplx<T>::t* dinv, T omega) {
+  using C = typename cplx<T>::t;
+  extern __shared__ __align__(16) unsigned char rsm[];
+  C* fs = reinterpret_cast<C*>(rsm);                 // [FY][FX] fine footprint
+  C* rx = fs + (size_t)fmax * fmax;                  // [FY][TR_CT] restricted along x
+  T* Rwx = reinterpret_cast<T*>(rx + (size_t)fmax * TR_CT);
+  T* Rwy = Rwx + TR_CT * wR;
+  int* Rlox = reinterpret_cast<int*>(Rwy + TR_CT * wR);
+  int* Rloy = Rlox + TR_CT;
+  const int tid = threadIdx.x;
+  const int cx0 = blockIdx.x * TR_CT, cy0 = blockIdx.y * TR_CT;
+  const int cxn = min(TR_CT, nxc - cx0), cyn = min(TR_CT, nyc - cy0);
+  const int fx0 = max(0, Rlo[cx0]), fx1 = min(nxf, Rlo[cx0 + cxn - 1] + wR);
+  const int fy0 = max(0, Rlo[cy0]), fy1 = min(nyf, Rlo[cy0 + cyn - 1] + wR);
+  const int FX = fx1 - fx0, FY = fy1 - fy0;
+  if (FX > fmax || FY > fmax || FX < 1 || FY < 1) return;   // cannot happen: fmax is the maximum over tiles
+  for (int i = tid; i < FY * FX; i += 256) {
+    const int r = i / FX, q = i - r * FX;
+    fs[i] = f[(size_t)(fy0 + r) * nxf + fx0 + q];
+  }
+  for (int i = tid; i < cxn * wR; i += 256) Rwx[i] = Rw[(size_t)cx0 * wR + i];
+  for (int i = tid; i < cyn * wR; i += 256) Rwy[i] = Rw[(size_t)cy0 * wR + i];
+  if (tid < cxn) Rlox[tid] = Rlo[cx0 + tid] - fx0;
+  if (tid < cyn) Rloy[tid] = Rlo[cy0 + tid] - fy0;
+  __syncthreads();
+  for (int i = tid; i < FY * cxn; i += 256) {
+    const int r = i / cxn, jx = i - r * cxn;
+    C acc = czero<C>();
+    for (int t = 0; t < wR; ++t) {
+      const T w = Rwx[jx * wR + t];
+      const int q = Rlox[jx] + t;
+      if (w != (T)0 && q >= 0 && q < FX) acc = cfma(w, fs[r * FX + q], acc);
+    }
+    rx[r * TR_CT + jx] = acc;
+  }
+  __syncthreads();
+  for (int i = tid; i < cyn * cxn; i += 256) {
+    const int jy = i / cxn, jx = i - jy * cxn;
+    C acc = czero<C>();
+    for (int t = 0; t < wR; ++t) {
+      const T w = Rwy[jy * wR + t];
+      const int q = Rloy[jy] + t;
+      if (w != (T)0 && q >= 0 && q < FY) acc = cfma(w, rx[q * TR_CT + jx], acc);
+    }
+    const size_t o = (size_t)(cy0 + jy) * nxc + cx0 + jx;
+    c[o] = acc;
+    if (xc) xc[o] = omega * cmul(dinv[o], acc);
+  }
+}
+
+template <typename C, typename T>
+__host__ __device__ inline size_t tp_smem(int cmax, int wP) {
+  return sizeof(C) * ((size_t)cmax * cmax + (size_t)cmax * TP_TX) + sizeof(T) * (TP_TX + TP_TY) * wP +
+         sizeof(int) * (TP_TX + TP_TY);
+}
+
+// f += P c on a fine TP_TX x TP_TY tile
+template <typename T>
+__global__ void __launch_bounds__(256) k_prolong_tiled(int nxf, int nyf, int nxc, int nyc, int wP, const T* Pw,
+                                                       const int* Plo, int cmax, const typename cplx<T>::t* c,
+                                                       typename cplx<T>::t* f) {
+  using C = typename cplx<T>::t;
+  extern __shared__ __align__(16) unsigned char psm[];
+  C* cs = reinterpret_cast<C*>(psm);                 // [CYN][CXN] coarse patch
+  C* t1 = cs + (size_t)cmax * cmax;                  // [CYN][TP_TX] prolonged along x
+  T* Pwx = reinterpret_cast<T*>(t1 + (size_t)cmax * TP_TX);
+  T* Pwy = Pwx + TP_TX * wP;
+  int* Plox = reinterpret_cast<int*>(Pwy + TP_TY * wP);
+  int* Ploy = Plox + TP_TX;
+  const int tid = threadIdx.x;
+  const int x0 = blockIdx.x * TP_TX, y0 = blockIdx.y * TP_TY;
+  const int xn = min(TP_TX, nxf - x0), yn = min(TP_TY, nyf - y0);
+  const int cxa = max(0, Plo[x0]), cxb = min(nxc, Plo[x0 + xn - 1] + wP);
+  const int cya = max(0, Plo[y0]), cyb = min(nyc, Plo[y0 + yn - 1] + wP);
+  const int CXN = cxb - cxa, CYN = cyb - cya;
+  if (CXN > cmax || CYN > cmax || CXN < 1 || CYN < 1) return;   // cannot happen: cmax is the maximum over tiles
+  for (int i = tid; i < CYN * CXN; i += 256) {
+    const int r = i / CXN, q = i - r * CXN;
+    cs[i] = c[(size_t)(cya + r) * nxc + cxa + q];
+  }
+  for (int i = tid; i < xn * wP; i += 256) Pwx[i] = Pw[(size_t)x0 * wP + i];
+  for (int i = tid; i < yn * wP; i += 256) Pwy[i] = Pw[(size_t)y0 * wP + i];
+  if (tid < xn) Plox[tid] = Plo[x0 + tid] - cxa;
+  if (tid < yn) Ploy[tid] = Plo[y0 + tid] - cya;
+  __syncthreads();
+  for (int i = tid; i < CYN * xn; i += 256) {
+    const int r = i / xn, q = i - r * xn;
+    C acc = czero<C>();
+    for (int t = 0; t < wP; ++t) {
+      const T w = Pwx[q * wP + t];
+      const int j = Plox[q] + t;
+      if (w != (T)0 && j >= 0 && j < CXN) acc = cfma(w, cs[r * CXN + j], acc);
+    }
+    t1[r * TP_TX + q] = acc;
+  }
+  __syncthreads();
+  for (int i = tid; i < yn * xn; i += 256) {
+    const int r = i / xn, q = i - r * xn;
+    C acc = czero<C>();
+    for (int t = 0; t < wP; ++t) {
+      const T w = Pwy[r * wP + t];
+      const int j = Ploy[r] + t;
+      if (w != (T)0 && j >= 0 && j < CYN) acc = cfma(w, t1[j * TP_TX + q], acc);
+    }
+    const size_t o = (size_t)(y0 + r) * nxf + x0 + q;
+    f[o] = f[o] + acc;
+  }
+}
+
+// Tile extents of the tiled transfers of level l -> l+1 (from the host copies
+// of the window tables).  0 when a window table is not monotone.
+iga_status setup_tiled_transfers(iga_ctx* ctx) {
+  if (ctx->dim != 2) return IGA_OK;
+  for (int l = 0; l + 1 < ctx->L; ++l) {
+    LevelData& F = ctx->lv[l];
+    LevelData& Cl = ctx->lv[l + 1];
+    std::vector<int> Rlo(Cl.nx), Plo(F.nx);
+    CK(cudaMemcpy(Rlo.data(), F.Rlo, sizeof(int) * Cl.nx, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(Plo.data(), F.Plo, sizeof(int) * F.nx, cudaMemcpyDeviceToHost));
+    bool mono = true;
+    for (int j = 1; j < Cl.nx; ++j) mono = mono && Rlo[j] >= Rlo[j - 1];
+    for (int i = 1; i < F.nx; ++i) mono = mono && Plo[i] >= Plo[i - 1];
+    F.tr_fmax = F.tp_cmax = 0;
+    if (!mono) continue;
+    int fmax = 1, cmax = 1;
+    for (int c0 = 0; c0 < Cl.nx; c0 += TR_CT) {
+      int cn = std::min(TR_CT, Cl.nx - c0);
+      fmax = std::max(fmax, std::min(F.nx, Rlo[c0 + cn - 1] + F.wR) - std::max(0, Rlo[c0]));
+    }
+    for (int T_ : {TP_TX, TP_TY})
+      for (int x0 = 0; x0 < F.nx; x0 += T_) {
+        int xn = std::min(T_, F.nx - x0);
+        cmax = std::max(cmax, std::min(Cl.nx, Plo[x0 + xn - 1] + F.wP) - std::max(0, Plo[x0]));
+      }
+    if (tr_smem<double2, double>(fmax, F.wR) <= 48 * 1024 && tp_smem<double2, double>(cmax, F.wP) <= 48 * 1024) {
+      F.tr_fmax = fmax;
+      F.tp_cmax = cmax;
+    }
+  }
+  return IGA_OK;
 }
 
 // x = Minv b, one block, dense
@@ -298,9 +460,26 @@ iga_status mg_jacobi0(iga_ctx* ctx, int l, const typename cplx<T>::t* b, typenam
 }
 
 template <typename T>
+static void launch_restrict_tiled(iga_ctx* ctx, int l, const typename cplx<T>::t* f, typename cplx<T>::t* c,
+                                  typename cplx<T>::t* xc, const typename cplx<T>::t* dinv) {
+  using C = typename cplx<T>::t;
+  LevelData& F = ctx->lv[l];
+  LevelData& Cc = ctx->lv[l + 1];
+  dim3 g(cdiv(Cc.nx, TR_CT), cdiv(Cc.ny, TR_CT));
+  k_restrict_tiled<T><<<g, 256, tr_smem<C, T>(F.tr_fmax, F.wR), ctx->st>>>(
+      F.nx, F.ny, Cc.nx, Cc.ny, F.wR, LvBuf<T>::Rw(F), F.Rlo, F.tr_fmax, f, c, xc, dinv, (T)ctx->prm.omega);
+  iga_count_launch();
+}
+
+template <typename T>
 iga_status mg_restrict(iga_ctx* ctx, int l, const typename cplx<T>::t* f, typename cplx<T>::t* c) {
   LevelData& F = ctx->lv[l];
   LevelData& Cc = ctx->lv[l + 1];
+  if (F.tr_fmax > 0) {
+    launch_restrict_tiled<T>(ctx, l, f, c, nullptr, nullptr);
+    CKL();
+    return IGA_OK;
+  }
   k_restrict<T><<<cdiv(Cc.n, 256), 256, 0, ctx->st>>>(F.nx, F.ny, Cc.nx, Cc.ny, F.wR, LvBuf<T>::Rw(F), F.Rlo, f, c,
                                                      nullptr, 0, nullptr, nullptr, czero<typename cplx<T>::t>(),
                                                      nullptr, (T)0); iga_count_launch();
@@ -318,6 +497,11 @@ static iga_status mg_restrict_j0(iga_ctx* ctx, int l, const typename cplx<T>::t*
   double2 cm = make_double2(-ctx->sig.x, -ctx->sig.y);
   if (!ctx->vark) cm = ctx->k2const * cm;
   const C* dinv = jac_dinv<T>(ctx, Cc);
+  if (F.tr_fmax > 0 && dinv) {            // D_c^{-1} in memory (FP64, or variable k)
+    launch_restrict_tiled<T>(ctx, l, f, c, xc, dinv);
+    CKL();
+    return IGA_OK;
+  }
   k_restrict<T><<<cdiv(Cc.n, 256), 256, 0, ctx->st>>>(F.nx, F.ny, Cc.nx, Cc.ny, F.wR, LvBuf<T>::Rw(F), F.Rlo, f, c, xc,
                                                      ctx->p, LvBuf<T>::K(Cc), LvBuf<T>::M(Cc), cconv<C>(cm), dinv,
                                                      (T)ctx->prm.omega); iga_count_launch();
@@ -327,8 +511,17 @@ static iga_status mg_restrict_j0(iga_ctx* ctx, int l, const typename cplx<T>::t*
 
 template <typename T>
 iga_status mg_prolong_add(iga_ctx* ctx, int l, const typename cplx<T>::t* c, typename cplx<T>::t* f) {
+  using C = typename cplx<T>::t;
   LevelData& F = ctx->lv[l];
   LevelData& Cc = ctx->lv[l + 1];
+  if (F.tp_cmax > 0) {
+    dim3 g(cdiv(F.nx, TP_TX), cdiv(F.ny, TP_TY));
+    k_prolong_tiled<T><<<g, 256, tp_smem<C, T>(F.tp_cmax, F.wP), ctx->st>>>(F.nx, F.ny, Cc.nx, Cc.ny, F.wP,
+                                                                          LvBuf<T>::Pw(F), F.Plo, F.tp_cmax, c, f);
+    iga_count_launch();
+    CKL();
+    return IGA_OK;
+  }
   k_prolong_add<T><<<cdiv(F.n, 256), 256, 0, ctx->st>>>(F.nx, F.ny, Cc.nx, Cc.ny, F.wP, LvBuf<T>::Pw(F), F.Plo, c, f); iga_count_launch();
   CKL();
   return IGA_OK;

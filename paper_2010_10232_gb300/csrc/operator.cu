@@ -3,8 +3,8 @@
 //
 // Constant k: Op = M_y (x) (K_x + c M_x) + K_y (x) M_x applied as two banded
 // 1D passes through a shared-memory tile with a p-wide halo:
-//   x-pass  u = K_x x + c M_x x,  t = M_x x   (rows of the tile + halo rows)
-//   y-pass  y = M_y u + K_y t
+//   y-pass  u = M_y x,  w = c u + K_y x     (tile rows, columns of tile + halo)
+//   x-pass  y = K_x u + M_x w
 // c = -k^2 for A and -(beta1 - i beta2) k^2 for M_beta.
 //
 // Variable k: S by the same banded passes, the k^2-mass by per-element
@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(256) k_kron1d(OpArgs<T> a) {
 template <int P, typename T, int TX, int TY>
 constexpr size_t kron2d_smem() {
   using C = typename cplx<T>::t;
-  return sizeof(C) * ((TY + 2 * P) * (TX + 2 * P) + 2 * (TY + 2 * P) * TX) + sizeof(T) * (2 * TX + 2 * TY) * (2 * P + 1);
+  return sizeof(C) * ((TY + 2 * P) * (TX + 2 * P) + 2 * TY * (TX + 2 * P)) + sizeof(T) * (2 * TX + 2 * TY) * (2 * P + 1);
 }
 
 template <int P, typename T, int EPI, int TX, int TY>
@@ -112,9 +112,9 @@ __global__ void __launch_bounds__(256) k_kron2d(OpArgs<T> a) {
   constexpr int W = 2 * P + 1, SX = TX + 2 * P, SY = TY + 2 * P;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* xs = (C*)smem_raw;
-  C* us = xs + SY * SX;
-  C* ts = us + SY * TX;
-  T* kx = (T*)(ts + SY * TX);
+  C* us = xs + SY * SX;           // [TY][SX]  M_y x
+  C* ws = us + TY * SX;           // [TY][SX]  c M_y x + K_y x
+  T* kx = (T*)(ws + TY * SX);
   T* mx = kx + TX * W;
   T* ky = mx + TX * W;
   T* my = ky + TY * W;
@@ -137,19 +137,23 @@ __global__ void __launch_bounds__(256) k_kron2d(OpArgs<T> a) {
     my[i] = gy < ny ? a.M[(size_t)y0 * W + i] : (T)0;
   }
   __syncthreads();
-  for (int i = tid; i < SY * TX; i += 256) {
-    int r = i / TX, c = i - r * TX;
+  // pass along y over the tile rows and all halo columns (the halo of the
+  // wider tile side is the one recomputed, so the first pass does the least
+  // redundant work): u = M_y x, w = c u + K_y x
+  for (int i = tid; i < TY * SX; i += 256) {
+    int r = i / SX, c = i - r * SX;
     C s1 = czero<C>(), s2 = czero<C>();
 #pragma unroll
     for (int d = 0; d < W; ++d) {
-      C v = xs[r * SX + c + d];
-      s1 = cfma(kx[c * W + d], v, s1);
-      s2 = cfma(mx[c * W + d], v, s2);
+      C v = xs[(r + d) * SX + c];
+      s1 = cfma(my[r * W + d], v, s1);
+      s2 = cfma(ky[r * W + d], v, s2);
     }
-    us[i] = s1 + cmul(a.c, s2);
-    ts[i] = s2;
+    us[i] = s1;
+    ws[i] = cmul(a.c, s1) + s2;
   }
   __syncthreads();
+  // pass along x: Op x = K_x u + M_x w
   for (int i = tid; i < TY * TX; i += 256) {
     int r = i / TX, c = i - r * TX;
     int gy = y0 + r, gx = x0 + c;
@@ -157,8 +161,8 @@ __global__ void __launch_bounds__(256) k_kron2d(OpArgs<T> a) {
     C acc = czero<C>();
 #pragma unroll
     for (int d = 0; d < W; ++d) {
-      acc = cfma(my[r * W + d], us[(r + d) * TX + c], acc);
-      acc = cfma(ky[r * W + d], ts[(r + d) * TX + c], acc);
+      acc = cfma(kx[c * W + d], us[r * SX + c + d], acc);
+      acc = cfma(mx[c * W + d], ws[r * SX + c + d], acc);
     }
     C diag = czero<C>();
     if (EPI == EPI_JACOBI) {

@@ -77,11 +77,13 @@ typedef struct {
                               1 (default): classical Gram-Schmidt with one
                               reorthogonalisation (CGS2, barrier-free, a fixed number
                               of launches per iteration; batched solves always use it) */
-  int fused_vcycle;        /* 1 (default): in 2D with constant k and nu_pre = nu_post = 1,
-                              each V-cycle level runs as two fused kernels (residual +
+  int fused_vcycle;        /* 0 (default): one kernel per V-cycle operation;
+                              1: the FP32 V-cycle (2D, constant k, nu_pre = nu_post = 1)
+                              runs each level as two fused kernels (residual +
                               restriction; prolongation + post-smoothing), the
-                              pre-smoothing sweep being recomputed where needed;
-                              0: one kernel per operation                               */
+                              pre-smoothing sweep recomputed where needed: half the
+                              DRAM bytes, more instructions (slower on GB300 as
+                              measured, kept for bandwidth-starved parts)               */
   int host_loop;           /* 0 (default): the GMRES loop runs on the device as a CUDA
                               graph with a WHILE conditional node; 1: the host launches
                               each iteration and reads the convergence flag (profiling)   */

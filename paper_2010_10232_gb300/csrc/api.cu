@@ -34,7 +34,7 @@ void iga_default_params(iga_params* prm) {
   d.skip_deflation = 0;
   d.host_loop = 0;
   d.arnoldi = 1;
-  d.fused_vcycle = 1;
+  d.fused_vcycle = 0;
   d.stream = nullptr;
   *prm = d;
 }

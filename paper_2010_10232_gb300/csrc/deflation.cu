@@ -303,24 +303,24 @@ __host__ __device__ inline size_t fdm_gemm_smem(int tk) {
 // stage n elements of a panel into shared memory, issuing FDM_LPT independent
 // loads per thread before any store (one round of L2 latency per batch)
 constexpr int FDM_LPT = 16;
-template <typename S, typename D, typename F>
+template <int LPT, typename D, typename F>
 __device__ __forceinline__ void stage_panel(int total, D* dst, F src_at) {
-  for (int base = 0; base < total; base += 128 * FDM_LPT) {
-    D v[FDM_LPT];
+  for (int base = 0; base < total; base += 128 * LPT) {
+    D v[LPT];
 #pragma unroll
-    for (int q = 0; q < FDM_LPT; ++q) {
+    for (int q = 0; q < LPT; ++q) {
       const int t = base + q * 128 + (int)threadIdx.x;
       v[q] = t < total ? src_at(t) : D{};
     }
 #pragma unroll
-    for (int q = 0; q < FDM_LPT; ++q) {
+    for (int q = 0; q < LPT; ++q) {
       const int t = base + q * 128 + (int)threadIdx.x;
       if (t < total) dst[t] = v[q];
     }
   }
 }
 
-template <bool LEFT, bool DIVIDE, bool ACC, typename XT, typename OT>
+template <bool LEFT, bool DIVIDE, bool ACC, typename XT, typename OT, int LPT>
 __global__ void __launch_bounds__(128) k_fdm_gemm32(const float* R, const XT* X, OT* out, int rows, int cols,
                                                    const float* dinv, int TK) {
   constexpr int TY = FDM_TY, TX = FDM_TX;
@@ -337,11 +337,11 @@ __global__ void __launch_bounds__(128) k_fdm_gemm32(const float* R, const XT* X,
     const int kc = min(TK, K - k0);
     if (LEFT) {
       // Rs[r][kk] = R[row0 + r][k0 + kk]; Xs[kk][c] = X[k0 + kk][col0 + c]  (coalesced)
-      stage_panel<float, float>(TY * kc, Rsm, [&](int t) {
+      stage_panel<LPT, float>(TY * kc, Rsm, [&](int t) {
         int r = t / kc, kk = t - r * kc;
         return row0 + r < rows ? R[(size_t)(row0 + r) * rows + k0 + kk] : 0.f;
       });
-      stage_panel<float2, float2>(kc * TX, Xsm, [&](int t) {
+      stage_panel<LPT, float2>(kc * TX, Xsm, [&](int t) {
         int kk = t / TX, c = t - kk * TX;
         return col0 + c < cols ? ld_f2(X + (size_t)(k0 + kk) * cols + col0 + c) : make_float2(0.f, 0.f);
       });
@@ -349,12 +349,12 @@ __global__ void __launch_bounds__(128) k_fdm_gemm32(const float* R, const XT* X,
 #pragma unroll 8
       for (int kk = 0; kk < kc; ++kk) acc = cfma(Rsm[ty * kc + kk], Xsm[kk * TX + tx], acc);
     } else {
-      stage_panel<float2, float2>(TY * kc, Xsm, [&](int t) {
+      stage_panel<LPT, float2>(TY * kc, Xsm, [&](int t) {
         int r = t / kc, kk = t - r * kc;
         return row0 + r < rows ? ld_f2(X + (size_t)(row0 + r) * cols + k0 + kk) : make_float2(0.f, 0.f);
       });
       // Rs[kk][c] = R[k0 + kk][col0 + c]  (c fastest: coalesced)
-      stage_panel<float, float>(kc * TX, Rsm, [&](int t) {
+      stage_panel<LPT, float>(kc * TX, Rsm, [&](int t) {
         int kk = t / TX, c = t - kk * TX;
         return col0 + c < cols ? R[(size_t)(k0 + kk) * cols + col0 + c] : 0.f;
       });
@@ -378,24 +378,27 @@ __global__ void __launch_bounds__(128) k_fdm_gemm32(const float* R, const XT* X,
 template <bool LEFT, bool DIVIDE, bool ACC, typename XT, typename OT>
 static void launch_fdm_gemm(iga_ctx* ctx, const float* R, const XT* X, OT* out, int rows, int cols,
                             const float* dinv) {
-  // the whole K extent in one stage up to 192 (one round of loads); longer
-  // panels in 64-deep stages (fewer loads in flight per thread per stage)
+  // up to FDM_TK the whole K extent in one stage, 16 loads in flight per
+  // thread; longer panels in 64-deep stages with 4 (measured faster there)
   const int K = LEFT ? rows : cols;
-  const int tk = K <= 192 ? K : 64;
   dim3 g(cdiv(cols, FDM_TX), cdiv(rows, FDM_TY));
-  k_fdm_gemm32<LEFT, DIVIDE, ACC, XT, OT><<<g, 128, fdm_gemm_smem(tk), ctx->st>>>(R, X, out, rows, cols, dinv, tk);
+  if (K <= FDM_TK) {
+    k_fdm_gemm32<LEFT, DIVIDE, ACC, XT, OT, 16><<<g, 128, fdm_gemm_smem(K), ctx->st>>>(R, X, out, rows, cols, dinv, K);
+  } else {
+    k_fdm_gemm32<LEFT, DIVIDE, ACC, XT, OT, 4><<<g, 128, fdm_gemm_smem(64), ctx->st>>>(R, X, out, rows, cols, dinv, 64);
+  }
   iga_count_launch();
 }
 
 // one-time: allow the whole-K panels above 48 KB of shared memory
 static iga_status fdm_gemm_attrs(iga_ctx* ctx) {
   const int sm = (int)fdm_gemm_smem(FDM_TK);
-  CK(cudaFuncSetAttribute(k_fdm_gemm32<false, true, false, double2, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-  CK(cudaFuncSetAttribute(k_fdm_gemm32<false, false, false, float2, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-  CK(cudaFuncSetAttribute(k_fdm_gemm32<false, false, true, float2, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-  CK(cudaFuncSetAttribute(k_fdm_gemm32<true, false, false, double2, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-  CK(cudaFuncSetAttribute(k_fdm_gemm32<false, true, false, float2, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-  CK(cudaFuncSetAttribute(k_fdm_gemm32<true, false, false, float2, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  CK(cudaFuncSetAttribute(k_fdm_gemm32<false, true, false, double2, float2, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  CK(cudaFuncSetAttribute(k_fdm_gemm32<false, false, false, float2, double2, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  CK(cudaFuncSetAttribute(k_fdm_gemm32<false, false, true, float2, double2, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  CK(cudaFuncSetAttribute(k_fdm_gemm32<true, false, false, double2, float2, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  CK(cudaFuncSetAttribute(k_fdm_gemm32<false, true, false, float2, float2, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  CK(cudaFuncSetAttribute(k_fdm_gemm32<true, false, false, float2, float2, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
   return IGA_OK;
 }
 

@@ -286,14 +286,21 @@ iga_status setup_tiled_transfers(iga_ctx* ctx) {
   return IGA_OK;
 }
 
-// x = Minv b, one block, dense
+// x = Minv b, dense: one warp per row, lanes over the columns, shuffle sum
+// (a row's dependent chain is a few FMAs instead of n)
 template <typename C>
 __global__ void k_dense_mv(int n, const C* Minv, const C* b, C* x) {
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    C acc = czero<C>();
-    for (int j = 0; j < n; ++j) acc = acc + cmul(Minv[(size_t)i * n + j], b[j]);
-    x[i] = acc;
+  const int lane = threadIdx.x & 31;
+  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (row >= n) return;
+  C acc = czero<C>();
+  for (int j = lane; j < n; j += 32) acc = acc + cmul(Minv[(size_t)row * n + j], b[j]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
   }
+  if (lane == 0) x[row] = acc;
 }
 
 // Gauss-Jordan inversion with partial pivoting (one block): A (n x n, row
@@ -530,7 +537,7 @@ iga_status mg_prolong_add(iga_ctx* ctx, int l, const typename cplx<T>::t* c, typ
 template <typename T>
 iga_status mg_coarse(iga_ctx* ctx, const typename cplx<T>::t* b, typename cplx<T>::t* x) {
   using C = typename cplx<T>::t;
-  k_dense_mv<C><<<1, 256, 0, ctx->st>>>(ctx->nc, LvBuf<T>::cinv(ctx), b, x); iga_count_launch();
+  k_dense_mv<C><<<cdiv(ctx->nc, 8), 256, 0, ctx->st>>>(ctx->nc, LvBuf<T>::cinv(ctx), b, x); iga_count_launch();
   CKL();
   return IGA_OK;
 }

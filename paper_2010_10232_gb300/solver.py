@@ -38,7 +38,7 @@ class Helmholtz:
 
     def __init__(self, dim=2, p=3, n_el=32, kfield=10.0, beta=(1.0, 0.5), eps=0.0, nu_pre=1, nu_post=1,
                  omega=0.6, n_vcycles=1, precision=0, flexible=0, skip_deflation=0, host_loop=0, arnoldi=None,
-                 fused_vcycle=1, stream=None):
+                 fused_vcycle=0, stream=None):
         self._L = _ffi.lib()
         prm = _ffi.IgaParams()
         self._L.iga_default_params(C.byref(prm))

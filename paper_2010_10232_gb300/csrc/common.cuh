@@ -37,7 +37,15 @@ __host__ __device__ __forceinline__ double2 cconjmul(double2 a, double2 b) { ret
 __host__ __device__ __forceinline__ double2 cfma(double s, double2 a, double2 acc) { return make_double2(fma(s, a.x, acc.x), fma(s, a.y, acc.y)); }
 __host__ __device__ __forceinline__ float2  cfma(float s, float2 a, float2 acc)    { return make_float2(fmaf(s, a.x, acc.x), fmaf(s, a.y, acc.y)); }
 __host__ __device__ __forceinline__ double2 cinv(double2 a) { double d = a.x * a.x + a.y * a.y; return make_double2(a.x / d, -a.y / d); }
-__host__ __device__ __forceinline__ float2  cinv(float2 a)  { float d = a.x * a.x + a.y * a.y; return make_float2(a.x / d, -a.y / d); }
+__host__ __device__ __forceinline__ float2  cinv(float2 a)  {   // one correctly rounded reciprocal on the device
+  float d = a.x * a.x + a.y * a.y;
+#ifdef __CUDA_ARCH__
+  float m = __frcp_rn(d);
+#else
+  float m = 1.0f / d;
+#endif
+  return make_float2(a.x * m, -a.y * m);
+}
 __host__ __device__ __forceinline__ double2 tod(float2 a) { return make_double2((double)a.x, (double)a.y); }
 __host__ __device__ __forceinline__ float2  tof(double2 a) { return make_float2((float)a.x, (float)a.y); }
 template <typename C> __host__ __device__ __forceinline__ C cconv(double2 a);

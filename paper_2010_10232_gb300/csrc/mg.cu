@@ -14,14 +14,14 @@ __global__ void k_jacobi0(int nx, int ny, int p, const T* K, const T* M, typenam
                           const typename cplx<T>::t* dinv, const typename cplx<T>::t* b,
                           typename cplx<T>::t* x, T omega) {
   using C = typename cplx<T>::t;
-  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (i >= (size_t)nx * ny) return;
+  const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;      // levels hold < 2^31 dofs
+  if (i >= (unsigned)nx * (unsigned)ny) return;
   C di;
   if (dinv) {
     di = dinv[i];
   } else {
     int W = 2 * p + 1;
-    int iy = (int)(i / nx), ix = (int)(i - (size_t)iy * nx);
+    int iy = (int)(i / (unsigned)nx), ix = (int)(i - (unsigned)iy * nx);
     T kx = K[(size_t)ix * W + p], mx = M[(size_t)ix * W + p];
     C d;
     if (ny == 1) {
@@ -131,8 +131,8 @@ __global__ void k_prolong_add(int nxf, int nyf, int nxc, int nyc, int wP, const 
 // one 1D window (p + 3 or p/2 + 3 taps) per output instead of the 2D window,
 // so a thread's dependent chain is a few FMAs (FP64 retires one warp
 // instruction per 64 cycles per SM sub-partition on this part).
-constexpr int TR_CT = 16;            // coarse tile of the restriction
-constexpr int TP_TX = 32, TP_TY = 8; // fine tile of the prolongation
+constexpr int TR_CT = 16;            // coarse tile of the restriction (TR_CT^2 = 256 threads)
+constexpr int TP_TX = 32, TP_TY = 32; // fine tile of the prolongation (32 x 8 on small levels)
 
 template <typename C, typename T>
 __host__ __device__ inline size_t tr_smem(int fmax, int wR) {
@@ -144,7 +144,8 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_restrict_tiled(int nxf, int nyf, int nxc, int nyc, int wR, const T* Rw,
                                                         const int* Rlo, int fmax, const typename cplx<T>::t* f,
                                                         typename cplx<T>::t* c, typename cplx<T>::t* xc,
-                                                        const typename cplx<T>::t* dinv, T omega) {
+                                                        const typename cplx<T>::t* dinv, T omega, int p,
+                                                        const T* Kc, const T* Mc, typename cplx<T>::t cm) {
   using C = typename cplx<T>::t;
   extern __shared__ __align__(16) unsigned char rsm[];
   C* fs = reinterpret_cast<C*>(rsm);                 // [FY][FX] fine footprint
@@ -160,28 +161,32 @@ __global__ void __launch_bounds__(256) k_restrict_tiled(int nxf, int nyf, int nx
   const int fy0 = max(0, Rlo[cy0]), fy1 = min(nyf, Rlo[cy0 + cyn - 1] + wR);
   const int FX = fx1 - fx0, FY = fy1 - fy0;
   if (FX > fmax || FY > fmax || FX < 1 || FY < 1) return;   // cannot happen: fmax is the maximum over tiles
-  for (int i = tid; i < FY * FX; i += 256) {
-    const int r = i / FX, q = i - r * FX;
-    fs[i] = f[(size_t)(fy0 + r) * nxf + fx0 + q];
-  }
+  const int lane = tid & 31, wp = tid >> 5;
+  for (int r = wp; r < FY; r += 8)                   // a warp per row: coalesced, no index division
+    for (int q = lane; q < FX; q += 32) fs[r * FX + q] = f[(size_t)(fy0 + r) * nxf + fx0 + q];
   for (int i = tid; i < cxn * wR; i += 256) Rwx[i] = Rw[(size_t)cx0 * wR + i];
   for (int i = tid; i < cyn * wR; i += 256) Rwy[i] = Rw[(size_t)cy0 * wR + i];
   if (tid < cxn) Rlox[tid] = Rlo[cx0 + tid] - fx0;
   if (tid < cyn) Rloy[tid] = Rlo[cy0 + tid] - fy0;
   __syncthreads();
-  for (int i = tid; i < FY * cxn; i += 256) {
-    const int r = i / cxn, jx = i - r * cxn;
-    C acc = czero<C>();
-    for (int t = 0; t < wR; ++t) {
-      const T w = Rwx[jx * wR + t];
-      const int q = Rlox[jx] + t;
-      if (w != (T)0 && q >= 0 && q < FX) acc = cfma(w, fs[r * FX + q], acc);
+  {
+    const int jx = tid & (TR_CT - 1);                // a thread per coarse column and every 16th row
+    if (jx < cxn) {
+      for (int r = tid / TR_CT; r < FY; r += 256 / TR_CT) {
+        C acc = czero<C>();
+        for (int t = 0; t < wR; ++t) {
+          const T w = Rwx[jx * wR + t];
+          const int q = Rlox[jx] + t;
+          if (w != (T)0 && q >= 0 && q < FX) acc = cfma(w, fs[r * FX + q], acc);
+        }
+        rx[r * TR_CT + jx] = acc;
+      }
     }
-    rx[r * TR_CT + jx] = acc;
   }
   __syncthreads();
-  for (int i = tid; i < cyn * cxn; i += 256) {
-    const int jy = i / cxn, jx = i - jy * cxn;
+  {
+    const int jy = tid / TR_CT, jx = tid & (TR_CT - 1);   // TR_CT^2 = 256: one coarse output per thread
+    if (jy >= cyn || jx >= cxn) return;
     C acc = czero<C>();
     for (int t = 0; t < wR; ++t) {
       const T w = Rwy[jy * wR + t];
@@ -190,66 +195,86 @@ __global__ void __launch_bounds__(256) k_restrict_tiled(int nxf, int nyf, int nx
     }
     const size_t o = (size_t)(cy0 + jy) * nxc + cx0 + jx;
     c[o] = acc;
-    if (xc) xc[o] = omega * cmul(dinv[o], acc);
+    if (xc) {
+      C di;
+      if (dinv) {
+        di = dinv[o];
+      } else {          // D_c from the coarse 1D band diagonals
+        const int W = 2 * p + 1, gx = cx0 + jx, gy = cy0 + jy;
+        const T kxd = Kc[gx * W + p], mxd = Mc[gx * W + p], kyd = Kc[gy * W + p], myd = Mc[gy * W + p];
+        di = cinv(myd * (mkc(kxd, (T)0) + mxd * cm) + mkc(kyd * mxd, (T)0));
+      }
+      xc[o] = omega * cmul(di, acc);
+    }
   }
 }
 
 template <typename C, typename T>
-__host__ __device__ inline size_t tp_smem(int cmax, int wP) {
-  return sizeof(C) * ((size_t)cmax * cmax + (size_t)cmax * TP_TX) + sizeof(T) * (TP_TX + TP_TY) * wP +
-         sizeof(int) * (TP_TX + TP_TY);
+__host__ __device__ inline size_t tp_smem(int cmax, int wP, int ty) {
+  return sizeof(C) * ((size_t)cmax * cmax + (size_t)cmax * TP_TX) + sizeof(T) * (TP_TX + ty) * wP +
+         sizeof(int) * (TP_TX + ty);
 }
 
-// f += P c on a fine TP_TX x TP_TY tile
-template <typename T>
+// f += P c on a fine TP_TX x TY tile: a lane per fine column, a warp per row;
+// the tile's f values are fetched first so their latency overlaps the
+// coarse-patch work
+template <typename T, int TY>
 __global__ void __launch_bounds__(256) k_prolong_tiled(int nxf, int nyf, int nxc, int nyc, int wP, const T* Pw,
                                                        const int* Plo, int cmax, const typename cplx<T>::t* c,
                                                        typename cplx<T>::t* f) {
   using C = typename cplx<T>::t;
+  constexpr int RPW = TY / 8;                        // fine rows per warp
   extern __shared__ __align__(16) unsigned char psm[];
   C* cs = reinterpret_cast<C*>(psm);                 // [CYN][CXN] coarse patch
   C* t1 = cs + (size_t)cmax * cmax;                  // [CYN][TP_TX] prolonged along x
   T* Pwx = reinterpret_cast<T*>(t1 + (size_t)cmax * TP_TX);
   T* Pwy = Pwx + TP_TX * wP;
-  int* Plox = reinterpret_cast<int*>(Pwy + TP_TY * wP);
+  int* Plox = reinterpret_cast<int*>(Pwy + TY * wP);
   int* Ploy = Plox + TP_TX;
-  const int tid = threadIdx.x;
-  const int x0 = blockIdx.x * TP_TX, y0 = blockIdx.y * TP_TY;
-  const int xn = min(TP_TX, nxf - x0), yn = min(TP_TY, nyf - y0);
+  const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
+  const int x0 = blockIdx.x * TP_TX, y0 = blockIdx.y * TY;
+  const int xn = min(TP_TX, nxf - x0), yn = min(TY, nyf - y0);
   const int cxa = max(0, Plo[x0]), cxb = min(nxc, Plo[x0 + xn - 1] + wP);
   const int cya = max(0, Plo[y0]), cyb = min(nyc, Plo[y0 + yn - 1] + wP);
   const int CXN = cxb - cxa, CYN = cyb - cya;
   if (CXN > cmax || CYN > cmax || CXN < 1 || CYN < 1) return;   // cannot happen: cmax is the maximum over tiles
-  for (int i = tid; i < CYN * CXN; i += 256) {
-    const int r = i / CXN, q = i - r * CXN;
-    cs[i] = c[(size_t)(cya + r) * nxc + cxa + q];
+  C fv[RPW];
+#pragma unroll
+  for (int k = 0; k < RPW; ++k) {
+    const int r = wp + 8 * k;
+    fv[k] = (r < yn && lane < xn) ? f[(size_t)(y0 + r) * nxf + x0 + lane] : czero<C>();
   }
+  for (int r = wp; r < CYN; r += 8)
+    for (int q = lane; q < CXN; q += 32) cs[r * CXN + q] = c[(size_t)(cya + r) * nxc + cxa + q];
   for (int i = tid; i < xn * wP; i += 256) Pwx[i] = Pw[(size_t)x0 * wP + i];
   for (int i = tid; i < yn * wP; i += 256) Pwy[i] = Pw[(size_t)y0 * wP + i];
   if (tid < xn) Plox[tid] = Plo[x0 + tid] - cxa;
   if (tid < yn) Ploy[tid] = Plo[y0 + tid] - cya;
   __syncthreads();
-  for (int i = tid; i < CYN * xn; i += 256) {
-    const int r = i / xn, q = i - r * xn;
-    C acc = czero<C>();
-    for (int t = 0; t < wP; ++t) {
-      const T w = Pwx[q * wP + t];
-      const int j = Plox[q] + t;
-      if (w != (T)0 && j >= 0 && j < CXN) acc = cfma(w, cs[r * CXN + j], acc);
+  if (lane < xn) {
+    for (int r = wp; r < CYN; r += 8) {
+      C acc = czero<C>();
+      for (int t = 0; t < wP; ++t) {
+        const T w = Pwx[lane * wP + t];
+        const int j = Plox[lane] + t;
+        if (w != (T)0 && j >= 0 && j < CXN) acc = cfma(w, cs[r * CXN + j], acc);
+      }
+      t1[r * TP_TX + lane] = acc;
     }
-    t1[r * TP_TX + q] = acc;
   }
   __syncthreads();
-  for (int i = tid; i < yn * xn; i += 256) {
-    const int r = i / xn, q = i - r * xn;
+  if (lane >= xn) return;
+#pragma unroll
+  for (int k = 0; k < RPW; ++k) {
+    const int r = wp + 8 * k;
+    if (r >= yn) break;
     C acc = czero<C>();
     for (int t = 0; t < wP; ++t) {
       const T w = Pwy[r * wP + t];
       const int j = Ploy[r] + t;
-      if (w != (T)0 && j >= 0 && j < CYN) acc = cfma(w, t1[j * TP_TX + q], acc);
+      if (w != (T)0 && j >= 0 && j < CYN) acc = cfma(w, t1[j * TP_TX + lane], acc);
     }
-    const size_t o = (size_t)(y0 + r) * nxf + x0 + q;
-    f[o] = f[o] + acc;
+    f[(size_t)(y0 + r) * nxf + x0 + lane] = fv[k] + acc;
   }
 }
 
@@ -278,7 +303,7 @@ iga_status setup_tiled_transfers(iga_ctx* ctx) {
         int xn = std::min(T_, F.nx - x0);
         cmax = std::max(cmax, std::min(Cl.nx, Plo[x0 + xn - 1] + F.wP) - std::max(0, Plo[x0]));
       }
-    if (tr_smem<double2, double>(fmax, F.wR) <= 48 * 1024 && tp_smem<double2, double>(cmax, F.wP) <= 48 * 1024) {
+    if (tr_smem<double2, double>(fmax, F.wR) <= 48 * 1024 && tp_smem<double2, double>(cmax, F.wP, TP_TY) <= 48 * 1024) {
       F.tr_fmax = fmax;
       F.tp_cmax = cmax;
     }
@@ -472,9 +497,11 @@ static void launch_restrict_tiled(iga_ctx* ctx, int l, const typename cplx<T>::t
   using C = typename cplx<T>::t;
   LevelData& F = ctx->lv[l];
   LevelData& Cc = ctx->lv[l + 1];
+  const C cm = cconv<C>(ctx->k2const * make_double2(-ctx->sig.x, -ctx->sig.y));
   dim3 g(cdiv(Cc.nx, TR_CT), cdiv(Cc.ny, TR_CT));
   k_restrict_tiled<T><<<g, 256, tr_smem<C, T>(F.tr_fmax, F.wR), ctx->st>>>(
-      F.nx, F.ny, Cc.nx, Cc.ny, F.wR, LvBuf<T>::Rw(F), F.Rlo, F.tr_fmax, f, c, xc, dinv, (T)ctx->prm.omega);
+      F.nx, F.ny, Cc.nx, Cc.ny, F.wR, LvBuf<T>::Rw(F), F.Rlo, F.tr_fmax, f, c, xc, dinv, (T)ctx->prm.omega, ctx->p,
+      LvBuf<T>::K(Cc), LvBuf<T>::M(Cc), cm);
   iga_count_launch();
 }
 
@@ -504,7 +531,7 @@ static iga_status mg_restrict_j0(iga_ctx* ctx, int l, const typename cplx<T>::t*
   double2 cm = make_double2(-ctx->sig.x, -ctx->sig.y);
   if (!ctx->vark) cm = ctx->k2const * cm;
   const C* dinv = jac_dinv<T>(ctx, Cc);
-  if (F.tr_fmax > 0 && dinv) {            // D_c^{-1} in memory (FP64, or variable k)
+  if (F.tr_fmax > 0 && (dinv || !ctx->vark)) {   // D_c^{-1} in memory, or from constant-k bands
     launch_restrict_tiled<T>(ctx, l, f, c, xc, dinv);
     CKL();
     return IGA_OK;
@@ -522,9 +549,15 @@ iga_status mg_prolong_add(iga_ctx* ctx, int l, const typename cplx<T>::t* c, typ
   LevelData& F = ctx->lv[l];
   LevelData& Cc = ctx->lv[l + 1];
   if (F.tp_cmax > 0) {
-    dim3 g(cdiv(F.nx, TP_TX), cdiv(F.ny, TP_TY));
-    k_prolong_tiled<T><<<g, 256, tp_smem<C, T>(F.tp_cmax, F.wP), ctx->st>>>(F.nx, F.ny, Cc.nx, Cc.ny, F.wP,
-                                                                          LvBuf<T>::Pw(F), F.Plo, F.tp_cmax, c, f);
+    if (F.nx >= 1024) {        // large level: 32 x 32 tiles, four rows per warp
+      dim3 g(cdiv(F.nx, TP_TX), cdiv(F.ny, 32));
+      k_prolong_tiled<T, 32><<<g, 256, tp_smem<C, T>(F.tp_cmax, F.wP, 32), ctx->st>>>(
+          F.nx, F.ny, Cc.nx, Cc.ny, F.wP, LvBuf<T>::Pw(F), F.Plo, F.tp_cmax, c, f);
+    } else {                   // enough blocks to fill the GPU on small levels
+      dim3 g(cdiv(F.nx, TP_TX), cdiv(F.ny, 8));
+      k_prolong_tiled<T, 8><<<g, 256, tp_smem<C, T>(F.tp_cmax, F.wP, 8), ctx->st>>>(
+          F.nx, F.ny, Cc.nx, Cc.ny, F.wP, LvBuf<T>::Pw(F), F.Plo, F.tp_cmax, c, f);
+    }
     iga_count_launch();
     CKL();
     return IGA_OK;

@@ -143,6 +143,8 @@ struct iga_ctx {
   double* mcb = nullptr;
   float2* cwf = nullptr;             // FP32 transform scratch
   float2* cwf2 = nullptr;
+  float2* ctf = nullptr;             // FP32 copies of Z^T x and of the refinement residual
+  float2* cef = nullptr;
   // variable-k E (block tridiagonal, banded in y): see deflation.cu
   int eblk = 0, enb = 0, els = 0;   // block size (lines per block * mx), number of blocks, lines
   double2* eDinv = nullptr;          // [enb][bs][bs] inverse diagonal blocks D_I^{-1}
@@ -244,7 +246,8 @@ iga_status setup_vark_diag(iga_ctx* ctx, int level);
 iga_status autotune_tiles(iga_ctx* ctx);
 // constant-coefficient tensor operator with explicit 1D bands (half width P)
 iga_status op_apply_bands(iga_ctx* ctx, int P, int nx, int ny, const double* K, const double* M, double2 c,
-                          const double2* x, double2* y, const double2* z, int epi);
+                          const double2* x, double2* y, const double2* z, int epi,
+                          float2* yf = nullptr);
 // op "which": 0 = A (c = -1), 1 = M_beta (c = -sigma)
 enum { OP_A = 0, OP_MB = 1 };
 // epilogues
@@ -262,9 +265,9 @@ template <typename T> iga_status mg_jacobi0(iga_ctx* ctx, int l, const typename 
 iga_status setup_coarse_inverse(iga_ctx* ctx);
 // deflation.cu
 iga_status setup_deflation(iga_ctx* ctx);
-iga_status defl_zt(iga_ctx* ctx, const double2* x, double2* c);
+iga_status defl_zt(iga_ctx* ctx, const double2* x, double2* c, float2* cf = nullptr);
 iga_status defl_z(iga_ctx* ctx, const double2* c, double2* x);
-iga_status defl_esolve(iga_ctx* ctx, const double2* t, double2* s);
+iga_status defl_esolve(iga_ctx* ctx, const double2* t, double2* s, const float2* tf = nullptr);
 iga_status defl_apply(iga_ctx* ctx, const double2* x, double2* y);        // y = P x
 iga_status defl_q(iga_ctx* ctx, const double2* x, double2* y);            // y = Q x
 // ecoarse.cu (variable k)

@@ -24,7 +24,7 @@ __device__ __forceinline__ double zt_w(int a, double eps) {   // a in -2..2
 }
 
 // c = Z^T x
-__global__ void k_zt(int nx, int ny, int mx, int my, double eps, const double2* x, double2* c) {
+__global__ void k_zt(int nx, int ny, int mx, int my, double eps, const double2* x, double2* c, float2* cf) {
   size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (j >= (size_t)mx * my) return;
   int jy = (int)(j / mx), jx = (int)(j - (size_t)jy * mx);
@@ -48,6 +48,7 @@ __global__ void k_zt(int nx, int ny, int mx, int my, double eps, const double2* 
     }
   }
   c[j] = acc;
+  if (cf) cf[j] = tof(acc);     // FP32 copy for the coarse solve's first transform
 }
 
 // 1D Z row for fine (0-based) i: up to 3 (coarse index, weight) pairs
@@ -522,7 +523,9 @@ iga_status setup_deflation(iga_ctx* ctx) {
   ctx->cw = dalloc<double2>(ctx, ctx->m);
   ctx->ce1 = dalloc<double2>(ctx, ctx->m);
   ctx->ce2 = dalloc<double2>(ctx, ctx->m);
-  if (!ctx->ce1 || !ctx->ce2) return set_err(ctx, IGA_E_OOM, "deflation alloc");
+  ctx->ctf = dalloc<float2>(ctx, ctx->m);
+  ctx->cef = dalloc<float2>(ctx, ctx->m);
+  if (!ctx->ce1 || !ctx->ce2 || !ctx->ctf || !ctx->cef) return set_err(ctx, IGA_E_OOM, "deflation alloc");
   ctx->kc = dalloc<double>(ctx, (size_t)ctx->mx * ctx->mx);
   ctx->mc = dalloc<double>(ctx, (size_t)ctx->mx * ctx->mx);
   if (!ctx->ct || !ctx->cs || !ctx->cw || !ctx->kc || !ctx->mc) return set_err(ctx, IGA_E_OOM, "deflation alloc");
@@ -533,10 +536,10 @@ iga_status setup_deflation(iga_ctx* ctx) {
   return fdm_setup(ctx);
 }
 
-iga_status defl_zt(iga_ctx* ctx, const double2* x, double2* c) {
+iga_status defl_zt(iga_ctx* ctx, const double2* x, double2* c, float2* cf) {
   const LevelData& L = ctx->lv[0];
   int my = ctx->dim == 2 ? ctx->mx : 1;
-  k_zt<<<cdiv(ctx->m, 256), 256, 0, ctx->st>>>(L.nx, L.ny, ctx->mx, my, ctx->prm.eps, x, c); iga_count_launch();
+  k_zt<<<cdiv(ctx->m, 256), 256, 0, ctx->st>>>(L.nx, L.ny, ctx->mx, my, ctx->prm.eps, x, c, cf); iga_count_launch();
   CKL();
   return IGA_OK;
 }
@@ -551,7 +554,10 @@ iga_status defl_z(iga_ctx* ctx, const double2* c, double2* x) {
 
 // s ~ E^{-1} t by fast diagonalisation with FP32 transforms (constant k); the
 // FP32 intermediates live in cwf, cwf2.
-static iga_status fdm_solve32(iga_ctx* ctx, const double2* t, double2* s, bool accumulate = false) {
+// tf (optional): the same right-hand side already rounded to FP32 (saves every
+// block of the first transform converting its FP64 panel)
+static iga_status fdm_solve32(iga_ctx* ctx, const double2* t, double2* s, bool accumulate = false,
+                              const float2* tf = nullptr) {
   const int mx = ctx->mx;
   const float* V = ctx->fdmVf;
   const float* Vt = ctx->fdmVtf;
@@ -562,7 +568,8 @@ static iga_status fdm_solve32(iga_ctx* ctx, const double2* t, double2* s, bool a
     else launch_fdm_gemm<false, false, false>(ctx, Vt, ctx->cwf, s, 1, mx, nullptr);
   } else {
     // T1 = V^T T; T2 = T1 V / D; T3 = V T2; S = T3 V^T (or s += S)
-    launch_fdm_gemm<true, false, false>(ctx, Vt, t, ctx->cwf, mx, mx, nullptr);
+    if (tf) launch_fdm_gemm<true, false, false>(ctx, Vt, tf, ctx->cwf, mx, mx, nullptr);
+    else launch_fdm_gemm<true, false, false>(ctx, Vt, t, ctx->cwf, mx, mx, nullptr);
     launch_fdm_gemm<false, true, false>(ctx, V, ctx->cwf, ctx->cwf2, mx, mx, ctx->fdmDinv);
     launch_fdm_gemm<true, false, false>(ctx, V, ctx->cwf2, ctx->cwf, mx, mx, nullptr);
     if (accumulate) launch_fdm_gemm<false, false, true>(ctx, Vt, ctx->cwf, s, mx, mx, nullptr);
@@ -578,15 +585,15 @@ static iga_status fdm_solve32(iga_ctx* ctx, const double2* t, double2* s, bool a
 // banded tensor-product kernel on the coarse grid).  Two steps bring the
 // solve to ~1e-11 of a sparse LU even where lambda_i + lambda_j ~ k^2 nearly
 // cancels.  Variable k: block LU.
-iga_status defl_esolve(iga_ctx* ctx, const double2* t, double2* s) {
+iga_status defl_esolve(iga_ctx* ctx, const double2* t, double2* s, const float2* tf) {
   if (ctx->vark) return block_E_solve(ctx, t, s);
-  TRY(fdm_solve32(ctx, t, s));
+  TRY(fdm_solve32(ctx, t, s, false, tf));
   const int bw = (ctx->p + 4) / 2;
   const int my = ctx->dim == 2 ? ctx->mx : 1;
   for (int it = 0; it < ctx->e_refine; ++it) {
     TRY(op_apply_bands(ctx, bw, ctx->mx, my, ctx->kcb, ctx->mcb, make_double2(-ctx->k2const, 0.0), s, ctx->ce1, t,
-                       EPI_ZMINUS));
-    TRY(fdm_solve32(ctx, ctx->ce1, s, true));          // s += FDM(r)
+                       EPI_ZMINUS, ctx->dim == 2 ? ctx->cef : nullptr));
+    TRY(fdm_solve32(ctx, ctx->ce1, s, true, ctx->dim == 2 ? ctx->cef : nullptr));   // s += FDM(r)
   }
   CKL();
   return IGA_OK;
@@ -594,8 +601,9 @@ iga_status defl_esolve(iga_ctx* ctx, const double2* t, double2* s) {
 
 // y = Q x = Z E^{-1} Z^T x
 iga_status defl_q(iga_ctx* ctx, const double2* x, double2* y) {
-  TRY(defl_zt(ctx, x, ctx->ct));
-  TRY(defl_esolve(ctx, ctx->ct, ctx->cs));
+  float2* ctf = (!ctx->vark && ctx->dim == 2) ? ctx->ctf : nullptr;
+  TRY(defl_zt(ctx, x, ctx->ct, ctf));
+  TRY(defl_esolve(ctx, ctx->ct, ctx->cs, ctf));
   return defl_z(ctx, ctx->cs, y);
 }
 

@@ -161,9 +161,10 @@ __global__ void __launch_bounds__(256) k_restrict_tiled(int nxf, int nyf, int nx
   const int fy0 = max(0, Rlo[cy0]), fy1 = min(nyf, Rlo[cy0 + cyn - 1] + wR);
   const int FX = fx1 - fx0, FY = fy1 - fy0;
   if (FX > fmax || FY > fmax || FX < 1 || FY < 1) return;   // cannot happen: fmax is the maximum over tiles
-  const int lane = tid & 31, wp = tid >> 5;
-  for (int r = wp; r < FY; r += 8)                   // a warp per row: coalesced, no index division
-    for (int q = lane; q < FX; q += 32) fs[r * FX + q] = f[(size_t)(fy0 + r) * nxf + fx0 + q];
+  for (int i = tid; i < FY * FX; i += 256) {         // flat over the footprint (measured faster than warp rows)
+    const int r = i / FX, q = i - r * FX;
+    fs[i] = f[(size_t)(fy0 + r) * nxf + fx0 + q];
+  }
   for (int i = tid; i < cxn * wR; i += 256) Rwx[i] = Rw[(size_t)cx0 * wR + i];
   for (int i = tid; i < cyn * wR; i += 256) Rwy[i] = Rw[(size_t)cy0 * wR + i];
   if (tid < cxn) Rlox[tid] = Rlo[cx0 + tid] - fx0;

@@ -25,6 +25,7 @@ template <typename T> struct OpArgs {
   C* y;
   const C* z;          // EPI_ZMINUS: minuend; EPI_JACOBI: right-hand side b
   const C* dinv;       // EPI_JACOBI with variable k: precomputed D^{-1}
+  float2* yf;          // EPI_ZMINUS: optional FP32 copy of y (nullptr: none)
   T omega;
   // variable k
   const T* B;          // [n_el][Q][p+1]
@@ -63,7 +64,11 @@ __device__ __forceinline__ void epilogue(const OpArgs<T>& a, size_t o, typename 
   if (EPI == EPI_Y) {
     a.y[o] = acc;
   } else if (EPI == EPI_ZMINUS) {
-    a.y[o] = a.z[o] - acc;
+    const C v = a.z[o] - acc;
+    a.y[o] = v;
+    if constexpr (sizeof(T) == 8) {
+      if (a.yf) a.yf[o] = tof(v);
+    }
   } else {
     C r = a.z[o] - acc;
     C di = a.dinv ? a.dinv[o] : cinv(diag);
@@ -404,7 +409,7 @@ iga_status op_apply(iga_ctx* ctx, int level, int which, const typename cplx<T>::
                     const typename cplx<T>::t* z, int epi, const typename cplx<T>::t* b, double omega) {
   using C = typename cplx<T>::t;
   const LevelData& L = ctx->lv[level];
-  OpArgs<T> a;
+  OpArgs<T> a{};
   a.nx = L.nx;
   a.ny = L.ny;
   a.n_el = L.n_el;
@@ -471,8 +476,9 @@ static void launch_bands(iga_ctx* ctx, const OpArgs<double>& a, int epi) {
 }
 
 iga_status op_apply_bands(iga_ctx* ctx, int P, int nx, int ny, const double* K, const double* M, double2 c,
-                          const double2* x, double2* y, const double2* z, int epi) {
+                          const double2* x, double2* y, const double2* z, int epi, float2* yf) {
   OpArgs<double> a{};
+  a.yf = yf;
   a.nx = nx;
   a.ny = ny;
   a.K = K;

@@ -194,10 +194,11 @@ iga_status iga_solve_host(iga_ctx* ctx, const iga_c128* rhs_host, iga_c128* x_ho
                           int maxit, int* iters, double* res_hist, double* true_res);
 
 /* Operator tile shape chosen by the setup-time autotuner for `level` and
-   precision (0 FP64, 1 FP32): 0 = 32x16, 1 = 16x16, 2 = 32x8 outputs per block,
-   -1 = not tuned (heuristic), -2 = bad argument.  The autotuner times the three
-   shapes on each level with >= 64^2 dofs (constant k, 2D) and caches the
-   choice per (p, precision, n_x) for the process. */
+   precision (0 FP64, 1 FP32): 0 = 32x16, 1 = 16x16, 2 = 32x8 outputs per
+   256-thread block, 3 = 8x8 per 64-thread block, -1 = not tuned (heuristic),
+   -2 = bad argument.  The autotuner times the four shapes on each level with
+   >= 64^2 dofs (constant k, 2D) and caches the choice per (p, precision, n_x)
+   for the process. */
 int iga_tile_choice(const iga_ctx* ctx, int level, int precision);
 
 /* Batched solves in one CUDA-graph launch (not in the paper; the batched form of

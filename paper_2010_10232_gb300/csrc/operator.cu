@@ -111,8 +111,8 @@ constexpr size_t kron2d_smem() {
   return sizeof(C) * ((TY + 2 * P) * (TX + 2 * P) + 2 * TY * (TX + 2 * P)) + sizeof(T) * (2 * TX + 2 * TY) * (2 * P + 1);
 }
 
-template <int P, typename T, int EPI, int TX, int TY>
-__global__ void __launch_bounds__(256) k_kron2d(OpArgs<T> a) {
+template <int P, typename T, int EPI, int TX, int TY, int NT = 256>
+__global__ void __launch_bounds__(NT) k_kron2d(OpArgs<T> a) {
   using C = typename cplx<T>::t;
   constexpr int W = 2 * P + 1, SX = TX + 2 * P, SY = TY + 2 * P;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -126,17 +126,17 @@ __global__ void __launch_bounds__(256) k_kron2d(OpArgs<T> a) {
   const int tid = threadIdx.x;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const int nx = a.nx, ny = a.ny;
-  for (int i = tid; i < SY * SX; i += 256) {
+  for (int i = tid; i < SY * SX; i += NT) {
     int r = i / SX, c = i - r * SX;
     int gy = y0 - P + r, gx = x0 - P + c;
     xs[i] = (gy >= 0 && gy < ny && gx >= 0 && gx < nx) ? a.x[(size_t)gy * nx + gx] : czero<C>();
   }
-  for (int i = tid; i < TX * W; i += 256) {
+  for (int i = tid; i < TX * W; i += NT) {
     int c = i / W, gx = x0 + c;
     kx[i] = gx < nx ? a.K[(size_t)x0 * W + i] : (T)0;
     mx[i] = gx < nx ? a.M[(size_t)x0 * W + i] : (T)0;
   }
-  for (int i = tid; i < TY * W; i += 256) {
+  for (int i = tid; i < TY * W; i += NT) {
     int r = i / W, gy = y0 + r;
     ky[i] = gy < ny ? a.K[(size_t)y0 * W + i] : (T)0;
     my[i] = gy < ny ? a.M[(size_t)y0 * W + i] : (T)0;
@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(256) k_kron2d(OpArgs<T> a) {
   // pass along y over the tile rows and all halo columns (the halo of the
   // wider tile side is the one recomputed, so the first pass does the least
   // redundant work): u = M_y x, w = c u + K_y x
-  for (int i = tid; i < TY * SX; i += 256) {
+  for (int i = tid; i < TY * SX; i += NT) {
     int r = i / SX, c = i - r * SX;
     C s1 = czero<C>(), s2 = czero<C>();
 #pragma unroll
@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(256) k_kron2d(OpArgs<T> a) {
   }
   __syncthreads();
   // pass along x: Op x = K_x u + M_x w
-  for (int i = tid; i < TY * TX; i += 256) {
+  for (int i = tid; i < TY * TX; i += NT) {
     int r = i / TX, c = i - r * TX;
     int gy = y0 + r, gx = x0 + c;
     if (gy >= ny || gx >= nx) continue;
@@ -349,17 +349,22 @@ __global__ void k_vark_diag(int nx, int n_el, int p, const double* K, const doub
 }
 
 // ------------------------------------------------------------------ host dispatch
-template <int P, typename T, int EPI, int TX, int TY>
+template <int P, typename T, int EPI, int TX, int TY, int NT = 256>
 static void launch_kron_tile(const OpArgs<T>& a, cudaStream_t st) {
   constexpr size_t sm = kron2d_smem<P, T, TX, TY>();
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_kron2d<P, T, EPI, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(k_kron2d<P, T, EPI, TX, TY, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     attr = true;
   }
   dim3 grid(cdiv(a.nx, TX), cdiv(a.ny, TY));
-  k_kron2d<P, T, EPI, TX, TY><<<grid, 256, sm, st>>>(a); iga_count_launch();
+  k_kron2d<P, T, EPI, TX, TY, NT><<<grid, NT, sm, st>>>(a); iga_count_launch();
 }
+
+// 8 x 8 tiles with 64 threads: on small levels (and the coarse E grid) more,
+// smaller blocks spread the FP64 dependency chains over more SMs
+template <int P, typename T, int EPI>
+static void launch_kron_small(const OpArgs<T>& a, cudaStream_t st) { launch_kron_tile<P, T, EPI, 8, 8, 64>(a, st); }
 
 template <int P, typename T, int EPI>
 static void launch_op(iga_ctx* ctx, const OpArgs<T>& a, int level) {
@@ -370,11 +375,14 @@ static void launch_op(iga_ctx* ctx, const OpArgs<T>& a, int level) {
     int tile = ctx->tile[level][sizeof(T) == 8 ? 0 : 1];
     if (tile < 0) {   // untuned: heuristic
       size_t big = (size_t)cdiv(a.nx, 32) * cdiv(a.ny, 16);
-      tile = big >= (size_t)3 * ctx->num_sms ? 0 : 1;
+      size_t mid = (size_t)cdiv(a.nx, 16) * cdiv(a.ny, 16);
+      // FP64 dependency chains favour more, smaller blocks on small grids
+      tile = big >= (size_t)3 * ctx->num_sms ? 0 : (mid >= (size_t)ctx->num_sms || sizeof(T) == 4 ? 1 : 3);
     }
     if (tile == 0) launch_kron_tile<P, T, EPI, 32, 16>(a, st);
     else if (tile == 1) launch_kron_tile<P, T, EPI, 16, 16>(a, st);
-    else launch_kron_tile<P, T, EPI, 32, 8>(a, st);
+    else if (tile == 2) launch_kron_tile<P, T, EPI, 32, 8>(a, st);
+    else launch_kron_small<P, T, EPI>(a, st);
   } else {
     constexpr size_t sm = elem2d_smem<P, T>();
     static bool attr = false;
@@ -471,8 +479,13 @@ static void launch_bands(iga_ctx* ctx, const OpArgs<double>& a, int epi) {
     else { k_kron1d<P, double, EPI_ZMINUS><<<cdiv(a.nx, 256), 256, 0, st>>>(a); iga_count_launch(); }
     return;
   }
-  if (epi == EPI_Y) launch_kron_tile<P, double, EPI_Y, 16, 16>(a, st);
-  else launch_kron_tile<P, double, EPI_ZMINUS, 16, 16>(a, st);
+  // the coarse grid is small (m_x ~ n_x / 2): 8 x 8 tiles unless 16 x 16 already fills the GPU
+  const bool small = (size_t)cdiv(a.nx, 16) * cdiv(a.ny, 16) < (size_t)ctx->num_sms;
+  if (epi == EPI_Y) {
+    if (small) launch_kron_small<P, double, EPI_Y>(a, st); else launch_kron_tile<P, double, EPI_Y, 16, 16>(a, st);
+  } else {
+    if (small) launch_kron_small<P, double, EPI_ZMINUS>(a, st); else launch_kron_tile<P, double, EPI_ZMINUS, 16, 16>(a, st);
+  }
 }
 
 iga_status op_apply_bands(iga_ctx* ctx, int P, int nx, int ny, const double* K, const double* M, double2 c,
@@ -500,8 +513,8 @@ iga_status op_apply_bands(iga_ctx* ctx, int P, int nx, int ny, const double* K, 
 }
 
 // ------------------------------------------------------------------ tile autotuner
-// For constant k in 2D the operator kernel has three tile shapes (32x16,
-// 16x16, 32x8 outputs per block).  At setup every level with at least 64^2
+// For constant k in 2D the operator kernel has four tile shapes (32x16,
+// 16x16, 32x8 outputs per 256-thread block, 8x8 per 64-thread block).  At setup every level with at least 64^2
 // dofs times each shape on the level's own operator (CUDA events, 2 warm-up +
 // 5 timed launches) in FP64 and FP32 and keeps the fastest.  Results are
 // cached per (p, precision, n_x) for the whole process, so batched instances
@@ -531,7 +544,7 @@ static iga_status tune_level(iga_ctx* ctx, int l, int slot) {
   CK(cudaEventCreate(&e1));
   float best = 1e30f;
   int best_tile = 0;
-  for (int t = 0; t < 3; ++t) {
+  for (int t = 0; t < 4; ++t) {
     ctx->tile[l][slot] = t;
     for (int w = 0; w < 2; ++w) TRY(op_apply<T>(ctx, l, OP_MB, x, y, nullptr, EPI_Y, nullptr, 0.0));
     CK(cudaEventRecord(e0, ctx->st));

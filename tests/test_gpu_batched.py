@@ -72,7 +72,7 @@ def test_autotuner_choices():
         for prec in (0, 1):
             c = L.iga_tile_choice(h._h, lvl, prec)
             if h.level_nx(lvl) >= 64:
-                assert c in (0, 1, 2)
+                assert c in (0, 1, 2, 3)
             else:
                 assert c == -1
     assert L.iga_tile_choice(h._h, 99, 0) == -2

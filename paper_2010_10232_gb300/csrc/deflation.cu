@@ -347,8 +347,17 @@ __global__ void __launch_bounds__(128) k_fdm_gemm32(const float* R, const XT* X,
         return col0 + c < cols ? ld_f2(X + (size_t)(k0 + kk) * cols + col0 + c) : make_float2(0.f, 0.f);
       });
       __syncthreads();
-#pragma unroll 8
-      for (int kk = 0; kk < kc; ++kk) acc = cfma(Rsm[ty * kc + kk], Xsm[kk * TX + tx], acc);
+      {   // four independent accumulators: a quarter of the dependent FMA chain
+        float2 a4[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+        int kk = 0;
+#pragma unroll 2
+        for (; kk + 4 <= kc; kk += 4) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) a4[u] = cfma(Rsm[ty * kc + kk + u], Xsm[(kk + u) * TX + tx], a4[u]);
+        }
+        for (; kk < kc; ++kk) a4[0] = cfma(Rsm[ty * kc + kk], Xsm[kk * TX + tx], a4[0]);
+        acc = acc + ((a4[0] + a4[1]) + (a4[2] + a4[3]));
+      }
     } else {
       stage_panel<LPT, float2>(TY * kc, Xsm, [&](int t) {
         int r = t / kc, kk = t - r * kc;
@@ -360,8 +369,17 @@ __global__ void __launch_bounds__(128) k_fdm_gemm32(const float* R, const XT* X,
         return col0 + c < cols ? R[(size_t)(k0 + kk) * cols + col0 + c] : 0.f;
       });
       __syncthreads();
-#pragma unroll 8
-      for (int kk = 0; kk < kc; ++kk) acc = cfma(Rsm[kk * TX + tx], Xsm[ty * kc + kk], acc);
+      {
+        float2 a4[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+        int kk = 0;
+#pragma unroll 2
+        for (; kk + 4 <= kc; kk += 4) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) a4[u] = cfma(Rsm[(kk + u) * TX + tx], Xsm[ty * kc + kk + u], a4[u]);
+        }
+        for (; kk < kc; ++kk) a4[0] = cfma(Rsm[kk * TX + tx], Xsm[ty * kc + kk], a4[0]);
+        acc = acc + ((a4[0] + a4[1]) + (a4[2] + a4[3]));
+      }
     }
     __syncthreads();
   }

@@ -106,14 +106,9 @@ struct GState {
   int* flag;       // [0] converged, [1] nonfinite
 };
 
-__device__ void givens_update(double2* Hj, int j, GState gs) {
-  for (int i = 0; i < j; ++i) {
-    double c = gs.cs[i];
-    double2 s = gs.sn[i];
-    double2 t = c * Hj[i] + cmul(s, Hj[i + 1]);
-    Hj[i + 1] = c * Hj[i + 1] - cconjmul(s, Hj[i]);
-    Hj[i] = t;
-  }
+// New rotation for column j (H[j][j], H[j+1][j] after the previous rotations),
+// applied to the column and to g; residual estimate and flags.
+__device__ void givens_new(double2* Hj, int j, GState gs) {
   double2 a = Hj[j], b = Hj[j + 1];
   double aa = hypot(a.x, a.y), ab = hypot(b.x, b.y);
   double c;
@@ -142,6 +137,47 @@ __device__ void givens_update(double2* Hj, int j, GState gs) {
   gs.hist[j + 1] = res;
   if (!isfinite(res)) gs.flag[1] = 1;
   if (res <= gs.scal[1]) gs.flag[0] = 1;
+}
+
+// Previous rotations applied to column j, then the new one (one thread).
+__device__ void givens_update(double2* Hj, int j, GState gs) {
+  for (int i = 0; i < j; ++i) {
+    double c = gs.cs[i];
+    double2 s = gs.sn[i];
+    double2 t = c * Hj[i] + cmul(s, Hj[i + 1]);
+    Hj[i + 1] = c * Hj[i + 1] - cconjmul(s, Hj[i]);
+    Hj[i] = t;
+  }
+  givens_new(Hj, j, gs);
+}
+
+// The same with the rotations' four real outputs (Re t, Im t, Re h, Im h) on
+// four lanes of one warp (called by all 32 lanes of the warp): every output
+// is c X + Y1 Z1 + Y2 Z2 with lane-selected operands, so a rotation costs
+// three FP64 instructions of the warp instead of twenty on one thread.
+__device__ void givens_update_warp(double2* Hj, int j, GState gs) {
+  const int lane = threadIdx.x & 31, k = lane & 3;
+  double2 a = Hj[0];                           // running H[i][j] after the previous rotations
+  for (int i = 0; i < j; ++i) {
+    const double c = gs.cs[i];
+    const double2 s = gs.sn[i], b = Hj[i + 1];
+    // t = c a + s b;  h = c b - conj(s) a
+    const double X = k == 0 ? a.x : k == 1 ? a.y : k == 2 ? b.x : b.y;
+    const double Y1 = k < 2 ? s.x : -s.x;
+    const double Z1 = k == 0 ? b.x : k == 1 ? b.y : k == 2 ? a.x : a.y;
+    const double Y2 = (k == 0 || k == 2) ? -s.y : s.y;
+    const double Z2 = k == 0 ? b.y : k == 1 ? b.x : k == 2 ? a.y : a.x;
+    const double o = fma(Y2, Z2, fma(Y1, Z1, c * X));
+    const double t_re = __shfl_sync(0xffffffffu, o, 0), t_im = __shfl_sync(0xffffffffu, o, 1);
+    const double h_re = __shfl_sync(0xffffffffu, o, 2), h_im = __shfl_sync(0xffffffffu, o, 3);
+    if (lane == 0) Hj[i] = make_double2(t_re, t_im);
+    a = make_double2(h_re, h_im);
+  }
+  if (lane == 0) {
+    Hj[j] = a;
+    givens_new(Hj, j, gs);
+  }
+  __syncwarp();
 }
 
 // v_{j+1} = w / ||w|| (w already holds the orthogonalised vector), H[j+1][j] =
@@ -491,15 +527,20 @@ __global__ void __launch_bounds__(CGS_T) k_cgs_normalize(double2* V, size_t ldv,
     last = atomicAdd(ticket, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (last && threadIdx.x == 0) {
+  if (last && threadIdx.x < 32) {            // one warp of the last block
     __threadfence();
-    *ticket = 0u;
     double2* hcol = H + (size_t)j * ldh;
-    hcol[j + 1] = make_double2(hn, 0.0);
-    givens_update(hcol, j, gs);
-    *jptr = j + 1;
-    unsigned go = (gs.flag[0] == 0 && gs.flag[1] == 0 && j + 1 < maxit) ? 1u : 0u;
-    if (use_cond) cudaGraphSetConditional(cond, go);
+    if (threadIdx.x == 0) {
+      *ticket = 0u;
+      hcol[j + 1] = make_double2(hn, 0.0);
+    }
+    __syncwarp();
+    givens_update_warp(hcol, j, gs);
+    if (threadIdx.x == 0) {
+      *jptr = j + 1;
+      unsigned go = (gs.flag[0] == 0 && gs.flag[1] == 0 && j + 1 < maxit) ? 1u : 0u;
+      if (use_cond) cudaGraphSetConditional(cond, go);
+    }
   }
 }
 

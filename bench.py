@@ -333,6 +333,14 @@ def _time_solves(h, f, x, stream, flush, reps):
     return sum(a.elapsed_time(b) for a, b in ev) / reps, it, tr
 
 
+def _measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
 def other_forms(h64, f, x, stream, flush, ws):
     """Mixed precision, learned correction and the batched 64-instance launch,
     each with its error against the oracle's direct FP64 solution."""
@@ -375,6 +383,27 @@ def other_forms(h64, f, x, stream, flush, ws):
             ms, it, tr = _time_solves(hm, f, xm, stream, flush, 5)
             out["learned_correction"] = {"ms": ms, "iterations": it, "true_res": tr,
                                          "rel_err_vs_oracle_direct": err(xm.cpu().numpy()), "tol_1e-10": tight(hm)}
+            # the network alone on the bench grid (one correction's inference)
+            nx = hm.level_nx(0)
+            xin = torch.zeros(1, nx, nx, 16, dtype=torch.bfloat16, device="cuda")
+            xin[..., :3] = torch.randn(1, nx, nx, 3, device="cuda").to(torch.bfloat16)
+            for _ in range(3):
+                net.forward(xin)
+            torch.cuda.synchronize()
+            a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a_.record()
+            for _ in range(20):
+                net.forward(xin)
+            b_.record()
+            torch.cuda.synchronize()
+            us = a_.elapsed_time(b_) / 20 * 1e3
+            flop = 2 * 9 * (3 * 32 + 32 * 32 + 32 * 32 + 32 * 2) * nx * nx     # algorithmic, unpadded channels
+            bf16_peak = _measured_peaks().get("bf16_tflops")
+            out["learned_correction"]["cnn_forward"] = {
+                "us": us, "pixels": nx * nx, "tflops": flop / us / 1e6,
+                "frac_of_bf16_peak": (flop / us / 1e6 / bf16_peak) if bf16_peak else None,
+                "note": "3x3 convs 3-32-32-32-2, bf16 mma.sync with FP32 accumulation; bound by launches "
+                        "and the pack/epilogue traffic at this size, not by the tensor pipe"}
             hm.attach(None)
         del hm
     except Exception as e:

@@ -94,7 +94,7 @@ __device__ __forceinline__ void mma_bf16(float* d, const unsigned* a, const unsi
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-constexpr int CV_TX = 16, CV_TY = 4;
+constexpr int CV_TX = 16, CV_TY = 16, CV_RPW = CV_TY / 4;   // 4 warps, CV_RPW pixel rows each (weights reused across rows)
 
 template <int CIN, int COUT>
 constexpr size_t conv_smem() {
@@ -131,33 +131,42 @@ __global__ void __launch_bounds__(128) k_conv3x3(const bf16* __restrict__ X, con
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = lane >> 2, tig = lane & 3;
   constexpr int NT = COUT / 8;
-  float acc[NT][4];
+  float acc[CV_RPW][NT][4];
 #pragma unroll
-  for (int nt = 0; nt < NT; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+  for (int r = 0; r < CV_RPW; ++r)
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) acc[r][nt][0] = acc[r][nt][1] = acc[r][nt][2] = acc[r][nt][3] = 0.f;
 #pragma unroll
   for (int t = 0; t < 9; ++t) {
     const int dy = t / 3, dx = t % 3;           // halo offsets 0..2
 #pragma unroll
     for (int kc = 0; kc < CIN / 16; ++kc) {
-      const bf16* r0 = Xs + ((warp + dy) * HX + (g + dx)) * XS + kc * 16 + 2 * tig;
-      const bf16* r1 = r0 + 8 * XS;             // pixel g + 8
-      unsigned a[4];
-      a[0] = *(const unsigned*)r0;
-      a[1] = *(const unsigned*)r1;
-      a[2] = *(const unsigned*)(r0 + 8);
-      a[3] = *(const unsigned*)(r1 + 8);
+      unsigned bb[NT][2];                       // weight fragments, reused by every row of the warp
 #pragma unroll
       for (int nt = 0; nt < NT; ++nt) {
         const bf16* wp = Ws + (nt * 8 + g) * WS + t * CIN + kc * 16 + 2 * tig;
-        unsigned bb[2];
-        bb[0] = *(const unsigned*)wp;
-        bb[1] = *(const unsigned*)(wp + 8);
-        mma_bf16(acc[nt], a, bb);
+        bb[nt][0] = *(const unsigned*)wp;
+        bb[nt][1] = *(const unsigned*)(wp + 8);
+      }
+#pragma unroll
+      for (int r = 0; r < CV_RPW; ++r) {
+        const int row = warp * CV_RPW + r;
+        const bf16* r0 = Xs + ((row + dy) * HX + (g + dx)) * XS + kc * 16 + 2 * tig;
+        const bf16* r1 = r0 + 8 * XS;           // pixel g + 8
+        unsigned a[4];
+        a[0] = *(const unsigned*)r0;
+        a[1] = *(const unsigned*)r1;
+        a[2] = *(const unsigned*)(r0 + 8);
+        a[3] = *(const unsigned*)(r1 + 8);
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) mma_bf16(acc[r][nt], a, bb[nt]);
       }
     }
   }
-  const int gy = y0 + warp;
-  if (gy >= H) return;
+#pragma unroll
+  for (int r = 0; r < CV_RPW; ++r) {
+  const int gy = y0 + warp * CV_RPW + r;
+  if (gy >= H) break;
 #pragma unroll
   for (int nt = 0; nt < NT; ++nt) {
     const int co = nt * 8 + 2 * tig;
@@ -166,7 +175,7 @@ __global__ void __launch_bounds__(128) k_conv3x3(const bf16* __restrict__ X, con
       const int gx = x0 + g + 8 * half;
       if (gx >= W) continue;
       const size_t p = img + (size_t)gy * W + gx;
-      float v0 = acc[nt][2 * half], v1 = acc[nt][2 * half + 1];
+      float v0 = acc[r][nt][2 * half], v1 = acc[r][nt][2 * half + 1];
       if (EPI == 0) {
         v0 = fmaxf(v0 + bias[co], 0.f);
         v1 = fmaxf(v1 + bias[co + 1], 0.f);
@@ -180,6 +189,7 @@ __global__ void __launch_bounds__(128) k_conv3x3(const bf16* __restrict__ X, con
         *(__nv_bfloat162*)((bf16*)Yout + p * COUT + co) = __floats2bfloat162_rn(v0, v1);
       }
     }
+  }
   }
 }
 

@@ -433,3 +433,35 @@ def test_vcycle_fused_levels(n_el, p, cycles):
             # kernels (both carry the FP32 rounding of the V-cycle, which
             # grows with p), and both stay within 1e-3 of the FP64 result
             assert ef <= max(2.0 * eu, 1e-5) and ef <= 1e-3, (ef, eu)
+
+
+@pytest.fixture(scope="module")
+def cfg3_full():
+    pr = W.config3()
+    d = asm.Discretization(2, pr.p, pr.n_el, pr.kfield)
+    return pr, d
+
+
+@pytest.mark.slow
+def test_config3_full_size_apply_and_solves(cfg3_full):
+    """Three-layer k (100/150/250), p = 3, 640 x 640 elements (410 881 dofs): the
+    oracle's sparse direct solve is out of reach at this size, so the check is by
+    properties the oracle can compute: sampled rows of A x against the oracle's
+    assembled matrix, and the true residual ||f - A u|| / ||f|| of the FP64 and
+    the FP32-V-cycle solutions of the first source, evaluated with that matrix,
+    against the residual the library reports."""
+    pr, d = cfg3_full
+    h64 = from_problem(pr)
+    x = rvec(h64.n, 101)
+    y = to_n(h64.apply_A(to_t(x)))
+    rows = np.random.default_rng(1).choice(h64.n, 4096, replace=False)
+    assert rel_err(y[rows], d.A[rows] @ x) <= 1e-13
+    f = asm.point_source(2, pr.p, pr.n_el, pr.sources[0])
+    for prec in (0, 1):
+        h = h64 if prec == 0 else from_problem(pr, precision=1)
+        u, it, hist, tr, st = h.solve(to_t(f), tol=1e-7, maxit=100)
+        assert st == 0 and 0 < it < 100
+        un = to_n(u)
+        true_res = np.linalg.norm(f - d.A @ un) / np.linalg.norm(f)
+        assert abs(true_res - tr) <= 1e-6 * tr + 1e-14
+        assert np.all(np.isfinite(un))

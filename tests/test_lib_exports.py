@@ -68,3 +68,28 @@ def test_setup_rejects_bad_parameters_without_gpu_work(lib_path):
     assert L.iga_setup(ctypes.byref(q), ctypes.byref(h)) == -1
     assert L.iga_setup(None, ctypes.byref(h)) == -1
     assert L.iga_solve(None, None, None, 1e-7, 10, None, None, None) == -1
+
+
+def test_params_struct_layout_matches_header(tmp_path):
+    """The ctypes mirror of iga_params has the header's size and field offsets
+    (checked by compiling a small C program against include/iga_helmholtz.h)."""
+    import shutil
+    import subprocess
+    from paper_2010_10232_gb300 import _ffi
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    fields = [f for f, _ in _ffi.IgaParams._fields_]
+    src = tmp_path / "layout.c"
+    prog = ['#include <stdio.h>', '#include <stddef.h>', '#include "iga_helmholtz.h"', 'int main(void) {',
+            '  printf("size %zu\\n", sizeof(iga_params));']
+    prog += [f'  printf("{f} %zu\\n", offsetof(iga_params, {f}));' for f in fields]
+    prog += ['  return 0;', '}']
+    src.write_text("\n".join(prog) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = dict(line.split() for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                         text=True).stdout.splitlines())
+    assert int(out["size"]) == ctypes.sizeof(_ffi.IgaParams)
+    for f in fields:
+        assert int(out[f]) == getattr(_ffi.IgaParams, f).offset, f

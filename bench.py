@@ -102,6 +102,21 @@ def _dist():
     return ws, rank, local
 
 
+def job_time(ms: float, ws: int, dist=None, device="cuda"):
+    """Replicas: every rank solves its own instance each step, so one step of
+    the job takes the slowest rank's time and retires ws solves.  Returns
+    (max over ranks of the per-step time, job-level time per solve).  The
+    reduction is a MAX all-reduce on `device` followed by a barrier; with one
+    rank (or no process group) it is the identity."""
+    if dist is not None and ws > 1:
+        import torch
+        t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    return ms, ms / ws
+
+
 # ---------------------------------------------------------------------------- CPU oracle legs
 ORACLE_SNIPPET = r"""
 import json, sys, time
@@ -186,17 +201,14 @@ def gpu_arm(args):
         torch.cuda.synchronize()
     launches = lib.iga_launch_count() - launches0 - 0   # fill_ is torch's, not counted
     ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        dist.barrier()
-    value = ms / ws          # job-level time per solve: N replicas solve N instances per step
+    ms, value = job_time(ms, ws, dist)     # job-level time per solve: N replicas solve N instances per step
 
     # ---- end to end through the public API with host buffers (copies inside the timed region)
     fh = f.cpu().numpy()
     h.solve_host(fh)
     torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
     e2e_t = []
     for k in range(max(3, args.steps // 2)):
         flush.fill_(k & 255)
@@ -205,6 +217,7 @@ def gpu_arm(args):
         xh, it2, *_ = h.solve_host(fh)
         e2e_t.append(time.perf_counter() - a)
     e2e_ms = 1000.0 * sum(e2e_t) / len(e2e_t)
+    _, e2e_ms = job_time(e2e_ms, ws, dist)
 
     # ---- dominant kernel: FP64 operator apply (constant-k banded tile kernel), timed alone
     peaks, src = _peaks()

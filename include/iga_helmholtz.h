@@ -195,11 +195,22 @@ iga_status iga_solve_host(iga_ctx* ctx, const iga_c128* rhs_host, iga_c128* x_ho
 
 /* Operator tile shape chosen by the setup-time autotuner for `level` and
    precision (0 FP64, 1 FP32): 0 = 32x16, 1 = 16x16, 2 = 32x8 outputs per
-   256-thread block, 3 = 8x8 per 64-thread block, -1 = not tuned (heuristic),
-   -2 = bad argument.  The autotuner times the four shapes on each level with
-   >= 64^2 dofs (constant k, 2D) and caches the choice per (p, precision, n_x)
-   for the process. */
+   256-thread block, 3 = 8x8 per 64-thread block; FP64 only: 4 = 8x8 per
+   256-thread block and 5 = 8x4 per 128-thread block with the real and
+   imaginary parts of each value on a lane pair; -1 = not tuned (heuristic),
+   -2 = bad argument.  The autotuner times every shape on each level with
+   n_x >= 8 (constant k, 2D), as dependent launches in one CUDA graph, and
+   caches the choice per (p, precision, n_x) for the process.  The E-residual
+   sweep on the deflation grid takes the FP64 choice of the level of nearest
+   n_x.  Constant k, 2D only (other operators have one kernel). */
 int iga_tile_choice(const iga_ctx* ctx, int level, int precision);
+
+/* Override the tile shape of `level` and `precision` (codes as above, -1 =
+   heuristic) for the calls that follow; every shape computes the same
+   operator.  Returns IGA_E_INVALID for a level or precision out of range or
+   a code the precision does not have.  Not stream-ordered: call it between
+   solves, not while work of this context is in flight or captured. */
+iga_status iga_set_tile(iga_ctx* ctx, int level, int precision, int tile);
 
 /* Batched solves in one CUDA-graph launch (not in the paper; the batched form of
    the method): instance b (context ctxs[b], each with its own k, p, mesh and

@@ -54,6 +54,7 @@ _SIG = {
     "iga_status_str": (C.c_char_p, [C.c_int]),
     "iga_launch_count": (C.c_ulonglong, []),
     "iga_tile_choice": (C.c_int, [_VP, C.c_int, C.c_int]),
+    "iga_set_tile": (C.c_int, [_VP, C.c_int, C.c_int, C.c_int]),
     "iga_solve_batched": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                                      C.POINTER(C.c_int), C.c_double, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                      _VP]),

@@ -178,6 +178,120 @@ __global__ void __launch_bounds__(NT) k_kron2d(OpArgs<T> a) {
   }
 }
 
+// ------------------------------------------------------------------ 2D constant k, FP64 lane pairs
+// The same two banded passes for small FP64 grids, with the real and the
+// imaginary part of every complex value on a lane pair (lane ^ 1): a thread
+// carries half as many FP64 FMA chains per pass.  On a small level the
+// time is the FP64 warp instructions each SM sub-partition issues (one per
+// 64 cycles on this part), and those are what the split halves.  The complex
+// factors (the mass coefficient c, D^{-1}) take the partner's component by a
+// shuffle.  Every thread runs the same number of rounds, so the shuffles see
+// full warps.
+template <int P, int TX, int TY>
+constexpr size_t kron2d_pair_smem() {
+  return sizeof(double2) * (TY + 2 * P) * (TX + 2 * P) + sizeof(double) * 4 * TY * (TX + 2 * P) +
+         sizeof(double) * (2 * TX + 2 * TY) * (2 * P + 1);
+}
+
+template <int P, int EPI, int TX, int TY, int NT>
+__global__ void __launch_bounds__(NT) k_kron2d_pair(OpArgs<double> a) {
+  constexpr int W = 2 * P + 1, SX = TX + 2 * P, SY = TY + 2 * P;
+  static_assert(NT % 32 == 0, "whole warps");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* xs = (double2*)smem_raw;            // [SY][SX]
+  double* us = (double*)(xs + SY * SX);         // [TY][SX][re, im]  M_y x
+  double* ws = us + 2 * TY * SX;                // [TY][SX][re, im]  c M_y x + K_y x
+  double* kx = ws + 2 * TY * SX;
+  double* mx = kx + TX * W;
+  double* ky = mx + TX * W;
+  double* my = ky + TY * W;
+  const int tid = threadIdx.x;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int nx = a.nx, ny = a.ny;
+  for (int i = tid; i < SY * SX; i += NT) {
+    int r = i / SX, c = i - r * SX;
+    int gy = y0 - P + r, gx = x0 - P + c;
+    xs[i] = (gy >= 0 && gy < ny && gx >= 0 && gx < nx) ? a.x[(size_t)gy * nx + gx] : make_double2(0.0, 0.0);
+  }
+  for (int i = tid; i < TX * W; i += NT) {
+    int c = i / W, gx = x0 + c;
+    kx[i] = gx < nx ? a.K[(size_t)x0 * W + i] : 0.0;
+    mx[i] = gx < nx ? a.M[(size_t)x0 * W + i] : 0.0;
+  }
+  for (int i = tid; i < TY * W; i += NT) {
+    int r = i / W, gy = y0 + r;
+    ky[i] = gy < ny ? a.K[(size_t)y0 * W + i] : 0.0;
+    my[i] = gy < ny ? a.M[(size_t)y0 * W + i] : 0.0;
+  }
+  __syncthreads();
+  const double* xd = (const double*)xs;
+  const double cre = a.c.x, cim = a.c.y;
+  // pass along y (tile rows, all halo columns); task q = 2 * point + component
+  constexpr int NY = 2 * TY * SX;
+  for (int base = 0; base < NY; base += NT) {
+    const int t = base + tid;
+    const int q = t < NY ? t : 0;
+    const int comp = q & 1, pt = q >> 1;
+    const int r = pt / SX, c = pt - r * SX;
+    double s1 = 0.0, s2 = 0.0;
+#pragma unroll
+    for (int d = 0; d < W; ++d) {
+      const double v = xd[2 * ((r + d) * SX + c) + comp];
+      s1 = fma(my[r * W + d], v, s1);
+      s2 = fma(ky[r * W + d], v, s2);
+    }
+    // w = c u + K_y x:  re = cre u_re - cim u_im + s2_re,  im = cre u_im + cim u_re + s2_im
+    const double so = __shfl_xor_sync(0xffffffffu, s1, 1);
+    const double w = fma(cre, s1, fma(comp ? cim : -cim, so, s2));
+    if (t < NY) {
+      us[q] = s1;
+      ws[q] = w;
+    }
+  }
+  __syncthreads();
+  // pass along x: Op x = K_x u + M_x w, then the epilogue per component
+  constexpr int NXT = 2 * TY * TX;
+  for (int base = 0; base < NXT; base += NT) {
+    const int t = base + tid;
+    const int q = t < NXT ? t : 0;
+    const int comp = q & 1, pt = q >> 1;
+    const int r = pt / TX, c = pt - r * TX;
+    const int gy = y0 + r, gx = x0 + c;
+    const bool ok = t < NXT && gy < ny && gx < nx;
+    double acc = 0.0;
+#pragma unroll
+    for (int d = 0; d < W; ++d) {
+      const int s = 2 * (r * SX + c + d) + comp;
+      acc = fma(kx[c * W + d], us[s], acc);
+      acc = fma(mx[c * W + d], ws[s], acc);
+    }
+    // clamped into the grid so that every lane may read (only `ok` lanes store)
+    const size_t o = (size_t)min(gy, ny - 1) * nx + min(gx, nx - 1);
+    if (EPI == EPI_Y) {
+      if (ok) ((double*)(a.y + o))[comp] = acc;
+    } else if (EPI == EPI_ZMINUS) {
+      if (ok) {
+        const double v = ((const double*)(a.z + o))[comp] - acc;
+        ((double*)(a.y + o))[comp] = v;
+        if (a.yf) ((float*)(a.yf + o))[comp] = (float)v;
+      }
+    } else {
+      // x_out = x + omega D^{-1} (b - Op x)
+      const double res = ((const double*)(a.z + o))[comp] - acc;
+      const double ro = __shfl_xor_sync(0xffffffffu, res, 1);
+      double2 di;
+      if (a.dinv) {
+        di = a.dinv[o];
+      } else {
+        const double kxd = kx[c * W + P], mxd = mx[c * W + P], kyd = ky[r * W + P], myd = my[r * W + P];
+        di = cinv(myd * (make_double2(kxd, 0.0) + mxd * a.c) + make_double2(kyd * mxd, 0.0));
+      }
+      const double dr = fma(di.x, res, (comp ? di.y : -di.y) * ro);
+      if (ok) ((double*)(a.y + o))[comp] = fma(a.omega, dr, xd[2 * ((r + P) * SX + c + P) + comp]);
+    }
+  }
+}
+
 // ------------------------------------------------------------------ 2D variable k
 constexpr int EL_T = 8;
 
@@ -366,6 +480,21 @@ static void launch_kron_tile(const OpArgs<T>& a, cudaStream_t st) {
 template <int P, typename T, int EPI>
 static void launch_kron_small(const OpArgs<T>& a, cudaStream_t st) { launch_kron_tile<P, T, EPI, 8, 8, 64>(a, st); }
 
+// FP64 lane-pair tiles: 4 = 8 x 8 outputs per 256-thread block, 5 = 8 x 4 per 128
+template <int P, int EPI, int TX, int TY, int NT>
+static void launch_kron_pair_tile(const OpArgs<double>& a, cudaStream_t st) {
+  constexpr size_t sm = kron2d_pair_smem<P, TX, TY>();
+  static_assert(sm <= 48 * 1024, "default shared-memory limit");
+  dim3 grid(cdiv(a.nx, TX), cdiv(a.ny, TY));
+  k_kron2d_pair<P, EPI, TX, TY, NT><<<grid, NT, sm, st>>>(a); iga_count_launch();
+}
+
+template <int P, int EPI>
+static void launch_kron_pair(const OpArgs<double>& a, cudaStream_t st, int tile) {
+  if (tile == 4) launch_kron_pair_tile<P, EPI, 8, 8, 256>(a, st);
+  else launch_kron_pair_tile<P, EPI, 8, 4, 128>(a, st);
+}
+
 template <int P, typename T, int EPI>
 static void launch_op(iga_ctx* ctx, const OpArgs<T>& a, int level) {
   cudaStream_t st = ctx->st;
@@ -382,6 +511,8 @@ static void launch_op(iga_ctx* ctx, const OpArgs<T>& a, int level) {
     if (tile == 0) launch_kron_tile<P, T, EPI, 32, 16>(a, st);
     else if (tile == 1) launch_kron_tile<P, T, EPI, 16, 16>(a, st);
     else if (tile == 2) launch_kron_tile<P, T, EPI, 32, 8>(a, st);
+    else if (tile == 3) launch_kron_small<P, T, EPI>(a, st);
+    else if constexpr (sizeof(T) == 8) launch_kron_pair<P, EPI>(a, st, tile);
     else launch_kron_small<P, T, EPI>(a, st);
   } else {
     constexpr size_t sm = elem2d_smem<P, T>();
@@ -479,9 +610,18 @@ static void launch_bands(iga_ctx* ctx, const OpArgs<double>& a, int epi) {
     else { k_kron1d<P, double, EPI_ZMINUS><<<cdiv(a.nx, 256), 256, 0, st>>>(a); iga_count_launch(); }
     return;
   }
-  // the coarse grid is small (m_x ~ n_x / 2): 8 x 8 tiles unless 16 x 16 already fills the GPU
+  // the coarse grid is small (m_x ~ n_x / 2): the small-tile shape the autotuner
+  // chose for the FP64 level of nearest size, else 8 x 8 tiles unless 16 x 16
+  // already fills the GPU
+  int tile = -1, dist = 1 << 30;
+  for (int l = 0; l < ctx->L; ++l) {
+    const int dd = abs(ctx->lv[l].nx - a.nx);
+    if (ctx->tile[l][0] >= 0 && dd < dist) { dist = dd; tile = ctx->tile[l][0]; }
+  }
   const bool small = (size_t)cdiv(a.nx, 16) * cdiv(a.ny, 16) < (size_t)ctx->num_sms;
-  if (epi == EPI_Y) {
+  if (tile >= 4) {
+    if (epi == EPI_Y) launch_kron_pair<P, EPI_Y>(a, st, tile); else launch_kron_pair<P, EPI_ZMINUS>(a, st, tile);
+  } else if (epi == EPI_Y) {
     if (small) launch_kron_small<P, double, EPI_Y>(a, st); else launch_kron_tile<P, double, EPI_Y, 16, 16>(a, st);
   } else {
     if (small) launch_kron_small<P, double, EPI_ZMINUS>(a, st); else launch_kron_tile<P, double, EPI_ZMINUS, 16, 16>(a, st);
@@ -513,18 +653,58 @@ iga_status op_apply_bands(iga_ctx* ctx, int P, int nx, int ny, const double* K, 
 }
 
 // ------------------------------------------------------------------ tile autotuner
-// For constant k in 2D the operator kernel has four tile shapes (32x16,
-// 16x16, 32x8 outputs per 256-thread block, 8x8 per 64-thread block).  At setup every level with at least 64^2
-// dofs times each shape on the level's own operator (CUDA events, 2 warm-up +
-// 5 timed launches) in FP64 and FP32 and keeps the fastest.  Results are
-// cached per (p, precision, n_x) for the whole process, so batched instances
-// of equal size are tuned once.
+// For constant k in 2D the operator kernel has six tile shapes: 32x16, 16x16,
+// 32x8 outputs per 256-thread block, 8x8 per 64-thread block, and (FP64 only)
+// the lane-pair kernel with 8x8 outputs per 256 threads or 8x4 per 128.  At
+// setup every level times each shape on its own operator, FP64 and FP32, as
+// the solve runs it: TUNE_REPS dependent launches captured in one CUDA graph
+// (host launch costs, which would hide the small levels' differences, stay
+// out of the measurement), and keeps the fastest.  Results are cached per
+// (p, precision, n_x) for the whole process, so batched instances of equal
+// size are tuned once.
 #include <map>
 #include <mutex>
 #include <tuple>
 
 static std::map<std::tuple<int, int, int>, int> g_tile_cache;
 static std::mutex g_tile_mu;
+constexpr int TUNE_REPS = 16;
+
+// in-graph time (ms) of TUNE_REPS applies of M_beta on level l with the current tile
+template <typename T>
+static iga_status time_in_graph(iga_ctx* ctx, int l, const typename cplx<T>::t* x, typename cplx<T>::t* y,
+                                cudaEvent_t e0, cudaEvent_t e1, float* ms) {
+  if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+  cudaStream_t saved = ctx->st;
+  // one untimed launch outside the capture (first-use attributes of the kernel)
+  TRY(op_apply<T>(ctx, l, OP_MB, x, y, nullptr, EPI_Y, nullptr, 0.0));
+  CK(cudaStreamSynchronize(ctx->st));
+  ctx->st = ctx->cap_stream;
+  const unsigned long long before = iga_launch_count();
+  cudaError_t e = cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) { ctx->st = saved; return set_err(ctx, IGA_E_CUDA, "tune capture: %s", cudaGetErrorString(e)); }
+  iga_status s = IGA_OK;
+  for (int r = 0; r < TUNE_REPS && s == IGA_OK; ++r) s = op_apply<T>(ctx, l, OP_MB, x, y, nullptr, EPI_Y, nullptr, 0.0);
+  cudaGraph_t g = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(ctx->st, &g);
+  ctx->st = saved;
+  iga_add_launches(-(long long)(iga_launch_count() - before));   // capture executes nothing
+  if (s != IGA_OK) { if (g) cudaGraphDestroy(g); return s; }
+  if (e2 != cudaSuccess) return set_err(ctx, IGA_E_CUDA, "tune end capture: %s", cudaGetErrorString(e2));
+  cudaGraphExec_t ge = nullptr;
+  cudaError_t e3 = cudaGraphInstantiate(&ge, g, 0);
+  cudaGraphDestroy(g);
+  if (e3 != cudaSuccess) return set_err(ctx, IGA_E_CUDA, "tune instantiate: %s", cudaGetErrorString(e3));
+  cudaError_t e4 = cudaGraphLaunch(ge, ctx->st);                 // warm-up
+  if (e4 == cudaSuccess) e4 = cudaEventRecord(e0, ctx->st);
+  if (e4 == cudaSuccess) e4 = cudaGraphLaunch(ge, ctx->st);
+  if (e4 == cudaSuccess) e4 = cudaEventRecord(e1, ctx->st);
+  if (e4 == cudaSuccess) e4 = cudaEventSynchronize(e1);
+  if (e4 == cudaSuccess) e4 = cudaEventElapsedTime(ms, e0, e1);
+  cudaGraphExecDestroy(ge);
+  if (e4 != cudaSuccess) return set_err(ctx, IGA_E_CUDA, "tune launch: %s", cudaGetErrorString(e4));
+  return IGA_OK;
+}
 
 template <typename T>
 static iga_status tune_level(iga_ctx* ctx, int l, int slot) {
@@ -544,19 +724,17 @@ static iga_status tune_level(iga_ctx* ctx, int l, int slot) {
   CK(cudaEventCreate(&e1));
   float best = 1e30f;
   int best_tile = 0;
-  for (int t = 0; t < 4; ++t) {
+  const int ntiles = sizeof(T) == 8 ? 6 : 4;
+  iga_status s = IGA_OK;
+  for (int t = 0; t < ntiles && s == IGA_OK; ++t) {
     ctx->tile[l][slot] = t;
-    for (int w = 0; w < 2; ++w) TRY(op_apply<T>(ctx, l, OP_MB, x, y, nullptr, EPI_Y, nullptr, 0.0));
-    CK(cudaEventRecord(e0, ctx->st));
-    for (int r = 0; r < 5; ++r) TRY(op_apply<T>(ctx, l, OP_MB, x, y, nullptr, EPI_Y, nullptr, 0.0));
-    CK(cudaEventRecord(e1, ctx->st));
-    CK(cudaEventSynchronize(e1));
     float ms = 0.f;
-    CK(cudaEventElapsedTime(&ms, e0, e1));
-    if (ms < best) { best = ms; best_tile = t; }
+    s = time_in_graph<T>(ctx, l, x, y, e0, e1, &ms);
+    if (s == IGA_OK && ms < best) { best = ms; best_tile = t; }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (s != IGA_OK) { ctx->tile[l][slot] = -1; return s; }
   ctx->tile[l][slot] = best_tile;
   std::lock_guard<std::mutex> lock(g_tile_mu);
   g_tile_cache[key] = best_tile;
@@ -566,10 +744,25 @@ static iga_status tune_level(iga_ctx* ctx, int l, int slot) {
 iga_status autotune_tiles(iga_ctx* ctx) {
   if (ctx->dim != 2 || ctx->vark) return IGA_OK;
   for (int l = 0; l < ctx->L; ++l) {
-    if (ctx->lv[l].nx < 64) continue;
+    if (ctx->lv[l].nx < 8) continue;
     TRY(tune_level<double>(ctx, l, 0));
     TRY(tune_level<float>(ctx, l, 1));
   }
+  return IGA_OK;
+}
+
+extern "C" iga_status iga_set_tile(iga_ctx* ctx, int level, int precision, int tile) {
+  if (!ctx) return IGA_E_INVALID;
+  if (level < 0 || level >= ctx->L || precision < 0 || precision > 1)
+    return set_err(ctx, IGA_E_INVALID, "iga_set_tile: level %d / precision %d out of range", level, precision);
+  if (tile < -1 || tile > (precision == 0 ? 5 : 3))
+    return set_err(ctx, IGA_E_INVALID, "iga_set_tile: tile %d not available in this precision", tile);
+  ctx->tile[level][precision] = tile;
+  // the cached loop graph captured the previous kernels
+  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+  if (ctx->graph) cudaGraphDestroy(ctx->graph);
+  ctx->gexec = nullptr;
+  ctx->graph = nullptr;
   return IGA_OK;
 }
 

@@ -107,6 +107,12 @@ class Helmholtz:
     def level_nx(self, level: int) -> int:
         return int(self._L.iga_level_nx(self._h, level))
 
+    def tile(self, level: int, precision: int = 0) -> int:
+        return int(self._L.iga_tile_choice(self._h, level, precision))
+
+    def set_tile(self, level: int, precision: int, tile: int) -> None:
+        self._check(self._L.iga_set_tile(self._h, level, precision, tile))
+
     def level_n(self, level: int) -> int:
         return self.level_nx(level) ** self.dim
 

@@ -71,8 +71,8 @@ def test_autotuner_choices():
     for lvl in range(h.levels):
         for prec in (0, 1):
             c = L.iga_tile_choice(h._h, lvl, prec)
-            if h.level_nx(lvl) >= 64:
-                assert c in (0, 1, 2, 3)
+            if h.level_nx(lvl) >= 8:
+                assert c in ((0, 1, 2, 3, 4, 5) if prec == 0 else (0, 1, 2, 3))
             else:
                 assert c == -1
     assert L.iga_tile_choice(h._h, 99, 0) == -2

@@ -192,6 +192,45 @@ def test_zt_z(name):
     assert rel_err(to_n(h.z(to_t(c))), Z @ c) <= 1e-14
 
 
+@pytest.mark.parametrize("tile", range(6))
+@pytest.mark.parametrize("name", ["2d_p1", "2d_p3", "2d_p5"])
+def test_every_tile_shape(name, tile):
+    """Each operator tile shape, forced on every level (FP64; the FP32 V-cycle
+    with the shapes FP32 has), against the oracle: the apply, the per-level
+    M_beta, Jacobi sweeps, the V-cycle, and the E solve whose refinement
+    residual takes the tile of the level of nearest size."""
+    pr = CASES[name]
+    s = ctx_and_oracle(name)[1]
+    h = from_problem(pr)
+    for l in range(h.levels):
+        h.set_tile(l, 0, tile)
+        assert h.tile(l, 0) == tile
+    x = rvec(h.n, 11)
+    assert rel_err(to_n(h.apply_A(to_t(x))), s.A @ x) <= 1e-13
+    for l, lvl in enumerate(s.mg.levels):
+        xl = rvec(lvl.Mb.shape[0], 20 + l)
+        assert rel_err(to_n(h.apply_Mshift(l, to_t(xl))), lvl.Mb @ xl) <= 1e-13, l
+    for l in (0, 1):
+        lvl = s.mg.levels[l]
+        b, x0 = rvec(lvl.Mb.shape[0], 30), rvec(lvl.Mb.shape[0], 31)
+        got = to_n(h.jacobi(l, to_t(b), to_t(x0), 2))
+        assert rel_err(got, s.mg.jacobi(lvl, x0.copy(), b, 2)) <= 1e-13, l
+    r = rvec(h.n, 80)
+    assert rel_err(to_n(h.vcycle(to_t(r))), s.mg.apply(r, 1)) <= 1e-11
+    t = rvec(h.m, 92)
+    assert rel_err(to_n(h.esolve(to_t(t))), s.defl.lu.solve(t)) <= 1e-10
+    if tile <= 3:
+        h32 = from_problem(pr, precision=1)
+        for l in range(h32.levels):
+            h32.set_tile(l, 1, tile)
+        assert rel_err(to_n(h32.vcycle(to_t(r))), s.mg.apply(r, 1)) <= 1e-4
+    else:
+        with pytest.raises(IgaError):
+            h.set_tile(0, 1, tile)
+    with pytest.raises(IgaError):
+        h.set_tile(h.levels, 0, 0)
+
+
 @pytest.mark.parametrize("name", ALL)
 def test_esolve_and_deflate(name):
     h, s, pr = ctx_and_oracle(name)

@@ -658,22 +658,25 @@ iga_status op_apply_bands(iga_ctx* ctx, int P, int nx, int ny, const double* K, 
 // the lane-pair kernel with 8x8 outputs per 256 threads or 8x4 per 128.  At
 // setup every level times each shape on its own operator, FP64 and FP32, as
 // the solve runs it: TUNE_REPS dependent launches captured in one CUDA graph
-// (host launch costs, which would hide the small levels' differences, stay
-// out of the measurement), and keeps the fastest.  Results are cached per
-// (p, precision, n_x) for the whole process, so batched instances of equal
-// size are tuned once.
+// per shape (host launch costs, which would hide the small levels'
+// differences, stay out of the measurement).  The graphs are timed in
+// TUNE_ROUNDS interleaved rounds and each shape keeps its fastest round, so a
+// clock ramp or a stray delay does not decide the choice.  Results are cached
+// per (p, precision, n_x) for the whole process, so batched instances of
+// equal size are tuned once.
 #include <map>
 #include <mutex>
 #include <tuple>
 
 static std::map<std::tuple<int, int, int>, int> g_tile_cache;
 static std::mutex g_tile_mu;
-constexpr int TUNE_REPS = 16;
+constexpr int TUNE_REPS = 24, TUNE_ROUNDS = 5, TUNE_MAX_TILES = 6;
 
-// in-graph time (ms) of TUNE_REPS applies of M_beta on level l with the current tile
+// graph of TUNE_REPS applies of M_beta on level l with the current tile
 template <typename T>
-static iga_status time_in_graph(iga_ctx* ctx, int l, const typename cplx<T>::t* x, typename cplx<T>::t* y,
-                                cudaEvent_t e0, cudaEvent_t e1, float* ms) {
+static iga_status capture_applies(iga_ctx* ctx, int l, const typename cplx<T>::t* x, typename cplx<T>::t* y,
+                                  cudaGraphExec_t* out) {
+  *out = nullptr;
   if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
   cudaStream_t saved = ctx->st;
   // one untimed launch outside the capture (first-use attributes of the kernel)
@@ -691,18 +694,9 @@ static iga_status time_in_graph(iga_ctx* ctx, int l, const typename cplx<T>::t* 
   iga_add_launches(-(long long)(iga_launch_count() - before));   // capture executes nothing
   if (s != IGA_OK) { if (g) cudaGraphDestroy(g); return s; }
   if (e2 != cudaSuccess) return set_err(ctx, IGA_E_CUDA, "tune end capture: %s", cudaGetErrorString(e2));
-  cudaGraphExec_t ge = nullptr;
-  cudaError_t e3 = cudaGraphInstantiate(&ge, g, 0);
+  cudaError_t e3 = cudaGraphInstantiate(out, g, 0);
   cudaGraphDestroy(g);
-  if (e3 != cudaSuccess) return set_err(ctx, IGA_E_CUDA, "tune instantiate: %s", cudaGetErrorString(e3));
-  cudaError_t e4 = cudaGraphLaunch(ge, ctx->st);                 // warm-up
-  if (e4 == cudaSuccess) e4 = cudaEventRecord(e0, ctx->st);
-  if (e4 == cudaSuccess) e4 = cudaGraphLaunch(ge, ctx->st);
-  if (e4 == cudaSuccess) e4 = cudaEventRecord(e1, ctx->st);
-  if (e4 == cudaSuccess) e4 = cudaEventSynchronize(e1);
-  if (e4 == cudaSuccess) e4 = cudaEventElapsedTime(ms, e0, e1);
-  cudaGraphExecDestroy(ge);
-  if (e4 != cudaSuccess) return set_err(ctx, IGA_E_CUDA, "tune launch: %s", cudaGetErrorString(e4));
+  if (e3 != cudaSuccess) { *out = nullptr; return set_err(ctx, IGA_E_CUDA, "tune instantiate: %s", cudaGetErrorString(e3)); }
   return IGA_OK;
 }
 
@@ -719,22 +713,42 @@ static iga_status tune_level(iga_ctx* ctx, int l, int slot) {
   C* x = (C*)(slot == 0 ? (void*)L.vb : (void*)L.fb);
   C* y = (C*)(slot == 0 ? (void*)L.vx : (void*)L.fx);
   CK(cudaMemsetAsync(x, 0, sizeof(C) * L.n, ctx->st));
-  cudaEvent_t e0, e1;
-  CK(cudaEventCreate(&e0));
-  CK(cudaEventCreate(&e1));
-  float best = 1e30f;
-  int best_tile = 0;
   const int ntiles = sizeof(T) == 8 ? 6 : 4;
+  cudaGraphExec_t ge[TUNE_MAX_TILES] = {};
+  cudaEvent_t ev[2 * TUNE_MAX_TILES] = {};
+  float best_ms[TUNE_MAX_TILES];
   iga_status s = IGA_OK;
   for (int t = 0; t < ntiles && s == IGA_OK; ++t) {
     ctx->tile[l][slot] = t;
-    float ms = 0.f;
-    s = time_in_graph<T>(ctx, l, x, y, e0, e1, &ms);
-    if (s == IGA_OK && ms < best) { best = ms; best_tile = t; }
+    best_ms[t] = 1e30f;
+    s = capture_applies<T>(ctx, l, x, y, &ge[t]);
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  for (int i = 0; i < 2 * ntiles && s == IGA_OK; ++i)
+    if (cudaEventCreate(&ev[i]) != cudaSuccess) s = set_err(ctx, IGA_E_CUDA, "tune events");
+  // one warm-up round, then TUNE_ROUNDS timed rounds over all shapes
+  for (int round = 0; round <= TUNE_ROUNDS && s == IGA_OK; ++round) {
+    cudaError_t e = cudaSuccess;
+    for (int t = 0; t < ntiles && e == cudaSuccess; ++t) {
+      e = cudaEventRecord(ev[2 * t], ctx->st);
+      if (e == cudaSuccess) e = cudaGraphLaunch(ge[t], ctx->st);
+      if (e == cudaSuccess) e = cudaEventRecord(ev[2 * t + 1], ctx->st);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
+    for (int t = 0; t < ntiles && e == cudaSuccess && round > 0; ++t) {
+      float ms = 0.f;
+      e = cudaEventElapsedTime(&ms, ev[2 * t], ev[2 * t + 1]);
+      if (e == cudaSuccess && ms < best_ms[t]) best_ms[t] = ms;
+    }
+    if (e != cudaSuccess) s = set_err(ctx, IGA_E_CUDA, "tune launch: %s", cudaGetErrorString(e));
+  }
+  for (int t = 0; t < ntiles; ++t)
+    if (ge[t]) cudaGraphExecDestroy(ge[t]);
+  for (int i = 0; i < 2 * ntiles; ++i)
+    if (ev[i]) cudaEventDestroy(ev[i]);
   if (s != IGA_OK) { ctx->tile[l][slot] = -1; return s; }
+  int best_tile = 0;
+  for (int t = 1; t < ntiles; ++t)
+    if (best_ms[t] < best_ms[best_tile]) best_tile = t;
   ctx->tile[l][slot] = best_tile;
   std::lock_guard<std::mutex> lock(g_tile_mu);
   g_tile_cache[key] = best_tile;

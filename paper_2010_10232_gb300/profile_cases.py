@@ -5,6 +5,9 @@
     python -m paper_2010_10232_gb300.profile_cases solve   # one bench solve
     python -m paper_2010_10232_gb300.profile_cases solve_host  # same, iterations launched from the host
 
+The solve cases open a profiler range around the solve only (capture them
+with `ncu --profile-from-start off`).
+
 Each case launches a handful of kernels on inputs of the bench problem so a
 capture (-k <kernel> -c <count>) ends in seconds.
 """
@@ -33,7 +36,13 @@ def main(case: str) -> None:
     elif case in ("solve", "solve_host"):
         h = Helmholtz(dim=2, p=3, n_el=320, kfield=200.0, host_loop=int(case == "solve_host"))
         f = h.point_source(0.5, 0.5)
+        torch.cuda.synchronize()
+        # the solve alone is the profiler range (ncu --profile-from-start off):
+        # the setup's launches, the tile autotuner's included, stay outside
+        torch.cuda.profiler.start()
         h.solve(f)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
     else:
         raise SystemExit(f"unknown case {case}")
     torch.cuda.synchronize()

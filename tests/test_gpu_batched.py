@@ -92,3 +92,23 @@ def test_cgs2_arnoldi_matches_mgs_and_oracle(precision):
     assert st == 0 and abs(it1 - it0) <= 1
     assert rel_err(x1.cpu().numpy(), ud) <= 1e-6
     assert rel_err(x1.cpu().numpy(), x0.cpu().numpy()) <= 1e-6
+
+
+def test_sharded_batched_equals_whole_batch():
+    """Instances split over two ranks (run one after the other on this GPU:
+    independent launches, nothing waits on another rank) give the whole
+    batch's iteration counts and solutions."""
+    from paper_2010_10232_gb300.sharding import solve_batched_sharded
+    probs = [(pr, len(pr.sources)) for pr, _ in _instances()]
+    whole, counts_whole = solve_batched_sharded(probs, 0, 1, precision=1)
+    assert sorted(whole) == list(range(len(probs)))
+    got = {}
+    for r in range(2):
+        sols, counts = solve_batched_sharded(probs, r, 2, precision=1)
+        assert sorted(sols) == sorted(counts)
+        for i, v in counts.items():
+            assert i not in got
+            got[i] = v
+            assert rel_err(sols[i].cpu().numpy(), whole[i].cpu().numpy()) <= 1e-12
+    assert got == counts_whole
+    assert all(st == [0] * len(st) for _, st in got.values())

@@ -100,3 +100,67 @@ def test_reference_arm_under_torchrun_prints_one_line(ws, tmp_path):
     assert rec["e2e"]["h2d_bytes_per_step"] == 0 and rec["e2e"]["d2h_bytes_per_step"] == 0
     assert rec["cpu_baseline"]["kind"] == "oracle"
     assert rec["value"] == rec["cpu_baseline"]["value"] > 0
+
+
+# ------------------------------------------------------------------ batched instances split by rank
+def _cfg4_work():
+    import workloads as W
+    from paper_2010_10232_gb300.sharding import instance_work
+    inst = W.config4(64)
+    return [instance_work((pr.n_el + pr.p - 2) ** pr.dim, nr) for pr, nr in inst]
+
+
+@pytest.mark.parametrize("world", [1, 2, 3, 8])
+def test_instance_split_covers_and_balances(world):
+    from paper_2010_10232_gb300.sharding import assign_instances, my_instances
+    work = _cfg4_work()
+    parts = assign_instances(work, world)
+    flat = sorted(i for p in parts for i in p)
+    assert flat == list(range(len(work)))                       # every instance exactly once
+    assert parts == assign_instances(list(work), world)         # same split on every rank
+    assert all(my_instances(work, r, world) == parts[r] for r in range(world))
+    loads = [sum(work[i] for i in p) for p in parts]
+    assert max(loads) - min(loads) <= max(work)                 # list-scheduling bound
+
+
+def test_instance_split_more_ranks_than_instances():
+    from paper_2010_10232_gb300.sharding import assign_instances
+    parts = assign_instances([5, 3], 4)
+    assert parts == [[0], [1], [], []]
+    with pytest.raises(ValueError):
+        assign_instances([1], 0)
+
+
+def _gather_worker(rank, ws, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    import torch.distributed as dist
+    from paper_2010_10232_gb300.sharding import my_instances, gather_counts
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    try:
+        work = _cfg4_work()
+        mine = my_instances(work, rank, ws)
+        # stand-in results of this rank's batched launch: iterations i + 10, status 0 per right-hand side
+        local = {i: ([i + 10] * 2, [0, 0]) for i in mine}
+        q.put((rank, mine, gather_counts(local, rank, ws, dist)))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_gather_counts_two_gloo_ranks():
+    """Each rank keeps its own instances; rank 0 alone receives every count, once."""
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_gather_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    (_, mine0, g0), (_, mine1, g1) = out
+    assert g1 is None
+    assert not set(mine0) & set(mine1) and len(mine0) + len(mine1) == 64
+    assert list(g0) == list(range(64))
+    assert all(g0[i] == ([i + 10] * 2, [0, 0]) for i in range(64))

@@ -16,6 +16,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import subprocess
 import sys
 import threading
@@ -132,15 +133,56 @@ print(json.dumps({{"setup_s": t1 - t0, "solve_s": times, "iters": iters, "true_r
 """
 
 
-def run_oracle(reps: int) -> dict:
-    """FP64 oracle on the host cores, single-threaded (BLAS threads pinned to 1)."""
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
-               CUDA_VISIBLE_DEVICES="")
+def run_oracle(reps: int, threads: int = 1) -> dict:
+    """FP64 oracle on the host cores: `threads` BLAS/OpenMP threads (1 =
+    single-threaded, the paper's serial setting)."""
+    t = str(int(threads))
+    env = dict(os.environ, OMP_NUM_THREADS=t, OPENBLAS_NUM_THREADS=t, MKL_NUM_THREADS=t, CUDA_VISIBLE_DEVICES="")
     code = ORACLE_SNIPPET.format(root=ROOT, k=K_WAVE, p=P_DEG, reps=reps)
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
     if out.returncode != 0:
         raise RuntimeError(out.stderr[-2000:])
     return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def host_cpu() -> dict:
+    """Core count and model of the host the oracle runs on."""
+    info = {"nproc": os.cpu_count(), "machine": platform.machine(), "model": None}
+    try:
+        with open("/proc/cpuinfo") as fh:
+            fields = {}
+            for line in fh:
+                if ":" in line:
+                    k_, v_ = (x.strip() for x in line.split(":", 1))
+                    fields.setdefault(k_, v_)
+        if "model name" in fields:
+            info["model"] = fields["model name"]
+        elif "CPU part" in fields:
+            info["model"] = f"implementer {fields.get('CPU implementer')} part {fields['CPU part']}"
+    except OSError:
+        pass
+    return info
+
+
+def cpu_baseline_record(reps: int = 3) -> dict:
+    """The oracle timed on this host: `reps` solves single-threaded (the
+    reported value, median) and `reps` with every core, setup and solve
+    reported separately."""
+    one = run_oracle(reps, 1)
+    med = lambda xs: sorted(xs)[len(xs) // 2]
+    rec = {"value": 1000.0 * med(one["solve_s"]), "unit": "ms", "cores": 1, "kind": "oracle",
+           "sample": f"{reps} full FP64 oracle solves of the bench problem, single-threaded, median, setup excluded",
+           "iters": one["iters"], "setup_s": one["setup_s"],
+           "solve_ms_runs": [1000.0 * x for x in one["solve_s"]], "host": host_cpu()}
+    ncores = os.cpu_count() or 1
+    if ncores > 1:
+        try:
+            allc = run_oracle(reps, ncores)
+            rec["all_cores"] = {"cores": ncores, "solve_ms_median": 1000.0 * med(allc["solve_s"]),
+                                "setup_s": allc["setup_s"], "iters": allc["iters"]}
+        except Exception as e:       # report, do not hide
+            rec["all_cores"] = {"cores": ncores, "error": str(e)[:200]}
+    return rec
 
 
 def reference_arm(args):
@@ -299,11 +341,7 @@ def gpu_arm(args):
     cpu = None
     if ws == 1 and not args.no_cpu:
         try:
-            r = run_oracle(3)
-            cpu_ms = 1000.0 * sum(r["solve_s"]) / len(r["solve_s"])
-            cpu = {"value": cpu_ms, "unit": "ms", "cores": 1, "kind": "oracle",
-                   "sample": "3 full FP64 oracle solves of the bench problem, single-threaded, setup excluded",
-                   "iters": r["iters"]}
+            cpu = cpu_baseline_record(3)
         except Exception as e:
             cpu = {"value": None, "unit": "ms", "cores": 1, "kind": "oracle", "sample": f"failed: {e}"[:200]}
     line = {

@@ -164,3 +164,9 @@ def test_gather_counts_two_gloo_ranks():
     assert not set(mine0) & set(mine1) and len(mine0) + len(mine1) == 64
     assert list(g0) == list(range(64))
     assert all(g0[i] == ([i + 10] * 2, [0, 0]) for i in range(64))
+
+
+def test_host_cpu_record():
+    import bench
+    info = bench.host_cpu()
+    assert info["nproc"] == os.cpu_count() and info["machine"]

@@ -180,10 +180,25 @@ class Discretization:
     def n(self) -> int:
         return self.S.shape[0]
 
-    def shifted(self, beta1: float, beta2: float):
-        """CSLP operator M_beta = S - (beta1 - i beta2) M^{k^2} (Section 3, CSLP
-        equation, read with the mass matrix in place of I)."""
-        return (self.S - (beta1 - 1j * beta2) * self.Mk).astype(np.complex128).tocsr()
+    def shifted(self, beta1: float, beta2: float, uses_mass: bool = True):
+        """CSLP operator of Section 3 (CSLP equation).
+
+        uses_mass=True (the reading used everywhere): M_beta = S - (beta1 -
+        i beta2) M^{k^2}, the shift on the mass matrix.  uses_mass=False: the
+        equation as printed, M = A + i beta2 k^2 I with A = S - beta1 M^{k^2}
+        (beta1 = 1 in the paper), the shift on the identity; defined here for
+        constant k only (the printed form does not say where a variable k^2
+        would be sampled).
+
+        Pins: tests/test_oracle_cslp.py (1D p = 1 closed-form eigenvalues of
+        both forms; the paper's Table 2 C_ex counts, met by the mass form only)."""
+        if uses_mass:
+            return (self.S - (beta1 - 1j * beta2) * self.Mk).astype(np.complex128).tocsr()
+        if len(self.kfield.lines) != 0:
+            raise ValueError("identity-shift CSLP is defined for constant k only")
+        k2 = float(self.kfield.values[0]) ** 2
+        ident = sp.identity(self.S.shape[0], format='csr')
+        return (self.S - beta1 * self.Mk + 1j * beta2 * k2 * ident).astype(np.complex128).tocsr()
 
 
 def point_source(dim: int, p: int, n_el: int, pos) -> np.ndarray:

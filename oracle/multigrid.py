@@ -79,9 +79,9 @@ def prolongation_interior_1d(n_el_coarse: int, p: int) -> np.ndarray:
 
 
 class Level:
-    def __init__(self, disc: Discretization, beta1: float, beta2: float):
+    def __init__(self, disc: Discretization, beta1: float, beta2: float, uses_mass: bool = True):
         self.disc = disc
-        self.Mb = disc.shifted(beta1, beta2)
+        self.Mb = disc.shifted(beta1, beta2, uses_mass)
         self.D = self.Mb.diagonal()
 
 
@@ -89,14 +89,14 @@ class MGHierarchy:
     """Rediscretised CSLP levels plus transfers for one problem description."""
 
     def __init__(self, dim, p, n_el, kfield, beta1, beta2, omega=0.6, nu_pre=1, nu_post=1,
-                 fine_disc: Discretization | None = None):
+                 fine_disc: Discretization | None = None, uses_mass: bool = True):
         self.sizes = level_sizes(n_el)
         self.omega, self.nu_pre, self.nu_post = omega, nu_pre, nu_post
         self.levels = []
         self.P = []
         for li, ne in enumerate(self.sizes):
             disc = fine_disc if (li == 0 and fine_disc is not None) else Discretization(dim, p, ne, kfield)
-            self.levels.append(Level(disc, beta1, beta2))
+            self.levels.append(Level(disc, beta1, beta2, uses_mass))
             if li > 0:
                 P1 = sp.csr_matrix(prolongation_interior_1d(ne, p))
                 self.P.append(P1 if dim == 1 else sp.kron(P1, P1).tocsr())

@@ -161,3 +161,35 @@ def test_point_source_partition_of_unity():
     for p in (1, 2, 4):
         f = asm.point_source(2, p, 12, (0.5, 0.5))
         assert abs(f.sum() - 1.0) < 1e-14      # boundary functions vanish at the centre
+
+
+def test_three_layer_k_at_hand_chosen_points():
+    """The three-layer field read for MP 2-B (interfaces y = 0.30 + 0.20 x and
+    y = 0.70 - 0.15 x; k = 100 below the first, 150 between, 250 above the
+    second; a point on an interface belongs to the layer above it).  Expected
+    values written by hand from that description, not from the KField
+    coefficients: points inside each layer, exactly on each line (where the
+    floating-point sums are exact), just below each line, the four corners,
+    and points that tell the two slopes apart."""
+    kf = W.three_layer_field()
+    pts = [
+        # (x, y, k): inside the layers
+        (0.5, 0.10, 100.0), (0.5, 0.50, 150.0), (0.5, 0.90, 250.0),
+        # exactly on a line at x = 0 (a*x = 0, so ((a x) + y) + c is exactly 0)
+        (0.0, 0.30, 150.0), (0.0, 0.70, 250.0),
+        # exactly on the first line at x = 1 (y = 0.5: 0.5 - 0.2 - 0.3 rounds to 0)
+        (1.0, 0.50, 150.0),
+        # just below each line
+        (0.0, 0.30 - 1e-9, 100.0), (0.0, 0.70 - 1e-9, 150.0),
+        # corners
+        (0.0, 0.0, 100.0), (1.0, 0.0, 100.0), (0.0, 1.0, 250.0), (1.0, 1.0, 250.0),
+        # slopes: the second line falls with x (0.685 at x = 0.1, 0.565 at x = 0.9),
+        # the first rises (0.32 at x = 0.1, 0.48 at x = 0.9)
+        (0.1, 0.62, 150.0), (0.9, 0.62, 250.0), (0.1, 0.40, 150.0), (0.9, 0.40, 100.0),
+    ]
+    x = np.array([p[0] for p in pts])
+    y = np.array([p[1] for p in pts])
+    want = np.array([p[2] for p in pts])
+    np.testing.assert_array_equal(asm.k_of(kf, x, y), want)
+    # the scaled field multiplies every layer value
+    np.testing.assert_array_equal(asm.k_of(W.three_layer_field(2.0), x, y), 2.0 * want)

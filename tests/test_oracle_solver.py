@@ -202,3 +202,31 @@ def test_planted_mistake_is_caught():
     good = s.defl.P(s.A @ s.Z[:, 3].toarray().ravel().astype(complex))
     bad = s.A @ s.Z[:, 3].toarray().ravel() + s.A @ s.defl.Q(s.A @ s.Z[:, 3].toarray().ravel())
     assert np.linalg.norm(good) < 1e-9 * np.linalg.norm(bad)
+
+
+@pytest.mark.parametrize("precond", ["mg", "none"])
+def test_literal_ordering_is_krylov_minimiser(precond):
+    """The literal ordering of Section 3's deflated system, GMRES on
+    P^T M~^{-1} A u = P^T M~^{-1} f from u = 0: after j steps its iterate is the
+    brute-force minimiser of ||b - B u|| over the Krylov space of the dense
+    B = P^T M~^{-1} A, b = P^T M~^{-1} f.  P is formed densely from its
+    definition I - A Z E^{-1} Z^T and transposed (not conjugated); M~^{-1} is the
+    V-cycle applied to unit vectors (or I without CSLP)."""
+    pr = W.small_2d(n_el=8, p=2, k=6.0)
+    if precond == "none":
+        pr.n_vcycles = 0
+    s = Solver(pr)
+    A = s.A.toarray()
+    Z = s.Z.toarray()
+    n = A.shape[0]
+    E = Z.T @ A @ Z
+    P = np.eye(n) - A @ Z @ np.linalg.solve(E, Z.T)
+    Minv = np.stack([s.precond(np.eye(n)[:, j].astype(complex)) for j in range(n)], axis=1)
+    B = P.T @ Minv @ A
+    f = s.load()
+    b = P.T @ (Minv @ f)
+    for j in (1, 3, 6):
+        r = s.solve(f, tol=0.0, maxit=j, variant='literal')
+        K = np.stack([np.linalg.matrix_power(B, i) @ b for i in range(j)], axis=1)
+        c, *_ = np.linalg.lstsq(B @ K, b, rcond=None)
+        np.testing.assert_allclose(r.u, K @ c, rtol=1e-8, atol=1e-10 * np.abs(K @ c).max())

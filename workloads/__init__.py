@@ -76,6 +76,9 @@ class Problem:
     n_vcycles: int = 1
     sources: list = field(default_factory=list)   # point-source positions
     name: str = ""
+    precond: str = "mg"               # "mg": n_vcycles V-cycles (0 = no CSLP); "exact": CSLP inverted exactly
+    deflation: bool = True            # ADP deflation on (D...) or off (C_ex alone)
+    shift_uses_mass: bool = True      # CSLP shift on the mass matrix (True) or the identity (False)
 
     @property
     def n_x(self) -> int:

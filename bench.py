@@ -281,13 +281,17 @@ def gpu_arm(args):
     apply_bytes = 32 * h.n
     # FP64 / FP32 FMA ceilings from the probe kernel
     sink = torch.zeros(2, dtype=torch.float64, device="cuda")
+    import measure
+    from measure import build as mbuild
+    mbuild.build()
+    mlib = measure.lib()
     probe = {}
     for prec, name in ((0, "fp64"), (1, "fp32")):
         fl = C.c_double(0.0)
         its = 4096 if prec == 0 else 65536
-        lib.iga_probe_fma(prec, 64, C.c_void_p(sink.data_ptr()), C.c_void_p(stream.cuda_stream), C.byref(fl))
+        mlib.measure_probe_fma(prec, 64, C.c_void_p(sink.data_ptr()), C.c_void_p(stream.cuda_stream), C.byref(fl))
         e0.record(stream)
-        lib.iga_probe_fma(prec, its, C.c_void_p(sink.data_ptr()), C.c_void_p(stream.cuda_stream), C.byref(fl))
+        mlib.measure_probe_fma(prec, its, C.c_void_p(sink.data_ptr()), C.c_void_p(stream.cuda_stream), C.byref(fl))
         e1.record(stream)
         torch.cuda.synchronize()
         probe[name] = fl.value / (e0.elapsed_time(e1) * 1e-3) / 1e12

@@ -88,12 +88,25 @@ typedef struct {
                               graph with a WHILE conditional node; 1: the host launches
                               each iteration and reads the convergence flag (profiling)   */
   void* stream;            /* cudaStream_t for all work of this context                   */
+  int precond;             /* preconditioner M~^{-1} of the solve (Section 4.3 list):
+                              0 (default): n_vcycles multigrid V-cycles of the CSLP
+                                 (C_MG^j); n_vcycles = 0 means no CSLP at all (the
+                                 deflation-only D / D_eps of Section 4.3.1);
+                              1: the CSLP matrix inverted exactly (C_ex): 2D/1D constant
+                                 k, n_x <= 2048, by fast diagonalisation of the finest
+                                 level with FP64 iterative refinement               */
+  int deflation;           /* 1 (default): ADP deflation, GMRES on M~^{-1} P A x^ =
+                              M~^{-1} P f, u = Q f + P^T x^ (the DEF1 reading of Section
+                              3's deflated system); 0: no deflation (GMRES on M~^{-1} A,
+                              C_ex / C_MG alone); 2: the literal ordering P^T M~^{-1} A u =
+                              P^T M~^{-1} f, iterate used as u (precision 0, flexible 0) */
 } iga_params;
 
 typedef struct iga_ctx iga_ctx;
 
 /* Fill *prm with the defaults: dim 2, p 3, n_el 32, k 10, beta (1, 0.5), eps 0,
-   nu 1/1, omega 0.6, one V-cycle, FP64, stream NULL. Host pointer. */
+   nu 1/1, omega 0.6, one V-cycle, FP64, DEF1 deflation, stream NULL. Host
+   pointer. */
 void iga_default_params(iga_params* prm);
 
 /* Build everything the solve needs on the device (Sections 2.3, 3): knots,
@@ -158,6 +171,12 @@ iga_status iga_coarse_solve(iga_ctx* ctx, const iga_c128* b, iga_c128* x);
    complex128.  In precision 1 the cycle runs in FP32 and r, z are converted. */
 iga_status iga_vcycle_cslp(iga_ctx* ctx, const iga_c128* r, iga_c128* z);
 
+/* z = M~^{-1} r, the preconditioner the solve applies (Section 4.3 list):
+   n_vcycles V-cycles (as iga_vcycle_cslp), the exact CSLP inverse M_beta^{-1}
+   (precond = 1; FP64 to ~1e-12 relative), or z = r (n_vcycles = 0).  r, z: n
+   complex128, must not alias. */
+iga_status iga_precond(iga_ctx* ctx, const iga_c128* r, iga_c128* z);
+
 /* Deflation pieces (Section 3, Eq. adef1 and the Z / Z^T stencils):
    zt: c = Z^T x (n -> m);  z: x = Z c (m -> n);  esolve: s = E^{-1} t (m);
    deflate: y = P x = x - A Z E^{-1} Z^T x (n). */
@@ -211,6 +230,18 @@ int iga_tile_choice(const iga_ctx* ctx, int level, int precision);
    a code the precision does not have.  Not stream-ordered: call it between
    solves, not while work of this context is in flight or captured. */
 iga_status iga_set_tile(iga_ctx* ctx, int level, int precision, int tile);
+
+/* Bounded device waits (failure detection without a GPU fault; not in the
+   paper).  The one wait in this library is the grid barrier of the
+   cooperative MGS Arnoldi step (arnoldi = 0); it gives up after `polls`
+   polls of ~64 ns (0 = the default 2^24, about one second), every block of
+   the step returns, the solve stops and iga_solve returns IGA_E_TIMEOUT with
+   the iterations done so far; the context stays usable.  phantom_arrivals = 1
+   makes the barrier wait for one block more than the grid has, which never
+   arrives: every wait then runs out (the deterministic way to exercise the
+   timeout path); 0 restores normal barriers.  Synchronises; takes effect
+   from the next solve. */
+iga_status iga_set_wait_limit(iga_ctx* ctx, long long polls, int phantom_arrivals);
 
 /* Batched solves in one CUDA-graph launch (not in the paper; the batched form of
    the method): instance b (context ctxs[b], each with its own k, p, mesh and
@@ -284,22 +315,19 @@ iga_status iga_net_pack(iga_ctx* ctx, const iga_c128* rt, const iga_c128* e, int
    blocks per SM).  Every GPU that loads the library holds that array until the
    process exits.  The function allocates nothing and calls no allocating
    library routine.  The first call on a device looks up the array's device
-   address (cudaGetSymbolAddress) with that device current; make that first
-   call before any stream capture.  All calls share the one array and it keeps
+   address (cudaGetSymbolAddress) with that device current and keeps it for
+   the rest of the process; make that first call before any stream capture,
+   and do not call the function on a device after cudaDeviceReset (the kept
+   address would no longer be valid).  All calls share the one array and it keeps
    the last call's contents (every entry is written before it is read), so two
    calls whose work overlaps on the GPU race: order them on one stream.
-   Errors: IGA_E_INVALID for NULL/misaligned pointers, n = 0, ldv < n, j < 0,
-   or a device whose reduction grid would exceed the 1024-block scratch;
+   Errors (no text is printed; there is no context to hold a message):
+   IGA_E_INVALID for NULL/misaligned pointers, n = 0, ldv < n, j < 0, or a
+   device with more than 512 SMs, whose reduction grid would exceed the
+   1024-block scratch;
    IGA_E_CUDA if the symbol lookup or a launch fails. */
 iga_status iga_mgs_noalloc(const iga_c128* V, size_t ldv, size_t n, int j, iga_c128* w, iga_c128* h,
                            void* stream);
-
-/* Measurement helper (no counterpart in the paper): launches 8 independent
-   FMA chains per thread on 8 x SM-count blocks of 256 threads, in FP64
-   (precision 0) or FP32 (1), on `stream`; *flops (HOST) receives the flop count
-   of the launch, so the caller can time it and state the ALU ceiling that
-   bounds the FP64 operators.  sink: device scratch of one double. */
-iga_status iga_probe_fma(int precision, int iters, void* sink, void* stream, double* flops);
 
 #ifdef __cplusplus
 }

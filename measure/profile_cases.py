@@ -1,9 +1,9 @@
 """Small, self-contained launch sequences for Nsight Compute captures.
 
-    python -m paper_2010_10232_gb300.profile_cases apply   # FP64 constant-k apply, bench size
-    python -m paper_2010_10232_gb300.profile_cases apply32 # FP32 M_beta Jacobi sweep, 4097^2 dofs
-    python -m paper_2010_10232_gb300.profile_cases solve   # one bench solve
-    python -m paper_2010_10232_gb300.profile_cases solve_host  # same, iterations launched from the host
+    python -m measure.profile_cases apply   # FP64 constant-k apply, bench size
+    python -m measure.profile_cases apply32 # FP32 V-cycle, 4097^2 dofs
+    python -m measure.profile_cases solve   # one bench solve
+    python -m measure.profile_cases solve_host  # same, iterations launched from the host
 
 The solve cases open a profiler range around the solve only (capture them
 with `ncu --profile-from-start off`).
@@ -17,7 +17,7 @@ import sys
 
 import torch
 
-from .solver import Helmholtz
+from paper_2010_10232_gb300.solver import Helmholtz
 
 
 def main(case: str) -> None:

@@ -38,6 +38,8 @@ class IgaParams(C.Structure):
         ("fused_vcycle", C.c_int),
         ("host_loop", C.c_int),
         ("stream", C.c_void_p),
+        ("precond", C.c_int),
+        ("deflation", C.c_int),
     ]
 
 
@@ -71,7 +73,6 @@ _SIG = {
     "iga_precond_pair": (C.c_int, [_VP, _VP, _VP, _VP, C.c_int]),
     "iga_net_pack": (C.c_int, [_VP, _VP, _VP, C.c_int, C.c_int, C.c_int, C.c_int, _VP, _VP, C.c_double]),
     "iga_mgs_noalloc": (C.c_int, [_VP, C.c_size_t, C.c_size_t, C.c_int, _VP, _VP, _VP]),
-    "iga_probe_fma": (C.c_int, [C.c_int, C.c_int, _VP, _VP, C.POINTER(C.c_double)]),
     "iga_last_error": (C.c_char_p, [_VP]),
     "iga_get_knots": (C.c_int, [_VP, C.c_int, _VP, C.c_int]),
     "iga_get_band": (C.c_int, [_VP, C.c_int, C.c_int, _VP, C.c_size_t]),
@@ -83,6 +84,8 @@ _SIG = {
     "iga_prolong_add": (C.c_int, [_VP, C.c_int, _VP, _VP]),
     "iga_coarse_solve": (C.c_int, [_VP, _VP, _VP]),
     "iga_vcycle_cslp": (C.c_int, [_VP, _VP, _VP]),
+    "iga_precond": (C.c_int, [_VP, _VP, _VP]),
+    "iga_set_wait_limit": (C.c_int, [_VP, C.c_longlong, C.c_int]),
     "iga_zt": (C.c_int, [_VP, _VP, _VP]),
     "iga_z": (C.c_int, [_VP, _VP, _VP]),
     "iga_esolve": (C.c_int, [_VP, _VP, _VP]),

@@ -36,6 +36,8 @@ void iga_default_params(iga_params* prm) {
   d.arnoldi = 1;
   d.fused_vcycle = 0;
   d.stream = nullptr;
+  d.precond = 0;
+  d.deflation = 1;
   *prm = d;
 }
 
@@ -83,7 +85,11 @@ iga_status iga_setup(const iga_params* prm, iga_ctx** out) {
   if (P.p < 1 || P.p > IGA_MAXP) return IGA_E_INVALID;
   if (P.n_el < 2 || P.n_el + P.p - 2 < 2) return IGA_E_INVALID;
   if (P.n_lines < 0 || P.n_lines > IGA_MAX_LINES || (P.n_lines > 0 && P.dim != 2)) return IGA_E_INVALID;
-  if (!(P.omega > 0.0) || P.nu_pre < 0 || P.nu_post < 0 || P.n_vcycles < 1) return IGA_E_INVALID;
+  if (!(P.omega > 0.0) || P.nu_pre < 0 || P.nu_post < 0 || P.n_vcycles < 0) return IGA_E_INVALID;
+  if (P.precond < 0 || P.precond > 1 || P.deflation < 0 || P.deflation > 2) return IGA_E_INVALID;
+  if (P.precond == 0 && P.n_vcycles < 1 && P.deflation == 0) return IGA_E_INVALID;   // nothing left to solve with
+  if (P.deflation == 2 && (P.precision != 0 || P.flexible != 0)) return IGA_E_INVALID;
+  if (P.precond == 1 && P.n_lines > 0) return IGA_E_UNSUPPORTED;
   if (P.precision < 0 || P.precision > 1) return IGA_E_INVALID;
   if (P.arnoldi < 0 || P.arnoldi > 1) return IGA_E_INVALID;
   if (P.fused_vcycle < 0 || P.fused_vcycle > 1) return IGA_E_INVALID;
@@ -132,7 +138,8 @@ iga_status iga_setup(const iga_params* prm, iga_ctx** out) {
       s = set_err(ctx, IGA_E_OOM, "work vectors");
       break;
     }
-    if (!P.skip_deflation && (s = setup_deflation(ctx)) != IGA_OK) break;
+    if (!P.skip_deflation && P.deflation != 0 && (s = setup_deflation(ctx)) != IGA_OK) break;
+    if (P.precond == 1 && (s = setup_exact_cslp(ctx)) != IGA_OK) break;
     cudaError_t e = cudaStreamSynchronize(ctx->st);
     if (e != cudaSuccess) { s = set_err(ctx, IGA_E_CUDA, "setup: %s", cudaGetErrorString(e)); break; }
   } while (0);
@@ -203,7 +210,8 @@ iga_status iga_get_prolongation(iga_ctx* ctx, int level, double* out, size_t cap
 }
 
 #define CHECK_CTX() do { if (!ctx) return IGA_E_INVALID; } while (0)
-#define CHECK_DEFL() do { if (ctx->prm.skip_deflation) return set_err(ctx, IGA_E_INVALID, "context built without deflation"); } while (0)
+#define CHECK_DEFL() do { if (ctx->prm.skip_deflation || ctx->prm.deflation == 0) return set_err(ctx, IGA_E_INVALID, "context built without deflation"); } while (0)
+#define CHECK_SOLVE() do { if (ctx->prm.skip_deflation) return set_err(ctx, IGA_E_INVALID, "context built for operators only"); } while (0)
 #define CHECK_PTR(p) do { if (!aligned16(p)) return set_err(ctx, IGA_E_INVALID, "pointer %s NULL or not 16-byte aligned", #p); } while (0)
 
 iga_status iga_apply_A(iga_ctx* ctx, const iga_c128* x, iga_c128* y) {
@@ -253,6 +261,7 @@ iga_status iga_coarse_solve(iga_ctx* ctx, const iga_c128* b, iga_c128* x) {
 
 iga_status iga_vcycle_cslp(iga_ctx* ctx, const iga_c128* r, iga_c128* z) {
   CHECK_CTX(); CHECK_PTR(r); CHECK_PTR(z);
+  if (ctx->prm.n_vcycles < 1) return set_err(ctx, IGA_E_INVALID, "context built with n_vcycles = 0");
   if ((const void*)r == (const void*)z) return set_err(ctx, IGA_E_INVALID, "r and z alias");
   if (ctx->prm.precision == 0) return mg_vcycle<double>(ctx, (const double2*)r, (double2*)z);
   size_t n = ctx->lv[0].n;
@@ -262,6 +271,12 @@ iga_status iga_vcycle_cslp(iga_ctx* ctx, const iga_c128* r, iga_c128* z) {
   launch_convert_f2d(ctx->fout, (double2*)z, n, ctx->st);
   CKL();
   return IGA_OK;
+}
+
+iga_status iga_precond(iga_ctx* ctx, const iga_c128* r, iga_c128* z) {
+  CHECK_CTX(); CHECK_PTR(r); CHECK_PTR(z);
+  if ((const void*)r == (const void*)z) return set_err(ctx, IGA_E_INVALID, "r and z alias");
+  return kry_precond(ctx, (const double2*)r, (double2*)z);
 }
 
 iga_status iga_zt(iga_ctx* ctx, const iga_c128* x, iga_c128* c) {
@@ -305,15 +320,20 @@ iga_status iga_mgs(iga_ctx* ctx, const iga_c128* V, size_t ldv, int j, iga_c128*
 
 iga_status iga_solve(iga_ctx* ctx, const iga_c128* rhs, iga_c128* x, double tol, int maxit, int* iters,
                      double* res_hist, double* true_res) {
-  CHECK_CTX(); CHECK_DEFL(); CHECK_PTR(rhs); CHECK_PTR(x);
+  CHECK_CTX(); CHECK_SOLVE(); CHECK_PTR(rhs); CHECK_PTR(x);
   if (maxit < 1 || maxit > 1000 || !(tol >= 0.0)) return set_err(ctx, IGA_E_INVALID, "tol / maxit");
   if ((const void*)rhs == (const void*)x) return set_err(ctx, IGA_E_INVALID, "rhs and x alias");
   return kry_solve(ctx, (const double2*)rhs, (double2*)x, tol, maxit, iters, res_hist, true_res);
 }
 
+iga_status iga_set_wait_limit(iga_ctx* ctx, long long polls, int phantom_arrivals) {
+  CHECK_CTX();
+  return kry_set_wait_limit(ctx, polls, phantom_arrivals);
+}
+
 iga_status iga_solve_host(iga_ctx* ctx, const iga_c128* rhs_host, iga_c128* x_host, double tol, int maxit,
                           int* iters, double* res_hist, double* true_res) {
-  CHECK_CTX(); CHECK_DEFL();
+  CHECK_CTX(); CHECK_SOLVE();
   if (!rhs_host || !x_host) return set_err(ctx, IGA_E_INVALID, "NULL host pointer");
   if (ctx->maxit_alloc < 0 && maxit > 0) { /* workspace is allocated by the solve itself */ }
   size_t n = ctx->lv[0].n;

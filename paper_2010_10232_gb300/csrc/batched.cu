@@ -69,7 +69,7 @@ extern "C" iga_status iga_solve_batched(iga_ctx* const* ctxs, int nb, const iga_
   int total = 0;
   for (int b = 0; b < nb; ++b) {
     iga_ctx* c = ctxs[b];
-    if (!c || c->prm.skip_deflation || nrhs[b] < 1 || !rhs[b] || !x[b]) return IGA_E_INVALID;
+    if (!c || c->prm.skip_deflation || c->prm.deflation != 1 || nrhs[b] < 1 || !rhs[b] || !x[b]) return IGA_E_INVALID;
     if (((uintptr_t)rhs[b] & 15u) || ((uintptr_t)x[b] & 15u)) return IGA_E_INVALID;
     if (dev < 0) dev = c->device;
     if (c->device != dev) return IGA_E_INVALID;

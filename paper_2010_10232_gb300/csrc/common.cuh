@@ -71,6 +71,21 @@ __device__ __forceinline__ double kfield_k2(const KFieldDev& kf, double x, doubl
 }
 
 // ------------------------------------------------------------------ context
+// Fast diagonalisation of a tensor-product operator Op = M (x) K + K (x) M
+// + c M (x) M (2D; K + c M in 1D) from the generalised eigenpairs of the 1D
+// pencil (K, M): Op^{-1} = (V (x) V) diag(1 / (lam_i + lam_j + c)) (V (x) V)^T.
+struct FdmData {
+  int n = 0;                         // 1D size
+  double* V = nullptr;               // generalised eigenvectors [n][n], row-major V[i][k]
+  double* lam = nullptr;             // eigenvalues [n] (Rayleigh quotients)
+  float* Vf = nullptr;               // FP32 copies of V and of V^T
+  float* Vtf = nullptr;
+  float2* dinv = nullptr;            // 1 / (lam_i + lam_j + c), formed in FP64, rounded once
+  float2* w1 = nullptr;              // FP32 transform scratch (n^dim each)
+  float2* w2 = nullptr;
+  int refine = 2;                    // FP64 iterative refinement steps per solve
+};
+
 struct LevelData {
   int n_el = 0, nx = 0, ny = 1, n = 0;
   double* knots = nullptr;       // n_el + 2p + 1
@@ -128,21 +143,16 @@ struct iga_ctx {
   size_t m = 0;
   double* kc = nullptr;              // 1D coarse Z^T K Z  [mx][mx] dense
   double* mc = nullptr;              // 1D coarse Z^T M Z
-  double* fdmV = nullptr;            // generalised eigenvectors [mx][mx], row-major V[i][k]
-  double* fdmL = nullptr;            // eigenvalues [mx]
   double2* ct = nullptr;             // m-sized scratch
   double2* cs = nullptr;
   double2* cw = nullptr;
   double2* ce1 = nullptr;            // refinement residual / correction
   double2* ce2 = nullptr;
-  int e_refine = 2;                  // iterative refinement steps of the FDM coarse solve
-  float* fdmVf = nullptr;            // FP32 copy of the eigenvectors
-  float* fdmVtf = nullptr;           // and of their transpose
-  float* fdmDinv = nullptr;          // FP32 reciprocal denominators (formed in FP64)
+  FdmData fdmE;                      // fast diagonalisation of E (constant k)
+  FdmData fdmC;                      // of the fine-level CSLP matrix (exact CSLP, constant k)
+  double2* cxr = nullptr;            // exact-CSLP refinement residual (n)
   double* kcb = nullptr;             // banded 1D coarse matrices (half width (p+4)/2)
   double* mcb = nullptr;
-  float2* cwf = nullptr;             // FP32 transform scratch
-  float2* cwf2 = nullptr;
   float2* ctf = nullptr;             // FP32 copies of Z^T x and of the refinement residual
   float2* cef = nullptr;
   // variable-k E (block tridiagonal, banded in y): see deflation.cu
@@ -176,6 +186,8 @@ struct iga_ctx {
   int* kint = nullptr;               // [0] j, [1] barrier timeout
   unsigned* kbar = nullptr;          // grid barrier state
   int coop_blocks = 0;
+  unsigned long long wait_polls = 1ull << 24;   // bounded device waits: polls before giving up
+  int wait_phantom = 0;              // test hook: arrivals a grid barrier waits for beyond the grid
   bool vc_fused = false;             // V-cycle by the fused level kernels
   bool arnoldi_cgs = false;          // CGS2 Arnoldi (no grid barrier) instead of cooperative MGS
   int cgs_blocks = 0;
@@ -270,6 +282,11 @@ iga_status defl_z(iga_ctx* ctx, const double2* c, double2* x);
 iga_status defl_esolve(iga_ctx* ctx, const double2* t, double2* s, const float2* tf = nullptr);
 iga_status defl_apply(iga_ctx* ctx, const double2* x, double2* y);        // y = P x
 iga_status defl_q(iga_ctx* ctx, const double2* x, double2* y);            // y = Q x
+// y = P^T x = x - Q A x (tmp: n-sized scratch distinct from x, y)
+iga_status defl_apply_T(iga_ctx* ctx, const double2* x, double2* y, double2* tmp1, double2* tmp2);
+// exact CSLP (constant k): z = M_beta^{-1} r on the finest level
+iga_status setup_exact_cslp(iga_ctx* ctx);
+iga_status cslp_exact_solve(iga_ctx* ctx, const double2* r, double2* z);
 // ecoarse.cu (variable k)
 iga_status setup_block_E(iga_ctx* ctx);
 iga_status block_E_solve(iga_ctx* ctx, const double2* t, double2* s);
@@ -280,5 +297,7 @@ iga_status kry_mgs(iga_ctx* ctx, const double2* V, size_t ldv, int j, double2* w
 iga_status kry_solve(iga_ctx* ctx, const double2* f, double2* x, double tol, int maxit, int* iters,
                      double* hist, double* true_res);
 iga_status vec_norm(iga_ctx* ctx, const double2* x, size_t n, double* dev_out);
+iga_status kry_precond(iga_ctx* ctx, const double2* r, double2* z);   // M~^{-1} as configured
+iga_status kry_set_wait_limit(iga_ctx* ctx, long long polls, int phantom);
 void launch_convert_d2f(const double2* a, float2* b, size_t n, cudaStream_t st);
 void launch_convert_f2d(const float2* a, double2* b, size_t n, cudaStream_t st);

@@ -323,7 +323,7 @@ __device__ __forceinline__ void stage_panel(int total, D* dst, F src_at) {
 
 template <bool LEFT, bool DIVIDE, bool ACC, typename XT, typename OT, int LPT>
 __global__ void __launch_bounds__(128) k_fdm_gemm32(const float* R, const XT* X, OT* out, int rows, int cols,
-                                                   const float* dinv, int TK) {
+                                                   const float2* dinv, int TK) {
   constexpr int TY = FDM_TY, TX = FDM_TX;
   extern __shared__ __align__(16) unsigned char fsm[];
   // LEFT: Rs[TY][TK+1] and Xs[TK][TX+1]; RIGHT: Xs[TY][TK+1] and Rs[TK][TX+1]
@@ -384,7 +384,7 @@ __global__ void __launch_bounds__(128) k_fdm_gemm32(const float* R, const XT* X,
     __syncthreads();
   }
   if (i < rows && j < cols) {
-    if (DIVIDE) acc = dinv[(size_t)i * cols + j] * acc;
+    if (DIVIDE) acc = cmul(dinv[(size_t)i * cols + j], acc);
     if constexpr (ACC) {
       OT* o = out + (size_t)i * cols + j;
       *o = *o + tod(acc);
@@ -396,7 +396,7 @@ __global__ void __launch_bounds__(128) k_fdm_gemm32(const float* R, const XT* X,
 
 template <bool LEFT, bool DIVIDE, bool ACC, typename XT, typename OT>
 static void launch_fdm_gemm(iga_ctx* ctx, const float* R, const XT* X, OT* out, int rows, int cols,
-                            const float* dinv) {
+                            const float2* dinv) {
   // up to FDM_TK the whole K extent in one stage, 16 loads in flight per
   // thread; longer panels in 64-deep stages with 4 (measured faster there)
   const int K = LEFT ? rows : cols;
@@ -421,16 +421,18 @@ static iga_status fdm_gemm_attrs(iga_ctx* ctx) {
   return IGA_OK;
 }
 
-// dinv[i][j] = 1 / (lambda_i + lambda_j - k^2) (2D) or 1 / (lambda_j - k^2) (1D):
-// the sum is formed in FP64 (it nearly cancels for modes close to k^2), the
-// reciprocal is rounded once to FP32.
-__global__ void k_fdm_dinv(const double* lam, int n, int dim, double k2, float* dinv) {
+// dinv[i][j] = 1 / (lambda_i + lambda_j + c) (2D) or 1 / (lambda_j + c) (1D),
+// c = -k^2 for E, -(beta1 - i beta2) k^2 for the CSLP matrix: the sum is formed
+// in FP64 (for E it nearly cancels for modes close to k^2), the reciprocal is
+// rounded once to FP32 (imaginary part exactly 0 when c is real).
+__global__ void k_fdm_dinv(const double* lam, int n, int dim, double2 c, float2* dinv) {
   size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   size_t tot = dim == 2 ? (size_t)n * n : (size_t)n;
   if (idx >= tot) return;
   int i = (int)(idx / n), j = (int)(idx - (size_t)i * n);
-  double d = (dim == 2 ? lam[i] : 0.0) + lam[j] - k2;
-  dinv[idx] = (float)(1.0 / d);
+  double2 d = make_double2((dim == 2 ? lam[i] : 0.0) + lam[j] + c.x, c.y);
+  if (d.y == 0.0) dinv[idx] = make_float2((float)(1.0 / d.x), 0.0f);
+  else dinv[idx] = tof(cinv(d));
 }
 
 __global__ void k_transpose_f(const float* A, float* B, int n) {
@@ -452,10 +454,22 @@ __global__ void k_d2f_vec(const double* a, float* b, size_t n) {
 }
 
 // ------------------------------------------------------------------ host
-static iga_status fdm_setup(iga_ctx* ctx) {
-  const int n = ctx->mx;
+// dense [n][n] from a band [n][2bw+1] (Mat[i][i+d] at B[i][d+bw])
+__global__ void k_band_to_dense(const double* B, int n, int bw, double* A) {
+  size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (idx >= (size_t)n * n) return;
+  int i = (int)(idx / n), j = (int)(idx - (size_t)i * n), d = j - i;
+  A[idx] = (d >= -bw && d <= bw) ? B[(size_t)i * (2 * bw + 1) + d + bw] : 0.0;
+}
+
+// Generalised eigenpairs of the dense SPD pencil (Kd, Md) of size n (both with
+// half bandwidth bw): Cholesky Md = L L^T, parallel cyclic Jacobi on
+// L^{-1} Kd L^{-T}, V = L^{-T} W, eigenvalues recomputed as Rayleigh quotients;
+// then the FP32 copies of V, V^T and the denominators 1 / (lam_i + lam_j + c).
+static iga_status fdm_build(iga_ctx* ctx, FdmData& F, int n, const double* Kd, const double* Md, int bw, double2 c) {
   const int np = n + (n & 1);
   cudaStream_t st = ctx->st;
+  F.n = n;
   double* Lm = dalloc<double>(ctx, (size_t)n * n);
   double* Y = dalloc<double>(ctx, (size_t)n * n);
   double* Yt = dalloc<double>(ctx, (size_t)n * n);
@@ -467,16 +481,16 @@ static iga_status fdm_setup(iga_ctx* ctx) {
   double* cs = dalloc<double>(ctx, (size_t)4 * (np / 2 + 1));
   double* nrm = dalloc<double>(ctx, 2);
   int* info = dalloc<int>(ctx, 1);
-  ctx->fdmV = dalloc<double>(ctx, (size_t)n * n);
-  ctx->fdmL = dalloc<double>(ctx, n);
-  if (!Lm || !Y || !Yt || !Cm || !A0 || !A1 || !Vj || !W || !cs || !nrm || !info || !ctx->fdmV || !ctx->fdmL)
+  F.V = dalloc<double>(ctx, (size_t)n * n);
+  F.lam = dalloc<double>(ctx, n);
+  if (!Lm || !Y || !Yt || !Cm || !A0 || !A1 || !Vj || !W || !cs || !nrm || !info || !F.V || !F.lam)
     return set_err(ctx, IGA_E_OOM, "fdm alloc");
   CK(cudaMemsetAsync(info, 0, sizeof(int), st));
-  CK(cudaMemcpyAsync(Lm, ctx->mc, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(Lm, Md, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, st));
   k_cholesky<<<1, 512, 0, st>>>(Lm, n, info); iga_count_launch();
   CKL();
-  // C = L^{-1} Kc L^{-T} = L^{-1} (L^{-1} Kc)^T
-  k_trsm_lower<<<cdiv(n, 64), 64, 0, st>>>(Lm, ctx->kc, Y, n); iga_count_launch();
+  // C = L^{-1} Kd L^{-T} = L^{-1} (L^{-1} Kd)^T
+  k_trsm_lower<<<cdiv(n, 64), 64, 0, st>>>(Lm, Kd, Y, n); iga_count_launch();
   k_transpose<<<cdiv((size_t)n * n, 256), 256, 0, st>>>(Y, Yt, n); iga_count_launch();
   k_trsm_lower<<<cdiv(n, 64), 64, 0, st>>>(Lm, Yt, Cm, n); iga_count_launch();
   k_pad_sym<<<cdiv((size_t)np * np, 256), 256, 0, st>>>(Cm, A0, n, np); iga_count_launch();
@@ -502,32 +516,40 @@ static iga_status fdm_setup(iga_ctx* ctx) {
     else if (hn[0] <= 1e-26 * hn[1] || hn[0] == 0.0) extra = sweep;
   }
   if (!conv) return set_err(ctx, IGA_E_INVALID, "Jacobi eigen-solver did not converge (off %.3e)", hn[0]);
-  k_diag_extract<<<cdiv(n, 128), 128, 0, st>>>(cur, np, n, ctx->fdmL); iga_count_launch();
+  k_diag_extract<<<cdiv(n, 128), 128, 0, st>>>(cur, np, n, F.lam); iga_count_launch();
   k_crop<<<cdiv((size_t)n * n, 256), 256, 0, st>>>(Vj, np, n, W); iga_count_launch();
   // generalised eigenvectors V = L^{-T} W
-  k_trsm_lower_t<<<cdiv(n, 64), 64, 0, st>>>(Lm, W, ctx->fdmV, n); iga_count_launch();
-  k_rayleigh<<<cdiv(n, 64), 64, 0, st>>>(ctx->fdmV, ctx->kc, ctx->mc, n, (ctx->p + 4) / 2 + 1, ctx->fdmL); iga_count_launch();
-  ctx->fdmVf = dalloc<float>(ctx, (size_t)n * n);
-  ctx->fdmVtf = dalloc<float>(ctx, (size_t)n * n);
-  const int bw = (ctx->p + 4) / 2;
-  ctx->kcb = dalloc<double>(ctx, (size_t)n * (2 * bw + 1));
-  ctx->mcb = dalloc<double>(ctx, (size_t)n * (2 * bw + 1));
-  ctx->cwf = dalloc<float2>(ctx, ctx->m);
-  ctx->cwf2 = dalloc<float2>(ctx, ctx->m);
-  ctx->fdmDinv = dalloc<float>(ctx, ctx->m);
-  if (!ctx->fdmVf || !ctx->fdmVtf || !ctx->kcb || !ctx->mcb || !ctx->cwf || !ctx->cwf2 || !ctx->fdmDinv)
-    return set_err(ctx, IGA_E_OOM, "fdm32 alloc");
-  k_fdm_dinv<<<cdiv(ctx->m, 256), 256, 0, st>>>(ctx->fdmL, n, ctx->dim, ctx->k2const, ctx->fdmDinv); iga_count_launch();
+  k_trsm_lower_t<<<cdiv(n, 64), 64, 0, st>>>(Lm, W, F.V, n); iga_count_launch();
+  k_rayleigh<<<cdiv(n, 64), 64, 0, st>>>(F.V, Kd, Md, n, bw, F.lam); iga_count_launch();
+  const size_t mm = ctx->dim == 2 ? (size_t)n * n : (size_t)n;
+  F.Vf = dalloc<float>(ctx, (size_t)n * n);
+  F.Vtf = dalloc<float>(ctx, (size_t)n * n);
+  F.w1 = dalloc<float2>(ctx, mm);
+  F.w2 = dalloc<float2>(ctx, mm);
+  F.dinv = dalloc<float2>(ctx, mm);
+  if (!F.Vf || !F.Vtf || !F.w1 || !F.w2 || !F.dinv) return set_err(ctx, IGA_E_OOM, "fdm32 alloc");
+  k_fdm_dinv<<<cdiv(mm, 256), 256, 0, st>>>(F.lam, n, ctx->dim, c, F.dinv); iga_count_launch();
   TRY(fdm_gemm_attrs(ctx));
-  k_d2f_vec<<<cdiv((size_t)n * n, 256), 256, 0, st>>>(ctx->fdmV, ctx->fdmVf, (size_t)n * n); iga_count_launch();
-  k_transpose_f<<<cdiv((size_t)n * n, 256), 256, 0, st>>>(ctx->fdmVf, ctx->fdmVtf, n); iga_count_launch();
-  k_dense_to_band<<<cdiv((size_t)n * (2 * bw + 1), 128), 128, 0, st>>>(ctx->kc, n, bw, ctx->kcb); iga_count_launch();
-  k_dense_to_band<<<cdiv((size_t)n * (2 * bw + 1), 128), 128, 0, st>>>(ctx->mc, n, bw, ctx->mcb); iga_count_launch();
+  k_d2f_vec<<<cdiv((size_t)n * n, 256), 256, 0, st>>>(F.V, F.Vf, (size_t)n * n); iga_count_launch();
+  k_transpose_f<<<cdiv((size_t)n * n, 256), 256, 0, st>>>(F.Vf, F.Vtf, n); iga_count_launch();
   CKL();
   int hinfo = 0;
   CK(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  if (hinfo) return set_err(ctx, IGA_E_INVALID, "coarse mass matrix not positive definite");
+  if (hinfo) return set_err(ctx, IGA_E_INVALID, "mass matrix of the fast diagonalisation not positive definite");
+  return IGA_OK;
+}
+
+static iga_status fdm_setup(iga_ctx* ctx) {
+  const int n = ctx->mx;
+  const int bw = (ctx->p + 4) / 2;
+  TRY(fdm_build(ctx, ctx->fdmE, n, ctx->kc, ctx->mc, bw + 1, make_double2(-ctx->k2const, 0.0)));
+  ctx->kcb = dalloc<double>(ctx, (size_t)n * (2 * bw + 1));
+  ctx->mcb = dalloc<double>(ctx, (size_t)n * (2 * bw + 1));
+  if (!ctx->kcb || !ctx->mcb) return set_err(ctx, IGA_E_OOM, "E bands");
+  k_dense_to_band<<<cdiv((size_t)n * (2 * bw + 1), 128), 128, 0, ctx->st>>>(ctx->kc, n, bw, ctx->kcb); iga_count_launch();
+  k_dense_to_band<<<cdiv((size_t)n * (2 * bw + 1), 128), 128, 0, ctx->st>>>(ctx->mc, n, bw, ctx->mcb); iga_count_launch();
+  CKL();
   return IGA_OK;
 }
 
@@ -570,48 +592,48 @@ iga_status defl_z(iga_ctx* ctx, const double2* c, double2* x) {
   return IGA_OK;
 }
 
-// s ~ E^{-1} t by fast diagonalisation with FP32 transforms (constant k); the
-// FP32 intermediates live in cwf, cwf2.
-// tf (optional): the same right-hand side already rounded to FP32 (saves every
-// block of the first transform converting its FP64 panel)
-static iga_status fdm_solve32(iga_ctx* ctx, const double2* t, double2* s, bool accumulate = false,
+// s ~ Op^{-1} t by fast diagonalisation with FP32 transforms (the FP32
+// intermediates live in F.w1, F.w2).  tf (optional): the same right-hand side
+// already rounded to FP32 (saves every block of the first transform
+// converting its FP64 panel).  accumulate: s += result.
+static iga_status fdm_solve32(iga_ctx* ctx, const FdmData& F, const double2* t, double2* s, bool accumulate = false,
                               const float2* tf = nullptr) {
-  const int mx = ctx->mx;
-  const float* V = ctx->fdmVf;
-  const float* Vt = ctx->fdmVtf;
+  const int mx = F.n;
+  const float* V = F.Vf;
+  const float* Vt = F.Vtf;
   if (ctx->dim == 1) {
     // s^T = ((t^T V) / d) V^T with t as a 1 x m row
-    launch_fdm_gemm<false, true, false>(ctx, V, t, ctx->cwf, 1, mx, ctx->fdmDinv);
-    if (accumulate) launch_fdm_gemm<false, false, true>(ctx, Vt, ctx->cwf, s, 1, mx, nullptr);
-    else launch_fdm_gemm<false, false, false>(ctx, Vt, ctx->cwf, s, 1, mx, nullptr);
+    launch_fdm_gemm<false, true, false>(ctx, V, t, F.w1, 1, mx, F.dinv);
+    if (accumulate) launch_fdm_gemm<false, false, true>(ctx, Vt, F.w1, s, 1, mx, nullptr);
+    else launch_fdm_gemm<false, false, false>(ctx, Vt, F.w1, s, 1, mx, nullptr);
   } else {
     // T1 = V^T T; T2 = T1 V / D; T3 = V T2; S = T3 V^T (or s += S)
-    if (tf) launch_fdm_gemm<true, false, false>(ctx, Vt, tf, ctx->cwf, mx, mx, nullptr);
-    else launch_fdm_gemm<true, false, false>(ctx, Vt, t, ctx->cwf, mx, mx, nullptr);
-    launch_fdm_gemm<false, true, false>(ctx, V, ctx->cwf, ctx->cwf2, mx, mx, ctx->fdmDinv);
-    launch_fdm_gemm<true, false, false>(ctx, V, ctx->cwf2, ctx->cwf, mx, mx, nullptr);
-    if (accumulate) launch_fdm_gemm<false, false, true>(ctx, Vt, ctx->cwf, s, mx, mx, nullptr);
-    else launch_fdm_gemm<false, false, false>(ctx, Vt, ctx->cwf, s, mx, mx, nullptr);
+    if (tf) launch_fdm_gemm<true, false, false>(ctx, Vt, tf, F.w1, mx, mx, nullptr);
+    else launch_fdm_gemm<true, false, false>(ctx, Vt, t, F.w1, mx, mx, nullptr);
+    launch_fdm_gemm<false, true, false>(ctx, V, F.w1, F.w2, mx, mx, F.dinv);
+    launch_fdm_gemm<true, false, false>(ctx, V, F.w2, F.w1, mx, mx, nullptr);
+    if (accumulate) launch_fdm_gemm<false, false, true>(ctx, Vt, F.w1, s, mx, mx, nullptr);
+    else launch_fdm_gemm<false, false, false>(ctx, Vt, F.w1, s, mx, mx, nullptr);
   }
   CKL();
   return IGA_OK;
 }
 
 // s = E^{-1} t.  Constant k: fast diagonalisation with FP32 transforms and
-// FP64 eigenvalue denominators, followed by e_refine steps of iterative
+// FP64 eigenvalue denominators, followed by fdmE.refine steps of iterative
 // refinement s += FDM(t - E s) with the residual in FP64 (E applied by the
 // banded tensor-product kernel on the coarse grid).  Two steps bring the
 // solve to ~1e-11 of a sparse LU even where lambda_i + lambda_j ~ k^2 nearly
 // cancels.  Variable k: block LU.
 iga_status defl_esolve(iga_ctx* ctx, const double2* t, double2* s, const float2* tf) {
   if (ctx->vark) return block_E_solve(ctx, t, s);
-  TRY(fdm_solve32(ctx, t, s, false, tf));
+  TRY(fdm_solve32(ctx, ctx->fdmE, t, s, false, tf));
   const int bw = (ctx->p + 4) / 2;
   const int my = ctx->dim == 2 ? ctx->mx : 1;
-  for (int it = 0; it < ctx->e_refine; ++it) {
+  for (int it = 0; it < ctx->fdmE.refine; ++it) {
     TRY(op_apply_bands(ctx, bw, ctx->mx, my, ctx->kcb, ctx->mcb, make_double2(-ctx->k2const, 0.0), s, ctx->ce1, t,
                        EPI_ZMINUS, ctx->dim == 2 ? ctx->cef : nullptr));
-    TRY(fdm_solve32(ctx, ctx->ce1, s, true, ctx->dim == 2 ? ctx->cef : nullptr));   // s += FDM(r)
+    TRY(fdm_solve32(ctx, ctx->fdmE, ctx->ce1, s, true, ctx->dim == 2 ? ctx->cef : nullptr));   // s += FDM(r)
   }
   CKL();
   return IGA_OK;
@@ -629,4 +651,57 @@ iga_status defl_q(iga_ctx* ctx, const double2* x, double2* y) {
 iga_status defl_apply(iga_ctx* ctx, const double2* x, double2* y) {
   TRY(defl_q(ctx, x, ctx->w3));
   return op_apply<double>(ctx, 0, OP_A, ctx->w3, y, x, EPI_ZMINUS, nullptr, 0.0);
+}
+
+__global__ void k_sub(const double2* a, const double2* b, double2* out, size_t n) {
+  size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (e < n) out[e] = a[e] - b[e];
+}
+
+// y = P^T x = x - Q A x (A and Q complex symmetric, so P^T = I - Q A)
+iga_status defl_apply_T(iga_ctx* ctx, const double2* x, double2* y, double2* tmp1, double2* tmp2) {
+  const size_t n = ctx->lv[0].n;
+  TRY(op_apply<double>(ctx, 0, OP_A, x, tmp1, nullptr, EPI_Y, nullptr, 0.0));
+  TRY(defl_q(ctx, tmp1, tmp2));
+  k_sub<<<cdiv(n, 256), 256, 0, ctx->st>>>(x, tmp2, y, n); iga_count_launch();
+  CKL();
+  return IGA_OK;
+}
+
+// ------------------------------------------------------------------ exact CSLP (C_ex)
+// The finest-level CSLP matrix M_beta = K (x) M + M (x) K - sigma k^2 M (x) M
+// (constant k) is a tensor-product operator like E, so it is inverted by the
+// same fast diagonalisation: the 1D pencil of the fine band matrices, complex
+// denominators 1 / (lam_i + lam_j - sigma k^2), FP32 transforms and FP64
+// iterative refinement whose residual r = t - M_beta s is the FP64 operator
+// kernel of the finest level.
+constexpr int EXACT_CSLP_MAX_N = 2048;
+
+iga_status setup_exact_cslp(iga_ctx* ctx) {
+  if (ctx->vark) return set_err(ctx, IGA_E_UNSUPPORTED, "exact CSLP: constant k only");
+  const LevelData& L = ctx->lv[0];
+  const int n = L.nx, p = ctx->p;
+  if (n > EXACT_CSLP_MAX_N)
+    return set_err(ctx, IGA_E_UNSUPPORTED, "exact CSLP: n_x = %d above %d (dense 1D eigenvectors)", n, EXACT_CSLP_MAX_N);
+  double* Kd = dalloc<double>(ctx, (size_t)n * n);
+  double* Md = dalloc<double>(ctx, (size_t)n * n);
+  ctx->cxr = dalloc<double2>(ctx, L.n);
+  if (!Kd || !Md || !ctx->cxr) return set_err(ctx, IGA_E_OOM, "exact CSLP alloc");
+  k_band_to_dense<<<cdiv((size_t)n * n, 256), 256, 0, ctx->st>>>(L.K, n, p, Kd); iga_count_launch();
+  k_band_to_dense<<<cdiv((size_t)n * n, 256), 256, 0, ctx->st>>>(L.M, n, p, Md); iga_count_launch();
+  CKL();
+  const double2 c = make_double2(-ctx->sig.x * ctx->k2const, -ctx->sig.y * ctx->k2const);   // -sigma k^2
+  TRY(fdm_build(ctx, ctx->fdmC, n, Kd, Md, p, c));
+  ctx->fdmC.refine = 2;
+  return IGA_OK;
+}
+
+// z = M_beta^{-1} r (finest level) to FP64 accuracy
+iga_status cslp_exact_solve(iga_ctx* ctx, const double2* r, double2* z) {
+  TRY(fdm_solve32(ctx, ctx->fdmC, r, z, false, nullptr));
+  for (int it = 0; it < ctx->fdmC.refine; ++it) {
+    TRY(op_apply<double>(ctx, 0, OP_MB, z, ctx->cxr, r, EPI_ZMINUS, nullptr, 0.0));
+    TRY(fdm_solve32(ctx, ctx->fdmC, ctx->cxr, z, true, nullptr));
+  }
+  return IGA_OK;
 }

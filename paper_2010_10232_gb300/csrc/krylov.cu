@@ -261,10 +261,12 @@ __global__ void k_add(const double2* a, const double2* b, double2* out, size_t n
 }
 
 // ------------------------------------------------------------------ device-resident iteration
-// Bounded grid barrier for a cooperative launch (all blocks co-resident).  A
-// barrier that waits longer than ~1 s sets *err and every block returns; the
-// host reports IGA_E_TIMEOUT.
-__device__ __forceinline__ bool grid_sync(unsigned* bar, unsigned nb, int* err) {
+// Bounded grid barrier for a cooperative launch (all blocks co-resident).  The
+// barrier opens when `expect` blocks have arrived (the grid size; a test sets
+// one more, which never arrives).  A block that has polled `limit` times
+// (default 2^24, ~1 s) sets *err and returns false; every other waiting block
+// sees *err and returns false too, and the host reports IGA_E_TIMEOUT.
+__device__ __forceinline__ bool grid_sync(unsigned* bar, unsigned expect, int* err, unsigned long long limit) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -274,14 +276,14 @@ __device__ __forceinline__ bool grid_sync(unsigned* bar, unsigned nb, int* err) 
     __threadfence();
     unsigned arrived = atomicAdd(bar, 1u);
     ok = 1;
-    if (arrived == nb - 1) {
+    if (arrived == expect - 1) {
       atomicExch(bar, 0u);
       __threadfence();
       atomicAdd(bar + 1, 1u);
     } else {
       unsigned long long spins = 0;
       while (*vgen == g) {
-        if (*verr || ++spins > (1ull << 24)) { atomicExch(err, 1); ok = 0; break; }
+        if (*verr || ++spins > limit) { atomicExch(err, 1); ok = 0; break; }
         __nanosleep(64);
       }
     }
@@ -303,6 +305,8 @@ struct ArnoldiArgs {
   double* part;        // 2 x gridDim.x (re, im) partial sums
   unsigned* bar;       // grid barrier {count, generation}
   int* err;            // barrier timeout flag
+  unsigned long long spin_limit;   // polls before a barrier wait gives up
+  unsigned phantom;    // extra arrivals the barrier waits for (0; a test sets 1)
   cudaGraphConditionalHandle cond;
   int use_cond;
 };
@@ -311,9 +315,15 @@ struct ArnoldiArgs {
 // modified Gram-Schmidt (i = 0..j: h_ij = v_i^H w, w -= h_ij v_i, one grid
 // barrier per coefficient), h_{j+1,j} = ||w||, v_{j+1} = w / h_{j+1,j}, the
 // Givens update of column j, j <- j + 1 and the loop condition.
+// A barrier that gave up (now or in an earlier iteration) ends the step in
+// every block; block 0 then clears the loop condition, so the WHILE node stops.
 __global__ void __launch_bounds__(256) k_arnoldi_coop(ArnoldiArgs a) {
   const int j = *a.jptr;
   const unsigned nb = gridDim.x;
+  if (*(volatile int*)a.err) {
+    if (a.use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(a.cond, 0u);
+    return;
+  }
   double2* hcol = a.H + (size_t)j * a.ldh;
   double2 hp = make_double2(0.0, 0.0);
   for (int i = 0; i <= j + 1; ++i) {
@@ -337,7 +347,10 @@ __global__ void __launch_bounds__(256) k_arnoldi_coop(ArnoldiArgs a) {
     double2 s = block_sum2(sa, sb);
     double* pb = a.part + (size_t)(i & 1) * 2 * nb;
     if (threadIdx.x == 0) { pb[2 * blockIdx.x] = s.x; pb[2 * blockIdx.x + 1] = s.y; }
-    if (!grid_sync(a.bar, nb, a.err)) return;
+    if (!grid_sync(a.bar, nb + a.phantom, a.err, a.spin_limit)) {
+      if (a.use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(a.cond, 0u);
+      return;
+    }
     hp = reduce_partials(pb, nb);
     if (i <= j && blockIdx.x == 0 && threadIdx.x == 0) hcol[i] = hp;
   }
@@ -646,10 +659,16 @@ static iga_status ensure_krylov(iga_ctx* ctx, int maxit, bool flexible) {
   return IGA_OK;
 }
 
-// z = M~^{-1} r in the context's precision
+// z = M~^{-1} r: the exact CSLP inverse (C_ex), z = r without a CSLP
+// (n_vcycles = 0: deflation alone), else the V-cycles in the context's precision
 static iga_status precond(iga_ctx* ctx, const double2* r, double2* z) {
-  if (ctx->prm.precision == 0) return mg_vcycle<double>(ctx, r, z);
   LevelData& L = ctx->lv[0];
+  if (ctx->prm.precond == 1) return cslp_exact_solve(ctx, r, z);
+  if (ctx->prm.n_vcycles < 1) {
+    CK(cudaMemcpyAsync(z, r, sizeof(double2) * L.n, cudaMemcpyDeviceToDevice, ctx->st));
+    return IGA_OK;
+  }
+  if (ctx->prm.precision == 0) return mg_vcycle<double>(ctx, r, z);
   launch_convert_d2f(r, ctx->fin, L.n, ctx->st);
   TRY(mg_vcycle<float>(ctx, ctx->fin, ctx->fout));
   if (ctx->net) TRY(net_correct(ctx, ctx->fin, ctx->fout));
@@ -684,6 +703,8 @@ static ArnoldiArgs arnoldi_args(iga_ctx* ctx, int maxit) {
   a.part = ctx->partials;
   a.bar = ctx->kbar;
   a.err = ctx->kint + 1;
+  a.spin_limit = ctx->wait_polls;
+  a.phantom = (unsigned)ctx->wait_phantom;
   a.cond = ctx->gcond;
   a.use_cond = 0;
   return a;
@@ -722,22 +743,38 @@ static iga_status launch_arnoldi(iga_ctx* ctx, ArnoldiArgs a) {
   return IGA_OK;
 }
 
-// One iteration's work after v_j is in vcur: w = M~^{-1} P A v_j (left) or
-// z_j = M~^{-1} v_j, w = P A z_j (flexible), then the Arnoldi step.
+iga_status kry_precond(iga_ctx* ctx, const double2* r, double2* z) { return precond(ctx, r, z); }
+
+// One iteration's work after v_j is in vcur, then the Arnoldi step:
+//   deflation 1 (DEF1): w = M~^{-1} P A v_j (left) or z_j = M~^{-1} v_j, w = P A z_j (flexible);
+//   deflation 0 (none): w = M~^{-1} A v_j (left) or w = A M~^{-1} v_j (flexible);
+//   deflation 2 (literal, left only): w = P^T M~^{-1} A v_j.
 static iga_status iteration_body(iga_ctx* ctx, bool flex, ArnoldiArgs a) {
   const size_t n = ctx->lv[0].n;
+  const int defl = ctx->prm.deflation;
   double2* vcur = ctx->kvec;
   double2* zcur = ctx->kvec + n;
   double2* wnext = ctx->kvec + 2 * n;
   if (flex) {
     TRY(precond(ctx, vcur, zcur));
     k_store_col<<<cdiv(n, 256), 256, 0, ctx->st>>>(ctx->Zb, n, n, ctx->kint, zcur); iga_count_launch();
-    TRY(op_apply<double>(ctx, 0, OP_A, zcur, ctx->w1, nullptr, EPI_Y, nullptr, 0.0));
-    TRY(defl_apply(ctx, ctx->w1, wnext));
+    if (defl == 1) {
+      TRY(op_apply<double>(ctx, 0, OP_A, zcur, ctx->w1, nullptr, EPI_Y, nullptr, 0.0));
+      TRY(defl_apply(ctx, ctx->w1, wnext));
+    } else {
+      TRY(op_apply<double>(ctx, 0, OP_A, zcur, wnext, nullptr, EPI_Y, nullptr, 0.0));
+    }
   } else {
     TRY(op_apply<double>(ctx, 0, OP_A, vcur, ctx->w1, nullptr, EPI_Y, nullptr, 0.0));
-    TRY(defl_apply(ctx, ctx->w1, ctx->w2));
-    TRY(precond(ctx, ctx->w2, wnext));
+    if (defl == 1) {
+      TRY(defl_apply(ctx, ctx->w1, ctx->w2));
+      TRY(precond(ctx, ctx->w2, wnext));
+    } else if (defl == 0) {
+      TRY(precond(ctx, ctx->w1, wnext));
+    } else {
+      TRY(precond(ctx, ctx->w1, ctx->w2));
+      TRY(defl_apply_T(ctx, ctx->w2, wnext, ctx->w1, ctx->w3));
+    }
   }
   return launch_arnoldi(ctx, a);
 }
@@ -778,11 +815,18 @@ iga_status solve_init(iga_ctx* ctx, const double2* f, double tol, bool flex, cud
   k_solve_reset<<<cdiv(nh, 256), 256, 0, st>>>(ctx->H, nh, ctx->kint, ctx->kbar, gs.scal, tol); iga_count_launch();
   if (ctx->cgs_ticket) CK(cudaMemsetAsync(ctx->cgs_ticket, 0, sizeof(unsigned), st));
   double2* V = ctx->Vb;
+  const int defl = ctx->prm.deflation;
   if (flex) {
-    TRY(defl_apply(ctx, f, V));
-  } else {
+    if (defl == 1) TRY(defl_apply(ctx, f, V));
+    else CK(cudaMemcpyAsync(V, f, sizeof(double2) * n, cudaMemcpyDeviceToDevice, st));
+  } else if (defl == 1) {
     TRY(defl_apply(ctx, f, ctx->w0));
     TRY(precond(ctx, ctx->w0, V));
+  } else if (defl == 0) {
+    TRY(precond(ctx, f, V));
+  } else {
+    TRY(precond(ctx, f, ctx->w0));
+    TRY(defl_apply_T(ctx, ctx->w0, V, ctx->w1, ctx->w2));
   }
   k_norm2_part<<<nb, IGA_RED_THREADS, 0, st>>>(V, n, ctx->partials); iga_count_launch();
   k_init_v0<<<nb, IGA_RED_THREADS, 0, st>>>(V, n, ctx->partials, gs, ctx->kvec, cond, use_cond); iga_count_launch();
@@ -790,18 +834,23 @@ iga_status solve_init(iga_ctx* ctx, const double2* f, double tol, bool flex, cud
   return IGA_OK;
 }
 
-// Phase 3 (kernels only): x^ = V y (Z y), u = x^ + Q (f - A x^), optional
-// true-residual norms into scal[2], scal[3].
+// Phase 3 (kernels only): x^ = V y (Z y), u = x^ + Q (f - A x^) (DEF1) or
+// u = x^ (no deflation, literal ordering), optional true-residual norms into
+// scal[2], scal[3].
 iga_status solve_finish(iga_ctx* ctx, const double2* f, double2* x, bool flex, bool true_res) {
   cudaStream_t st = ctx->st;
   const size_t n = ctx->lv[0].n;
   const int ldh = ctx->maxit_alloc + 1;
   GState gs = gstate_of(ctx);
   k_backsolve_dev<<<1, 1, 0, st>>>(ctx->H, ldh, gs.g, ctx->gy, ctx->kint); iga_count_launch();
-  k_combine_dev<<<cdiv(n, 256), 256, 0, st>>>(flex ? ctx->Zb : ctx->Vb, n, n, ctx->gy, ctx->kint, ctx->w0); iga_count_launch();
-  TRY(op_apply<double>(ctx, 0, OP_A, ctx->w0, ctx->w1, f, EPI_ZMINUS, nullptr, 0.0));
-  TRY(defl_q(ctx, ctx->w1, ctx->w2));
-  k_add<<<cdiv(n, 256), 256, 0, st>>>(ctx->w0, ctx->w2, x, n); iga_count_launch();
+  if (ctx->prm.deflation == 1) {
+    k_combine_dev<<<cdiv(n, 256), 256, 0, st>>>(flex ? ctx->Zb : ctx->Vb, n, n, ctx->gy, ctx->kint, ctx->w0); iga_count_launch();
+    TRY(op_apply<double>(ctx, 0, OP_A, ctx->w0, ctx->w1, f, EPI_ZMINUS, nullptr, 0.0));
+    TRY(defl_q(ctx, ctx->w1, ctx->w2));
+    k_add<<<cdiv(n, 256), 256, 0, st>>>(ctx->w0, ctx->w2, x, n); iga_count_launch();
+  } else {
+    k_combine_dev<<<cdiv(n, 256), 256, 0, st>>>(flex ? ctx->Zb : ctx->Vb, n, n, ctx->gy, ctx->kint, x); iga_count_launch();
+  }
   CKL();
   if (true_res) {
     TRY(op_apply<double>(ctx, 0, OP_A, x, ctx->w1, f, EPI_ZMINUS, nullptr, 0.0));
@@ -836,6 +885,15 @@ iga_status capture_body(iga_ctx* ctx, cudaGraph_t body, bool flex, int maxit, cu
 }
 
 iga_status kry_prepare(iga_ctx* ctx, int maxit, bool flex) { return ensure_krylov(ctx, maxit, flex); }
+
+iga_status kry_set_wait_limit(iga_ctx* ctx, long long polls, int phantom) {
+  if (polls < 0 || phantom < 0 || phantom > 1) return set_err(ctx, IGA_E_INVALID, "wait limit");
+  CK(cudaStreamSynchronize(ctx->st));
+  ctx->wait_polls = polls == 0 ? (1ull << 24) : (unsigned long long)polls;
+  ctx->wait_phantom = phantom;
+  drop_graph(ctx);                       // the captured Arnoldi step holds the old limit
+  return IGA_OK;
+}
 
 iga_status kry_solve(iga_ctx* ctx, const double2* f, double2* x, double tol, int maxit, int* iters, double* hist,
                      double* true_res) {

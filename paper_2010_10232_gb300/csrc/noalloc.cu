@@ -24,7 +24,8 @@ __global__ void k_finish_h(const double* part, int nb, double2* h);
 
 // Device address of g_mgs_scratch, looked up once per device.  In host code the
 // array's name only stands in for the device symbol, so the kernels are given
-// this address instead.
+// this address instead.  The cache lives for the process: after a
+// cudaDeviceReset the address would be stale (the header says so).
 static double* g_scratch_addr[IGA_NOALLOC_MAX_DEVICES];
 static int g_sms[IGA_NOALLOC_MAX_DEVICES];
 static std::mutex g_scratch_mu;
@@ -66,11 +67,7 @@ extern "C" iga_status iga_mgs_noalloc(const iga_c128* V, size_t ldv, size_t n, i
   if (s != IGA_OK) return s;
   // same grid rule as the context path: two blocks per SM
   size_t nb = (size_t)2 * sms;
-  if (nb > IGA_NOALLOC_MAX_BLOCKS) {
-    fprintf(stderr, "iga_mgs_noalloc: %zu reduction blocks exceed the static scratch (%d blocks)\n", nb,
-            IGA_NOALLOC_MAX_BLOCKS);
-    return IGA_E_INVALID;
-  }
+  if (nb > IGA_NOALLOC_MAX_BLOCKS) return IGA_E_INVALID;   // more SMs than the static scratch serves
   cudaStream_t st = (cudaStream_t)stream;
   double* pa = scratch;
   double* pb = scratch + 2 * nb;

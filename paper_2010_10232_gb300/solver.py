@@ -38,7 +38,7 @@ class Helmholtz:
 
     def __init__(self, dim=2, p=3, n_el=32, kfield=10.0, beta=(1.0, 0.5), eps=0.0, nu_pre=1, nu_post=1,
                  omega=0.6, n_vcycles=1, precision=0, flexible=0, skip_deflation=0, host_loop=0, arnoldi=None,
-                 fused_vcycle=0, stream=None):
+                 fused_vcycle=0, stream=None, precond=0, deflation=1):
         self._L = _ffi.lib()
         prm = _ffi.IgaParams()
         self._L.iga_default_params(C.byref(prm))
@@ -68,6 +68,8 @@ class Helmholtz:
         if arnoldi is not None:
             prm.arnoldi = int(arnoldi)
         prm.fused_vcycle = int(fused_vcycle)
+        prm.precond = int(precond)
+        prm.deflation = int(deflation)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -174,6 +176,15 @@ class Helmholtz:
         self._check(self._L.iga_vcycle_cslp(self._h, _ptr(r), _ptr(z)))
         return z
 
+    def precond(self, r, z=None):
+        """z = M~^{-1} r as the solve applies it (V-cycles, exact CSLP or identity)."""
+        z = self.vec() if z is None else z
+        self._check(self._L.iga_precond(self._h, _ptr(r), _ptr(z)))
+        return z
+
+    def set_wait_limit(self, polls=0, phantom_arrivals=0):
+        self._check(self._L.iga_set_wait_limit(self._h, int(polls), int(phantom_arrivals)))
+
     def zt(self, x):
         c = self.vec(self.m)
         self._check(self._L.iga_zt(self._h, _ptr(x), _ptr(c)))
@@ -262,7 +273,11 @@ def from_problem(pr, **kw) -> Helmholtz:
     """Build a context from a workloads.Problem-like description."""
     kf = pr.kfield
     kfield = float(kf.values[0]) if len(kf.lines) == 0 else kf
+    if not getattr(pr, "shift_uses_mass", True):
+        raise ValueError("the identity-shift CSLP is not built on the GPU (see the CSLP reading of Section 3)")
     args = dict(dim=pr.dim, p=pr.p, n_el=pr.n_el, kfield=kfield, beta=pr.shift, eps=pr.eps, nu_pre=pr.nu_pre,
-                nu_post=pr.nu_post, omega=pr.omega, n_vcycles=pr.n_vcycles)
+                nu_post=pr.nu_post, omega=pr.omega, n_vcycles=pr.n_vcycles,
+                precond={"mg": 0, "exact": 1}[getattr(pr, "precond", "mg")],
+                deflation=1 if getattr(pr, "deflation", True) else 0)
     args.update(kw)
     return Helmholtz(**args)

@@ -48,6 +48,7 @@ def test_status_strings_and_defaults(lib_path):
     prm = _ffi.IgaParams()
     L.iga_default_params(ctypes.byref(prm))
     assert prm.dim == 2 and prm.p == 3 and abs(prm.omega - 0.6) < 1e-15 and prm.nu_pre == 1
+    assert prm.precond == 0 and prm.deflation == 1
 
 
 def test_setup_rejects_bad_parameters_without_gpu_work(lib_path):
@@ -57,11 +58,18 @@ def test_setup_rejects_bad_parameters_without_gpu_work(lib_path):
     prm = _ffi.IgaParams()
     L.iga_default_params(ctypes.byref(prm))
     h = ctypes.c_void_p()
-    for field, bad in (("p", 0), ("p", 6), ("dim", 3), ("n_el", 1), ("n_vcycles", 0), ("precision", 7)):
+    for bad in ({"p": 0}, {"p": 6}, {"dim": 3}, {"n_el": 1}, {"n_vcycles": -1}, {"precision": 7},
+                {"precond": 2}, {"deflation": 3}, {"n_vcycles": 0, "deflation": 0},
+                {"deflation": 2, "precision": 1}, {"deflation": 2, "flexible": 1}):
         q = _ffi.IgaParams()
         ctypes.memmove(ctypes.byref(q), ctypes.byref(prm), ctypes.sizeof(prm))
-        setattr(q, field, bad)
-        assert L.iga_setup(ctypes.byref(q), ctypes.byref(h)) == -1
+        for field, v in bad.items():
+            setattr(q, field, v)
+        assert L.iga_setup(ctypes.byref(q), ctypes.byref(h)) == -1, bad
+    q = _ffi.IgaParams()
+    ctypes.memmove(ctypes.byref(q), ctypes.byref(prm), ctypes.sizeof(prm))
+    q.precond, q.n_lines = 1, 1                 # exact CSLP needs constant k
+    assert L.iga_setup(ctypes.byref(q), ctypes.byref(h)) == -7
     q = _ffi.IgaParams()
     ctypes.memmove(ctypes.byref(q), ctypes.byref(prm), ctypes.sizeof(prm))
     q.omega = 0.0

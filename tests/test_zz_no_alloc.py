@@ -36,10 +36,16 @@ def test_mgs_noalloc_matches_context_path_twice():
         h_ref = h.mgs(V, j, w_ref)                                          # context path
         w_na = w0.clone()
         h_na = torch.zeros(j + 2, dtype=torch.complex128, device="cuda")
+        torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
+        reserved_before = torch.cuda.memory_reserved()
         rc = L.iga_mgs_noalloc(C.c_void_p(V.data_ptr()), n, n, j, C.c_void_p(w_na.data_ptr()),
                                C.c_void_p(h_na.data_ptr()), stream)
         assert rc == 0, f"call {call}: status {rc}"
         torch.cuda.synchronize()
+        if call > 0:        # after the first call (module load, address lookup) nothing is allocated
+            assert torch.cuda.mem_get_info()[0] == free_before
+            assert torch.cuda.memory_reserved() == reserved_before
         np.testing.assert_allclose(h_na.cpu().numpy(), h_ref.cpu().numpy(), rtol=1e-12, atol=1e-12)
         np.testing.assert_allclose(w_na.cpu().numpy(), w_ref.cpu().numpy(), rtol=1e-12, atol=1e-12)
 

@@ -1,6 +1,7 @@
 #!/usr/bin/env python
 """Benchmark: 2D deflated, CSLP-multigrid-preconditioned GMRES solve to 1e-7
-on the GB300 (one solve = one step), plus operator / V-cycle bandwidth.
+on the GB300 (one solve = one step), plus operator / V-cycle bandwidth and the
+other forms and configurations of the method.
 
 Workload (one step): MP 2-A, unit square, constant k = 200, p = 3, 320 x 320
 elements (n = 103 041 complex128 dofs), unit point source at the centre,
@@ -8,7 +9,15 @@ CSLP shift (1, 0.5), one V-cycle (nu = 1/1), ADP deflation, FP64 throughout,
 tol 1e-7, maxit 100.  Inputs are resident on the device before the timed
 region; L2 is flushed (a 512 MiB buffer is written) before every timed solve.
 
+Secondary rows (not the headline): the FP32 V-cycle and its operator sweep at
+4097^2 dofs against the measured HBM peak; the mixed-precision and learned
+forms at 1e-7 and at a tolerance where every form's error against the
+oracle's direct solution is <= 1e-6; the exact CSLP C_ex and the deflation
+alone D; the k x p sweep of MP 2-A; the 1D problem; the three-layer field at
+640^2; 1280^2 with k = 800; the 64-instance batch.
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                       [--no-cpu] [--no-forms] [--no-configs]
 Prints one JSON line (rank 0).
 """
 from __future__ import annotations
@@ -31,6 +40,11 @@ APPLY_DRAM_BYTES = 1695232
 K_WAVE, P_DEG, N_EL = 200.0, 3, 320
 METRIC = "2D solve time to 1e-7 rel. residual + iterations; apply/V-cycle HBM GB/s vs peak"
 WORKLOAD = f"MP2-A constant k={int(K_WAVE)}, p={P_DEG}, {N_EL}x{N_EL} elements, centre point source"
+# algorithmic bytes of one FP32 V-cycle per fine dof (2D, nu = 1/1, complex64
+# storage: read x, b and write x per sweep, residual, transfers; x 4/3 for the
+# coarser levels)
+VCYCLE_ALG_BYTES_PER_DOF = 131
+TOL_MATCHED = 1e-9
 
 
 def _peaks():
@@ -132,14 +146,34 @@ for _ in range({reps}):
 print(json.dumps({{"setup_s": t1 - t0, "solve_s": times, "iters": iters, "true_res": r.true_res}}))
 """
 
+# true residual of GPU solutions with the oracle's assembled matrix (the
+# three-layer field at 640^2, too large for the oracle's direct solve in bench
+# time); reads the solutions from a .npy file written by the GPU arm
+ORACLE_RESIDUAL_SNIPPET = r"""
+import json, sys
+import numpy as np
+sys.path.insert(0, {root!r})
+import workloads as W
+from oracle import assembly as asm
+pr = W.config3()
+d = asm.Discretization(2, pr.p, pr.n_el, pr.kfield)
+f = asm.point_source(2, pr.p, pr.n_el, pr.sources[0])
+us = np.load({path!r})
+print(json.dumps([float(np.linalg.norm(f - d.A @ u) / np.linalg.norm(f)) for u in us]))
+"""
+
+
+def _oracle_env(threads: int) -> dict:
+    t = str(int(threads))
+    return dict(os.environ, OMP_NUM_THREADS=t, OPENBLAS_NUM_THREADS=t, MKL_NUM_THREADS=t, CUDA_VISIBLE_DEVICES="")
+
 
 def run_oracle(reps: int, threads: int = 1) -> dict:
     """FP64 oracle on the host cores: `threads` BLAS/OpenMP threads (1 =
     single-threaded, the paper's serial setting)."""
-    t = str(int(threads))
-    env = dict(os.environ, OMP_NUM_THREADS=t, OPENBLAS_NUM_THREADS=t, MKL_NUM_THREADS=t, CUDA_VISIBLE_DEVICES="")
     code = ORACLE_SNIPPET.format(root=ROOT, k=K_WAVE, p=P_DEG, reps=reps)
-    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=_oracle_env(threads),
+                         timeout=1800)
     if out.returncode != 0:
         raise RuntimeError(out.stderr[-2000:])
     return json.loads(out.stdout.strip().splitlines()[-1])
@@ -204,6 +238,50 @@ def reference_arm(args):
     print(json.dumps(line))
 
 
+# ---------------------------------------------------------------------------- GPU helpers
+def _events(n):
+    import torch
+    return [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+
+
+def _time_solves(h, f, x, stream, flush, reps, tol=1e-7, maxit=100):
+    """Mean device time of `reps` solves (L2 flushed before each), with the
+    last solve's iterations, true residual and status."""
+    import torch
+    ev = _events(reps)
+    it = tr = st = None
+    for k in range(reps):
+        flush.fill_(k & 255)
+        ev[k][0].record(stream)
+        _, it, hist, tr, st = h.solve(f, x=x, tol=tol, maxit=maxit)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in ev) / reps, it, tr, st
+
+
+def _measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def _load_net():
+    import numpy as np
+    from paper_2010_10232_gb300.learned import Net
+    wpath = os.path.join(ROOT, "paper_2010_10232_gb300", "weights", "cslp_correction.npz")
+    d = np.load(wpath)
+    net = Net(seed=0)
+    net.set_params(d["params"])
+    return net, float(d["gamma"])
+
+
+def _rel(a, b):
+    import numpy as np
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
 # ---------------------------------------------------------------------------- GPU arm
 def gpu_arm(args):
     import numpy as np
@@ -231,7 +309,7 @@ def gpu_arm(args):
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev = _events(args.steps)
     launches0 = lib.iga_launch_count()
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
@@ -241,7 +319,7 @@ def gpu_arm(args):
             _, iters, hist, tr, st = h.solve(f, x=x)
             ev[k][1].record(stream)
         torch.cuda.synchronize()
-    launches = lib.iga_launch_count() - launches0 - 0   # fill_ is torch's, not counted
+    launches = lib.iga_launch_count() - launches0   # fill_ is torch's, not counted
     ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
     ms, value = job_time(ms, ws, dist)     # job-level time per solve: N replicas solve N instances per step
 
@@ -261,7 +339,7 @@ def gpu_arm(args):
     e2e_ms = 1000.0 * sum(e2e_t) / len(e2e_t)
     _, e2e_ms = job_time(e2e_ms, ws, dist)
 
-    # ---- dominant kernel: FP64 operator apply (constant-k banded tile kernel), timed alone
+    # ---- dominant kernel of the FP64 step: the operator apply (constant-k banded tile kernel), timed alone
     peaks, src = _peaks()
     reps = 200
     xr = torch.randn(h.n, dtype=torch.complex128, device="cuda")
@@ -279,7 +357,7 @@ def gpu_arm(args):
     flops_dof = 16 * W_ + 8                      # x-pass 2 bands, y-pass 2 bands, complex scale
     apply_flops = flops_dof * h.n
     apply_bytes = 32 * h.n
-    # FP64 / FP32 FMA ceilings from the probe kernel
+    # FP64 / FP32 FMA ceilings from the probe kernel (measurement tool, measure/)
     sink = torch.zeros(2, dtype=torch.float64, device="cuda")
     import measure
     from measure import build as mbuild
@@ -298,48 +376,10 @@ def gpu_arm(args):
     fp64_nominal = 1.25                            # TFLOP/s, GB300 FP64 (profiling recipe)
     achieved_gflops = apply_flops / t_apply / 1e9
 
-    # ---- out-of-L2 operator / V-cycle bandwidth (n = 4097^2, 268 MB per complex128 vector)
-    big = {}
-    try:
-        hb64 = Helmholtz(dim=2, p=P_DEG, n_el=4096, kfield=K_WAVE * 4096 / N_EL, skip_deflation=1)
-        nb = hb64.n
-        xb = torch.randn(nb, dtype=torch.complex128, device="cuda")
-        yb = hb64.vec()
-        for _ in range(3):
-            hb64.apply_A(xb, yb)
-        e0.record(stream)
-        for _ in range(10):
-            hb64.apply_A(xb, yb)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        tb = e0.elapsed_time(e1) / 10 * 1e-3
-        big["apply_fp64_n"] = nb
-        big["apply_fp64_gbs"] = 32 * nb / tb / 1e9
-        big["apply_fp64_tflops"] = flops_dof * nb / tb / 1e12
-        del hb64, yb
-        hb32 = Helmholtz(dim=2, p=P_DEG, n_el=4096, kfield=K_WAVE * 4096 / N_EL, skip_deflation=1, precision=1)
-        zb = hb32.vec()
-        for _ in range(2):
-            hb32.vcycle(xb, zb)
-        e0.record(stream)
-        for _ in range(5):
-            hb32.vcycle(xb, zb)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        tv = e0.elapsed_time(e1) / 5 * 1e-3
-        # algorithmic bytes of one FP32 V-cycle (nu = 1/1) with complex64 storage:
-        # per level n_l*(16 jacobi0 + 24 residual + 8 restrict-read + 16 prolong rmw + 24 post)
-        # + n_{l+1}*(8 restrict-write + 8 prolong-read); plus the c128<->c64 conversions at level 0.
-        ns = [hb32.level_n(l) for l in range(hb32.levels)]
-        vb = sum(ns[l] * 88 + ns[l + 1] * 16 for l in range(len(ns) - 1)) + 48 * ns[0]
-        big["vcycle_fp32_gbs"] = vb / tv / 1e9
-        big["vcycle_fp32_ms"] = tv * 1e3
-        big["vcycle_fp32_bytes"] = vb
-        del hb32, zb, xb
-    except Exception as e:       # report, do not hide
-        big["error"] = str(e)[:200]
-
-    forms = {} if (args.no_forms or ws > 1) else other_forms(h, f, x, stream, flush, ws)
+    big = {} if args.no_forms else out_of_l2(peaks, src, stream)
+    forms = {} if (args.no_forms or ws > 1) else other_forms(h, f, x, stream, flush)
+    configs = {} if (args.no_configs or ws > 1) else other_configs(stream, flush)
+    sharded = batched_sharded(ws, rank, dist) if ws > 1 else None
     if rank != 0:
         return
     cpu = None
@@ -353,7 +393,9 @@ def gpu_arm(args):
         "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_dof": h.n, "coarse_dof": h.m, "levels": h.levels, "tol": 1e-7,
-                   "precision": "fp64", "l2": "flushed (512 MiB write) before every timed solve",
+                   "precision": "fp64 (E solve: FP32 fast-diagonalisation transforms + 2 FP64 refinement "
+                                "steps, ~1e-11 of an FP64 LU)",
+                   "l2": "flushed (512 MiB write) before every timed solve",
                    "parallelism": f"replicas x{ws}"},
         "iterations": iters, "true_res": tr,
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": 16 * h.n, "d2h_bytes_per_step": 16 * h.n},
@@ -364,41 +406,82 @@ def gpu_arm(args):
                      "traffic_note": "DRAM bytes read + written per launch, one ncu capture at this size "
                                      "(cold L2; the output stays in L2, so about the x read)",
                      "algorithmic": f"{flops_dof} flop/dof x {h.n} dofs per launch",
-                     "peak_source": "nominal FP64 of the profiling recipe",
+                     "peak_source": "nominal FP64 of the profiling recipe (no FP64 peak is measured)",
                      "probe_fma_tflops": probe, "launch_us": t_apply * 1e6,
                      "hbm_gbs": apply_bytes / t_apply / 1e9},
-        "out_of_l2": dict(big, hbm_peak_gbs=peaks.get("hbm_gbs"), peak_source=src),
+        "out_of_l2": big,
         "forms": forms,
+        "configs": configs,
         "clocks": clk.summary(),
     }
+    if sharded is not None:
+        line["batched_cfg4_split"] = sharded
     if cpu is not None:
         line["cpu_baseline"] = cpu
     print(json.dumps(line))
 
 
-def _time_solves(h, f, x, stream, flush, reps):
+def out_of_l2(peaks, src, stream):
+    """FP64 apply, FP32 operator sweep and FP32 V-cycle at 4097^2 dofs (268 MB
+    per complex128 vector, far above L2) against the measured HBM peak."""
     import torch
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
-    for k in range(reps):
-        flush.fill_(k & 255)
-        ev[k][0].record(stream)
-        _, it, hist, tr, st = h.solve(f, x=x)
-        ev[k][1].record(stream)
-    torch.cuda.synchronize()
-    return sum(a.elapsed_time(b) for a, b in ev) / reps, it, tr
+    from paper_2010_10232_gb300.solver import Helmholtz
+    big = {"hbm_peak_gbs": peaks.get("hbm_gbs"), "peak_source": src}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
+    def timed(fn, reps):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps * 1e-3
 
-def _measured_peaks():
     try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
-            return json.load(fh)
-    except (OSError, ValueError):
-        return {}
+        kb = K_WAVE * 4096 / N_EL
+        hb64 = Helmholtz(dim=2, p=P_DEG, n_el=4096, kfield=kb, skip_deflation=1)
+        nb = hb64.n
+        xb = torch.randn(nb, dtype=torch.complex128, device="cuda")
+        yb = hb64.vec()
+        tb = timed(lambda: hb64.apply_A(xb, yb), 10)
+        big["apply_fp64_n"] = nb
+        big["apply_fp64_gbs"] = 32 * nb / tb / 1e9
+        big["apply_fp64_tflops"] = (16 * (2 * P_DEG + 1) + 8) * nb / tb / 1e12
+        del hb64, yb
+        hb32 = Helmholtz(dim=2, p=P_DEG, n_el=4096, kfield=kb, skip_deflation=1, precision=1)
+        big["fp32_tiles"] = [hb32.tile(l, 1) for l in range(hb32.levels)]
+        xs = torch.randn(nb, dtype=torch.complex64, device="cuda")
+        bs = torch.randn(nb, dtype=torch.complex64, device="cuda")
+        xo = torch.empty_like(xs)
+        ts = timed(lambda: hb32.jacobi32(0, bs, xs, xo), 20)
+        big["sweep_fp32_us"] = ts * 1e6
+        big["sweep_fp32_gbs"] = 24 * nb / ts / 1e9           # x, b in; x out (complex64)
+        big["sweep_fp32_frac"] = big["sweep_fp32_gbs"] / peaks.get("hbm_gbs", 6800.0)
+        zb = hb32.vec()
+        tv = timed(lambda: hb32.vcycle(xb, zb), 5)
+        alg = VCYCLE_ALG_BYTES_PER_DOF * nb
+        big["vcycle_fp32_ms"] = tv * 1e3
+        big["vcycle_fp32_alg_bytes"] = alg
+        big["vcycle_fp32_gbs"] = alg / tv / 1e9
+        big["vcycle_fp32_frac"] = big["vcycle_fp32_gbs"] / peaks.get("hbm_gbs", 6800.0)
+        big["vcycle_note"] = (f"{VCYCLE_ALG_BYTES_PER_DOF} B/dof algorithmic (complex64 V-cycle, nu = 1/1, x 4/3 "
+                              "for the coarser levels); the timed call includes the complex128 <-> complex64 "
+                              "conversions of its input and output")
+        del hb32, zb, xb, xs, bs, xo
+    except Exception as e:       # report, do not hide
+        big["error"] = str(e)[:300]
+    torch.cuda.empty_cache()
+    return big
 
 
-def other_forms(h64, f, x, stream, flush, ws):
-    """Mixed precision, learned correction and the batched 64-instance launch,
-    each with its error against the oracle's direct FP64 solution."""
+def other_forms(h64, f, x, stream, flush):
+    """Mixed precision and learned correction against the plain FP64 form, at
+    1e-7 and at a tolerance where every form's error against the oracle's
+    direct FP64 solution is <= 1e-6; the exact CSLP C_ex (no deflation) and
+    the deflation alone D on the same problem; the 64-instance batch."""
     import numpy as np
     import torch
     import workloads as W
@@ -407,62 +490,71 @@ def other_forms(h64, f, x, stream, flush, ws):
     pr = W.config2(k=K_WAVE, p=P_DEG)
     ref = None
     try:
-        from oracle.solver import Solver, rel_err      # error report only (CPU, untimed)
+        from oracle.solver import Solver      # error report only (CPU, untimed)
         s_or = Solver(pr)
         ref = s_or.direct(s_or.load())
     except Exception as e:
         out["oracle_error"] = str(e)[:200]
-    err = (lambda u: float(np.linalg.norm(u - ref) / np.linalg.norm(ref))) if ref is not None else (lambda u: None)
-    def tight(h):
-        """error of the same form solved to a relative residual of 1e-10"""
-        xt = h.vec()
-        _, it_t, _, tr_t, st_t = h.solve(f, x=xt, tol=1e-10, maxit=300)
-        return {"rel_err_vs_oracle_direct": err(xt.cpu().numpy()), "iterations": it_t, "status": st_t}
+    err = (lambda u: _rel(u, ref)) if ref is not None else (lambda u: None)
 
-    out["plain_fp64"] = {"rel_err_vs_oracle_direct": err(x.cpu().numpy()), "tol_1e-10": tight(h64)}
+    def record(h, tol, reps=5):
+        xx = h.vec()
+        h.solve(f, x=xx, tol=tol, maxit=300)
+        ms, it, tr, st = _time_solves(h, f, xx, stream, flush, reps, tol=tol, maxit=300)
+        return {"ms": ms, "iterations": it, "true_res": tr, "status": st,
+                "rel_err_vs_oracle_direct": err(xx.cpu().numpy())}
+
     try:
+        forms = {"plain_fp64": (h64, None)}
         hm = from_problem(pr, precision=1)
-        xm = hm.vec()
-        hm.solve(f, x=xm)
-        ms, it, tr = _time_solves(hm, f, xm, stream, flush, 5)
-        out["mixed_fp32_vcycle"] = {"ms": ms, "iterations": it, "true_res": tr,
-                                    "rel_err_vs_oracle_direct": err(xm.cpu().numpy()), "tol_1e-10": tight(hm)}
-        wpath = os.path.join(ROOT, "paper_2010_10232_gb300", "weights", "cslp_correction.npz")
-        if os.path.exists(wpath):
-            from paper_2010_10232_gb300.learned import Net
-            d = np.load(wpath)
-            net = Net(seed=0)
-            net.set_params(d["params"])
-            hm.attach(net, float(d["gamma"]))
-            hm.solve(f, x=xm)
-            ms, it, tr = _time_solves(hm, f, xm, stream, flush, 5)
-            out["learned_correction"] = {"ms": ms, "iterations": it, "true_res": tr,
-                                         "rel_err_vs_oracle_direct": err(xm.cpu().numpy()), "tol_1e-10": tight(hm)}
-            # the network alone on the bench grid (one correction's inference)
-            nx = hm.level_nx(0)
-            xin = torch.zeros(1, nx, nx, 16, dtype=torch.bfloat16, device="cuda")
-            xin[..., :3] = torch.randn(1, nx, nx, 3, device="cuda").to(torch.bfloat16)
-            for _ in range(3):
-                net.forward(xin)
-            torch.cuda.synchronize()
-            a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a_.record()
-            for _ in range(20):
-                net.forward(xin)
-            b_.record()
-            torch.cuda.synchronize()
-            us = a_.elapsed_time(b_) / 20 * 1e3
-            flop = 2 * 9 * (3 * 32 + 32 * 32 + 32 * 32 + 32 * 2) * nx * nx     # algorithmic, unpadded channels
-            bf16_peak = _measured_peaks().get("bf16_tflops")
-            out["learned_correction"]["cnn_forward"] = {
-                "us": us, "pixels": nx * nx, "tflops": flop / us / 1e6,
-                "frac_of_bf16_peak": (flop / us / 1e6 / bf16_peak) if bf16_peak else None,
-                "note": "3x3 convs 3-32-32-32-2, bf16 mma.sync with FP32 accumulation; bound by launches "
-                        "and the pack/epilogue traffic at this size, not by the tensor pipe"}
-            hm.attach(None)
-        del hm
+        forms["mixed_fp32_vcycle"] = (hm, None)
+        net, gamma = _load_net()
+        forms["learned_correction"] = (hm, (net, gamma))
+        for tol, key in ((1e-7, "tol_1e-7"), (TOL_MATCHED, "matched_error")):
+            out[key] = {"tol": tol}
+            for name, (hh, nn) in forms.items():
+                if nn is not None:
+                    hh.attach(nn[0], nn[1])
+                out[key][name] = record(hh, tol)
+                if nn is not None:
+                    hh.attach(None)
+        out["matched_error"]["note"] = ("the tolerance at which every form's error against the oracle's direct "
+                                        "FP64 solution is <= 1e-6 (at 1e-7 the deflated preconditioned residual "
+                                        "leaves ~5e-6 in the solution at this nearly singular coarse matrix)")
+        # the network alone on the bench grid (one correction's inference)
+        nx = hm.level_nx(0)
+        xin = torch.zeros(1, nx, nx, 16, dtype=torch.bfloat16, device="cuda")
+        xin[..., :3] = torch.randn(1, nx, nx, 3, device="cuda").to(torch.bfloat16)
+        for _ in range(3):
+            net.forward(xin)
+        torch.cuda.synchronize()
+        a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a_.record()
+        for _ in range(20):
+            net.forward(xin)
+        b_.record()
+        torch.cuda.synchronize()
+        us = a_.elapsed_time(b_) / 20 * 1e3
+        flop = 2 * 9 * (3 * 32 + 32 * 32 + 32 * 32 + 32 * 2) * nx * nx     # algorithmic, unpadded channels
+        bf16_peak = _measured_peaks().get("bf16_tflops")
+        out["cnn_forward"] = {"us": us, "pixels": nx * nx, "tflops": flop / us / 1e6,
+                              "frac_of_bf16_peak": (flop / us / 1e6 / bf16_peak) if bf16_peak else None}
+        del hm, net
     except Exception as e:
         out["mixed_error"] = str(e)[:200]
+    try:
+        # Section 4.3's comparison systems on the same problem: C_ex (beta_2 = 1/(3k), no deflation)
+        # and D (deflation alone); the paper's D_eps C_MG^12 setting (beta_2 = 4.2, nu = 3, 12 cycles)
+        comp = {}
+        for name, kw in (("C_ex", dict(precond=1, deflation=0, beta=(1.0, 1.0 / (3.0 * K_WAVE)))),
+                         ("D", dict(n_vcycles=0)),
+                         ("DC_MG^12_beta4.2_nu3", dict(n_vcycles=12, nu_pre=3, nu_post=3, beta=(1.0, 4.2)))):
+            hc = from_problem(pr, **kw)
+            comp[name] = record(hc, 1e-7, reps=3)
+            del hc
+        out["section4_comparison"] = comp
+    except Exception as e:
+        out["comparison_error"] = str(e)[:200]
     try:
         inst = W.config4(64)
         ctxs, rhs = [], []
@@ -520,7 +612,154 @@ def other_forms(h64, f, x, stream, flush, ws):
         del ctxs32, ctxs64, rhs
     except Exception as e:
         out["batched_error"] = str(e)[:200]
+    torch.cuda.empty_cache()
     return out
+
+
+def other_configs(stream, flush):
+    """The other configurations of the workload: the 1D problem (microseconds
+    per iteration), the MP 2-A k x p sweep, the three-layer field at 640^2
+    (true residual with the oracle's assembled matrix, and the gap to the FP64
+    solve at 1e-12), and 1280^2 elements at k = 800 (plain, mixed, learned;
+    gap to the FP64 solve at 1e-12)."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2010_10232_gb300.solver import Helmholtz, from_problem
+    out = {}
+    try:
+        pr1 = W.config1()[0]
+        h1 = from_problem(pr1)
+        rows = {}
+        for name, f_ in (("point_source", h1.point_source(0.5)),
+                         ("seeded_normal", torch.from_numpy(W.seeded_normal_rhs(h1.n, 0).astype(np.complex128)).cuda())):
+            xx = h1.vec()
+            ms, it, tr, st = _time_solves(h1, f_, xx, stream, flush, 10)
+            rows[name] = {"ms": ms, "iterations": it, "us_per_iteration": 1e3 * ms / max(it, 1), "true_res": tr}
+        out["cfg1_1d_k50_p2"] = rows
+        del h1
+    except Exception as e:
+        out["cfg1_error"] = str(e)[:200]
+    try:
+        sweep = {}
+        for k in (50.0, 100.0, 200.0, 400.0):
+            for p in (1, 2, 3, 4):
+                prk = W.config2(k=k, p=p)
+                hk = from_problem(prk)
+                fk = hk.point_source(0.5, 0.5)
+                xx = hk.vec()
+                hk.solve(fk, x=xx)
+                ms, it, tr, st = _time_solves(hk, fk, xx, stream, flush, 3)
+                sweep[f"k{int(k)}_p{p}"] = {"n_el": prk.n_el, "n_dof": hk.n, "ms": ms, "iterations": it,
+                                            "true_res": tr, "status": st}
+                del hk
+        out["cfg2_sweep"] = sweep
+    except Exception as e:
+        out["cfg2_sweep_error"] = str(e)[:200]
+    torch.cuda.empty_cache()
+    try:
+        pr3 = W.config3()
+        rows, sols = {}, []
+        for prec in (0, 1):
+            t0 = time.perf_counter()
+            h3 = from_problem(pr3, precision=prec)
+            setup_s = time.perf_counter() - t0
+            f3 = h3.point_source(*pr3.sources[0])
+            xx = h3.vec()
+            h3.solve(f3, x=xx)
+            ms, it, tr, st = _time_solves(h3, f3, xx, stream, flush, 3)
+            rows["plain_fp64" if prec == 0 else "mixed_fp32_vcycle"] = {"setup_s": setup_s, "ms": ms,
+                                                                        "iterations": it, "true_res": tr}
+            sols.append(xx.cpu().numpy())
+            if prec == 0:
+                xt = h3.vec()
+                h3.solve(f3, x=xt, tol=1e-12, maxit=300)
+                tight = xt.cpu().numpy()
+            del h3
+        for name, u in zip(("plain_fp64", "mixed_fp32_vcycle"), sols):
+            rows[name]["rel_gap_to_fp64_tol1e-12"] = _rel(u, tight)
+        path = os.path.join(ROOT, "_bench_cfg3_sols.npy")
+        np.save(path, np.stack(sols))
+        try:
+            code = ORACLE_RESIDUAL_SNIPPET.format(root=ROOT, path=path)
+            r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=_oracle_env(1),
+                               timeout=240)
+            if r.returncode == 0:
+                res = json.loads(r.stdout.strip().splitlines()[-1])
+                rows["plain_fp64"]["true_res_oracle_matrix"] = res[0]
+                rows["mixed_fp32_vcycle"]["true_res_oracle_matrix"] = res[1]
+            else:
+                rows["oracle_error"] = r.stderr[-200:]
+        finally:
+            os.remove(path)
+        rows["note"] = ("three-layer k 100/150/250, p = 3, 640^2 elements, first seeded source; the oracle's "
+                        "direct solve does not finish in bench time at 410 881 dofs, so the error is reported as "
+                        "the true residual with the oracle's assembled matrix and as the gap to the validated "
+                        "FP64 path solved to 1e-12")
+        out["cfg3_three_layer_640"] = rows
+    except Exception as e:
+        out["cfg3_error"] = str(e)[:300]
+    torch.cuda.empty_cache()
+    try:
+        rows = {}
+        t0 = time.perf_counter()
+        h5 = Helmholtz(dim=2, p=3, n_el=1280, kfield=800.0)
+        setup_s = time.perf_counter() - t0
+        f5 = h5.point_source(0.5, 0.5)
+        xt = h5.vec()
+        h5.solve(f5, x=xt, tol=1e-12, maxit=300)
+        tight = xt.cpu().numpy()
+        xx = h5.vec()
+        h5.solve(f5, x=xx)
+        ms, it, tr, st = _time_solves(h5, f5, xx, stream, flush, 2)
+        rows["plain_fp64"] = {"setup_s": setup_s, "ms": ms, "iterations": it, "true_res": tr,
+                              "rel_gap_to_fp64_tol1e-12": _rel(xx.cpu().numpy(), tight)}
+        del h5
+        h5m = Helmholtz(dim=2, p=3, n_el=1280, kfield=800.0, precision=1)
+        for name, nn in (("mixed_fp32_vcycle", None), ("learned_correction", _load_net())):
+            if nn is not None:
+                h5m.attach(nn[0], nn[1])
+            xx = h5m.vec()
+            h5m.solve(f5, x=xx)
+            ms, it, tr, st = _time_solves(h5m, f5, xx, stream, flush, 2)
+            rows[name] = {"ms": ms, "iterations": it, "true_res": tr,
+                          "rel_gap_to_fp64_tol1e-12": _rel(xx.cpu().numpy(), tight)}
+            if nn is not None:
+                h5m.attach(None)
+        rows["note"] = ("constant k = 800, p = 3, 1280^2 elements (1 640 961 dofs), centre source; the three-layer "
+                        "field scaled to k <= 800 is not timed here (its block-LU coarse solve takes ~74 s of setup "
+                        "at this size)")
+        out["cfg5_1280_k800"] = rows
+        del h5m
+    except Exception as e:
+        out["cfg5_error"] = str(e)[:300]
+    torch.cuda.empty_cache()
+    return out
+
+
+def batched_sharded(ws, rank, dist):
+    """N > 1: the 64-instance batch split by instance across the ranks (the
+    multi-GPU design of the batched form): each rank solves its share in one
+    graph launch; the wall time is the maximum over ranks."""
+    import torch
+    import workloads as W
+    from paper_2010_10232_gb300.sharding import solve_batched_sharded
+    try:
+        probs = W.config4(64)
+        solve_batched_sharded(probs, rank, ws, dist=dist, precision=1)     # warm-up, builds the workspaces
+        torch.cuda.synchronize()
+        dist.barrier()
+        t0 = time.perf_counter()
+        _, counts = solve_batched_sharded(probs, rank, ws, dist=dist, precision=1)
+        torch.cuda.synchronize()
+        dt = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device="cuda")
+        dist.all_reduce(dt, op=dist.ReduceOp.MAX)
+        rec = {"instances": len(probs), "wall_ms_max_over_ranks": 1e3 * float(dt.item()), "ranks": ws}
+        if counts is not None:
+            rec["rhs"] = sum(len(v[0]) for v in counts.values())
+        return rec
+    except Exception as e:
+        return {"error": str(e)[:200]}
 
 
 def main():
@@ -531,6 +770,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--no-configs", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)

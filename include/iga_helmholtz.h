@@ -158,6 +158,14 @@ iga_status iga_apply_Mshift(iga_ctx* ctx, int level, const iga_c128* x, iga_c128
 iga_status iga_jacobi(iga_ctx* ctx, int level, const iga_c128* b, iga_c128* x_in,
                       iga_c128* x_out, int sweeps);
 
+/* FP32 forms of the two operators above, as the FP32 V-cycle (precision 1)
+   applies them: y = M_beta x and one damped Jacobi sweep x_out = x_in +
+   omega D^{-1} (b - M_beta x_in) on level `level`, with FP32 bands and
+   FP32 accumulation (single rounding per fused multiply-add).  Vectors:
+   complex64, DEVICE, 8-byte aligned; x_in and x_out must not alias. */
+iga_status iga_apply_Mshift32(iga_ctx* ctx, int level, const iga_c64* x, iga_c64* y);
+iga_status iga_jacobi32(iga_ctx* ctx, int level, const iga_c64* b, const iga_c64* x_in, iga_c64* x_out);
+
 /* Multigrid transfers between level l (fine) and l+1 (coarse): knot-insertion
    prolongation P_l (Section 4.2: linear interpolation is the p = 1 case).
    restrict: coarse = P_l^T fine.  prolong_add: fine += P_l coarse.  FP64. */

@@ -4,6 +4,7 @@
     python -m measure.profile_cases apply32 # FP32 V-cycle, 4097^2 dofs
     python -m measure.profile_cases solve   # one bench solve
     python -m measure.profile_cases solve_host  # same, iterations launched from the host
+    python -m measure.profile_cases sweep32     # FP32 Jacobi sweep on level 0, 4097^2 dofs
 
 The solve cases open a profiler range around the solve only (capture them
 with `ncu --profile-from-start off`).
@@ -33,6 +34,20 @@ def main(case: str) -> None:
         x = torch.randn(h.n, dtype=torch.complex128, device="cuda")
         z = h.vec()
         h.vcycle(x, z)
+    elif case == "sweep32":
+        # one FP32 Jacobi sweep on level 0 at 4097^2 dofs inside the profiler
+        # range (capture with ncu --profile-from-start off)
+        h = Helmholtz(dim=2, p=3, n_el=4096, kfield=2560.0, skip_deflation=1, precision=1)
+        xs = torch.randn(h.n, dtype=torch.complex64, device="cuda")
+        bs = torch.randn(h.n, dtype=torch.complex64, device="cuda")
+        xo = torch.empty_like(xs)
+        h.jacobi32(0, bs, xs, xo)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        for _ in range(2):
+            h.jacobi32(0, bs, xs, xo)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
     elif case in ("solve", "solve_host"):
         h = Helmholtz(dim=2, p=3, n_el=320, kfield=200.0, host_loop=int(case == "solve_host"))
         f = h.point_source(0.5, 0.5)

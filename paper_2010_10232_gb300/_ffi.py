@@ -80,6 +80,8 @@ _SIG = {
     "iga_apply_A": (C.c_int, [_VP, _VP, _VP]),
     "iga_apply_Mshift": (C.c_int, [_VP, C.c_int, _VP, _VP]),
     "iga_jacobi": (C.c_int, [_VP, C.c_int, _VP, _VP, _VP, C.c_int]),
+    "iga_apply_Mshift32": (C.c_int, [_VP, C.c_int, _VP, _VP]),
+    "iga_jacobi32": (C.c_int, [_VP, C.c_int, _VP, _VP, _VP]),
     "iga_restrict": (C.c_int, [_VP, C.c_int, _VP, _VP]),
     "iga_prolong_add": (C.c_int, [_VP, C.c_int, _VP, _VP]),
     "iga_coarse_solve": (C.c_int, [_VP, _VP, _VP]),

@@ -242,6 +242,25 @@ iga_status iga_jacobi(iga_ctx* ctx, int level, const iga_c128* b, iga_c128* x_in
   return IGA_OK;
 }
 
+static bool aligned8(const void* p) { return p && (((uintptr_t)p) & 7u) == 0; }
+
+iga_status iga_apply_Mshift32(iga_ctx* ctx, int level, const iga_c64* x, iga_c64* y) {
+  CHECK_CTX();
+  if (!aligned8(x) || !aligned8(y)) return set_err(ctx, IGA_E_INVALID, "x / y NULL or not 8-byte aligned");
+  if (level < 0 || level >= ctx->L) return set_err(ctx, IGA_E_INVALID, "level");
+  if ((const void*)x == (const void*)y) return set_err(ctx, IGA_E_INVALID, "x and y alias");
+  return op_apply<float>(ctx, level, OP_MB, (const float2*)x, (float2*)y, nullptr, EPI_Y, nullptr, 0.0);
+}
+
+iga_status iga_jacobi32(iga_ctx* ctx, int level, const iga_c64* b, const iga_c64* x_in, iga_c64* x_out) {
+  CHECK_CTX();
+  if (!aligned8(b) || !aligned8(x_in) || !aligned8(x_out)) return set_err(ctx, IGA_E_INVALID, "NULL or not 8-byte aligned");
+  if (level < 0 || level >= ctx->L) return set_err(ctx, IGA_E_INVALID, "level");
+  if ((const void*)x_in == (const void*)x_out) return set_err(ctx, IGA_E_INVALID, "x_in and x_out alias");
+  return op_apply<float>(ctx, level, OP_MB, (const float2*)x_in, (float2*)x_out, nullptr, EPI_JACOBI,
+                         (const float2*)b, ctx->prm.omega);
+}
+
 iga_status iga_restrict(iga_ctx* ctx, int level, const iga_c128* fine, iga_c128* coarse) {
   CHECK_CTX(); CHECK_PTR(fine); CHECK_PTR(coarse);
   if (level < 0 || level + 1 >= ctx->L) return set_err(ctx, IGA_E_INVALID, "level");

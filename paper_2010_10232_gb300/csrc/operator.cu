@@ -495,6 +495,9 @@ static void launch_kron_pair(const OpArgs<double>& a, cudaStream_t st, int tile)
   else launch_kron_pair_tile<P, EPI, 8, 4, 128>(a, st);
 }
 
+void sweep32_launch(int p, int epi, int nx, int ny, const float* K, const float* M, float2 cm, const float2* x,
+                    float2* y, const float2* z, float omega, cudaStream_t st);
+
 template <int P, typename T, int EPI>
 static void launch_op(iga_ctx* ctx, const OpArgs<T>& a, int level) {
   cudaStream_t st = ctx->st;
@@ -507,6 +510,12 @@ static void launch_op(iga_ctx* ctx, const OpArgs<T>& a, int level) {
       size_t mid = (size_t)cdiv(a.nx, 16) * cdiv(a.ny, 16);
       // FP64 dependency chains favour more, smaller blocks on small grids
       tile = big >= (size_t)3 * ctx->num_sms ? 0 : (mid >= (size_t)ctx->num_sms || sizeof(T) == 4 ? 1 : 3);
+    }
+    if constexpr (sizeof(T) == 4) {
+      if (tile == 6) {
+        sweep32_launch(P, EPI, a.nx, a.ny, a.K, a.M, a.c, a.x, a.y, a.z, a.omega, st);
+        return;
+      }
     }
     if (tile == 0) launch_kron_tile<P, T, EPI, 32, 16>(a, st);
     else if (tile == 1) launch_kron_tile<P, T, EPI, 16, 16>(a, st);
@@ -655,7 +664,8 @@ iga_status op_apply_bands(iga_ctx* ctx, int P, int nx, int ny, const double* K, 
 // ------------------------------------------------------------------ tile autotuner
 // For constant k in 2D the operator kernel has six tile shapes: 32x16, 16x16,
 // 32x8 outputs per 256-thread block, 8x8 per 64-thread block, and (FP64 only)
-// the lane-pair kernel with 8x8 outputs per 256 threads or 8x4 per 128.  At
+// the lane-pair kernel with 8x8 outputs per 256 threads or 8x4 per 128; FP32
+// has in their place the register-stencil sweep of sweep32.cu (code 6).  At
 // setup every level times each shape on its own operator, FP64 and FP32, as
 // the solve runs it: TUNE_REPS dependent launches captured in one CUDA graph
 // per shape (host launch costs, which would hide the small levels'
@@ -713,13 +723,16 @@ static iga_status tune_level(iga_ctx* ctx, int l, int slot) {
   C* x = (C*)(slot == 0 ? (void*)L.vb : (void*)L.fb);
   C* y = (C*)(slot == 0 ? (void*)L.vx : (void*)L.fx);
   CK(cudaMemsetAsync(x, 0, sizeof(C) * L.n, ctx->st));
-  const int ntiles = sizeof(T) == 8 ? 6 : 4;
+  // candidate shapes: FP64 0..5; FP32 0..3 and the register-stencil sweep (6)
+  static const int cand64[] = {0, 1, 2, 3, 4, 5}, cand32[] = {0, 1, 2, 3, 6};
+  const int* cand = sizeof(T) == 8 ? cand64 : cand32;
+  const int ntiles = sizeof(T) == 8 ? 6 : 5;
   cudaGraphExec_t ge[TUNE_MAX_TILES] = {};
   cudaEvent_t ev[2 * TUNE_MAX_TILES] = {};
   float best_ms[TUNE_MAX_TILES];
   iga_status s = IGA_OK;
   for (int t = 0; t < ntiles && s == IGA_OK; ++t) {
-    ctx->tile[l][slot] = t;
+    ctx->tile[l][slot] = cand[t];
     best_ms[t] = 1e30f;
     s = capture_applies<T>(ctx, l, x, y, &ge[t]);
   }
@@ -749,9 +762,9 @@ static iga_status tune_level(iga_ctx* ctx, int l, int slot) {
   int best_tile = 0;
   for (int t = 1; t < ntiles; ++t)
     if (best_ms[t] < best_ms[best_tile]) best_tile = t;
-  ctx->tile[l][slot] = best_tile;
+  ctx->tile[l][slot] = cand[best_tile];
   std::lock_guard<std::mutex> lock(g_tile_mu);
-  g_tile_cache[key] = best_tile;
+  g_tile_cache[key] = cand[best_tile];
   return IGA_OK;
 }
 
@@ -769,8 +782,8 @@ extern "C" iga_status iga_set_tile(iga_ctx* ctx, int level, int precision, int t
   if (!ctx) return IGA_E_INVALID;
   if (level < 0 || level >= ctx->L || precision < 0 || precision > 1)
     return set_err(ctx, IGA_E_INVALID, "iga_set_tile: level %d / precision %d out of range", level, precision);
-  if (tile < -1 || tile > (precision == 0 ? 5 : 3))
-    return set_err(ctx, IGA_E_INVALID, "iga_set_tile: tile %d not available in this precision", tile);
+  const bool ok = tile >= -1 && (precision == 0 ? tile <= 5 : (tile <= 3 || tile == 6));
+  if (!ok) return set_err(ctx, IGA_E_INVALID, "iga_set_tile: tile %d not available in this precision", tile);
   ctx->tile[level][precision] = tile;
   // the cached loop graph captured the previous kernels
   if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);

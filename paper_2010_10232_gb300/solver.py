@@ -157,6 +157,19 @@ class Helmholtz:
         self._check(self._L.iga_jacobi(self._h, level, _ptr(b), _ptr(xin), _ptr(out), int(sweeps)))
         return out
 
+    def vec32(self, n=None):
+        return torch.zeros(self.n if n is None else n, dtype=torch.complex64, device=self.device)
+
+    def apply_Mshift32(self, level, x, y=None):
+        y = self.vec32(self.level_n(level)) if y is None else y
+        self._check(self._L.iga_apply_Mshift32(self._h, level, _ptr(x), _ptr(y)))
+        return y
+
+    def jacobi32(self, level, b, x, out=None):
+        out = torch.empty_like(x) if out is None else out
+        self._check(self._L.iga_jacobi32(self._h, level, _ptr(b), _ptr(x), _ptr(out)))
+        return out
+
     def restrict(self, level, fine):
         c = self.vec(self.level_n(level + 1))
         self._check(self._L.iga_restrict(self._h, level, _ptr(fine), _ptr(c)))

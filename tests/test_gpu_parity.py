@@ -541,3 +541,54 @@ def test_config3_full_size_apply_and_solves(cfg3_full):
         true_res = np.linalg.norm(f - d.A @ un) / np.linalg.norm(f)
         assert abs(true_res - tr) <= 1e-6 * tr + 1e-14
         assert np.all(np.isfinite(un))
+
+
+@pytest.mark.parametrize("n_el,p,k", [(40, 1, 15.0), (34, 2, 15.0), (256, 3, 150.0), (24, 4, 12.0), (20, 5, 10.0),
+                                      (160, 5, 100.0)])
+def test_fp32_register_stencil_sweep(n_el, p, k):
+    """The FP32 register-stencil sweep (tile code 6: interior tiles take the
+    uniform-knot stencil from registers, edge tiles their own band rows)
+    forced on every level: the FP32 V-cycle stays within the FP32 tolerance
+    of the oracle and within FP32 rounding of the shared-memory tile kernel."""
+    pr = W.small_2d(n_el=n_el, p=p, k=k)
+    hier = mg.MGHierarchy(2, p, n_el, pr.kfield, 1.0, 0.5)
+    r = rvec(pr.n_x ** 2, 84)
+    ref = hier.apply(r, 1)
+    h6 = from_problem(pr, precision=1, skip_deflation=1)
+    h0 = from_problem(pr, precision=1, skip_deflation=1)
+    for l in range(h6.levels):
+        h6.set_tile(l, 1, 6)
+        h0.set_tile(l, 1, 0)
+        assert h6.tile(l, 1) == 6
+    z6 = to_n(h6.vcycle(to_t(r)))
+    z0 = to_n(h0.vcycle(to_t(r)))
+    e0, e6 = rel_err(z0, ref), rel_err(z6, ref)
+    print(f"n_el={n_el} p={p}: FP32 V-cycle error tile 0 {e0:.2e}, tile 6 {e6:.2e}, gap {rel_err(z6, z0):.2e}")
+    # both carry the FP32 rounding of the V-cycle (it grows with p); the two
+    # kernels round in different orders, so they agree to that level
+    assert e6 <= max(1e-4, 2.0 * e0)
+    assert rel_err(z6, z0) <= max(2e-6, 2.0 * e0)
+
+
+@pytest.mark.parametrize("n_el,p,k", [(40, 1, 15.0), (128, 3, 80.0), (20, 5, 10.0), (200, 5, 100.0)])
+@pytest.mark.parametrize("tile", [0, 1, 2, 3, 6])
+def test_fp32_operator_and_sweep_every_tile(n_el, p, k, tile):
+    """FP32 M_beta x and one FP32 damped Jacobi sweep on every level, each FP32
+    tile shape forced, against the oracle's FP64 level operator applied to the
+    same complex64 inputs: FP32 rounding (a few ulps times the band width)."""
+    pr = W.small_2d(n_el=n_el, p=p, k=k)
+    hier = mg.MGHierarchy(2, p, n_el, pr.kfield, 1.0, 0.5)
+    h = from_problem(pr, precision=1, skip_deflation=1)
+    for l, lvl in enumerate(hier.levels):
+        h.set_tile(l, 1, tile)
+        n = lvl.Mb.shape[0]
+        x = rvec(n, 300 + l).astype(np.complex64)
+        b = rvec(n, 400 + l).astype(np.complex64)
+        xt = torch.from_numpy(x).cuda()
+        bt = torch.from_numpy(b).cuda()
+        y = h.apply_Mshift32(l, xt)
+        ref = lvl.Mb @ x.astype(np.complex128)
+        assert rel_err(to_n(y).astype(np.complex128), ref) <= 2e-6, l
+        xo = h.jacobi32(l, bt, xt)
+        refj = hier.jacobi(lvl, x.astype(np.complex128), b.astype(np.complex128), 1)
+        assert rel_err(to_n(xo).astype(np.complex128), refj) <= 2e-6, l

@@ -283,6 +283,7 @@ iga_status iga_vcycle_cslp(iga_ctx* ctx, const iga_c128* r, iga_c128* z) {
   if (ctx->prm.n_vcycles < 1) return set_err(ctx, IGA_E_INVALID, "context built with n_vcycles = 0");
   if ((const void*)r == (const void*)z) return set_err(ctx, IGA_E_INVALID, "r and z alias");
   if (ctx->prm.precision == 0) return mg_vcycle<double>(ctx, (const double2*)r, (double2*)z);
+  if (!ctx->net) return mg_vcycle32_c128(ctx, (const double2*)r, (double2*)z);
   size_t n = ctx->lv[0].n;
   launch_convert_d2f((const double2*)r, ctx->fin, n, ctx->st);
   TRY(mg_vcycle<float>(ctx, ctx->fin, ctx->fout));

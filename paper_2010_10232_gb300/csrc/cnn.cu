@@ -46,6 +46,8 @@ struct iga_net {
   size_t cap_part = 0;
   float* lossbuf = nullptr;   // per-sample (num, den) and the loss
   int cap_b = 0;
+  int* tc_err = nullptr;      // set by a tensor-core convolution whose bounded wait gave up
+  int num_sms = 148;
   DevBuf bufs;
   std::string err;
 };
@@ -362,12 +364,36 @@ static iga_status net_workspace(iga_net* n, int B, int H, int W) {
   return IGA_OK;
 }
 
-// forward: act[0] already holds the input; result in n->out
+cudaError_t conv_tc_launch(int cin, int n, int epi, const bf16* X, const bf16* Wt, int coutp, const float* bias,
+                           const bf16* mask, void* Y, int B, int H, int W, int* err, int num_sms, cudaStream_t st);
+
+// one convolution layer on the tensor cores (conv_tc.cu): CIN input channels,
+// N accumulator columns, Wt with coutp rows
+static void conv(iga_net* n, int cin, int N, int epi, const bf16* X, const bf16* Wt, int coutp, const float* bias,
+                 const bf16* mask, void* Y, int B, int H, int W, cudaStream_t st) {
+  conv_tc_launch(cin, N, epi, X, Wt, coutp, bias, mask, Y, B, H, W, n->tc_err, n->num_sms, st);
+}
+
+// forward: act[0] already holds the input; result in n->out (the output
+// layer runs with 16 accumulator columns: its 8 stored weight rows and zeros)
 static void net_forward(iga_net* n, int B, int H, int W, cudaStream_t st) {
-  launch_conv<16, 32, 0>(n->act[0], n->wf[0], n->master + n->off_b[0], nullptr, n->act[1], B, H, W, st);
-  launch_conv<32, 32, 0>(n->act[1], n->wf[1], n->master + n->off_b[1], nullptr, n->act[2], B, H, W, st);
-  launch_conv<32, 32, 0>(n->act[2], n->wf[2], n->master + n->off_b[2], nullptr, n->act[3], B, H, W, st);
-  launch_conv<32, 8, 1>(n->act[3], n->wf[3], n->master + n->off_b[3], nullptr, n->out, B, H, W, st);
+  conv(n, 16, 32, 0, n->act[0], n->wf[0], 32, n->master + n->off_b[0], nullptr, n->act[1], B, H, W, st);
+  conv(n, 32, 32, 0, n->act[1], n->wf[1], 32, n->master + n->off_b[1], nullptr, n->act[2], B, H, W, st);
+  conv(n, 32, 32, 0, n->act[2], n->wf[2], 32, n->master + n->off_b[2], nullptr, n->act[3], B, H, W, st);
+  conv(n, 32, 16, 1, n->act[3], n->wf[3], 8, n->master + n->off_b[3], nullptr, n->out, B, H, W, st);
+}
+
+// status of the tensor-core waits since the last check (synchronises)
+static iga_status net_check_tc(iga_net* n, cudaStream_t st) {
+  int h = 0;
+  if (cudaMemcpyAsync(&h, n->tc_err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return net_err(n, IGA_E_CUDA, "net: stream error");
+  if (h) {
+    cudaMemsetAsync(n->tc_err, 0, sizeof(int), st);
+    return net_err(n, IGA_E_TIMEOUT, "net: a tensor-core accumulator wait gave up");
+  }
+  return IGA_OK;
 }
 
 template <int CINP, int COUTP>
@@ -387,11 +413,11 @@ static void net_backward(iga_net* n, const float* T, int B, int H, int W, cudaSt
   k_loss_grad<<<cdiv(px * B, 256), 256, 0, st>>>(n->out, T, px, B, n->lossbuf, n->g16, n->lossbuf + 2 * B); iga_count_launch();
   // layer 4 (32 -> 2): weight gradient, then input gradient through the ReLU of act[3]
   net_wgrad<32, 16>(n, 3, n->act[3], n->g16, B, H, W, st);
-  launch_conv<16, 32, 2>(n->g16, n->wb[3], nullptr, n->act[3], n->ga, B, H, W, st);
+  conv(n, 16, 32, 2, n->g16, n->wb[3], 32, nullptr, n->act[3], n->ga, B, H, W, st);
   net_wgrad<32, 32>(n, 2, n->act[2], n->ga, B, H, W, st);
-  launch_conv<32, 32, 2>(n->ga, n->wb[2], nullptr, n->act[2], n->gb, B, H, W, st);
+  conv(n, 32, 32, 2, n->ga, n->wb[2], 32, nullptr, n->act[2], n->gb, B, H, W, st);
   net_wgrad<32, 32>(n, 1, n->act[1], n->gb, B, H, W, st);
-  launch_conv<32, 32, 2>(n->gb, n->wb[1], nullptr, n->act[1], n->ga, B, H, W, st);
+  conv(n, 32, 32, 2, n->gb, n->wb[1], 32, nullptr, n->act[1], n->ga, B, H, W, st);
   net_wgrad<16, 32>(n, 0, n->act[0], n->ga, B, H, W, st);
 }
 
@@ -421,7 +447,8 @@ iga_status iga_net_create(unsigned long long seed, iga_net** out) {
   n->grad = nalloc<float>(n, k);
   n->m = nalloc<float>(n, k);
   n->v = nalloc<float>(n, k);
-  bool ok = n->master && n->grad && n->m && n->v;
+  n->tc_err = nalloc<int>(n, 1);
+  bool ok = n->master && n->grad && n->m && n->v && n->tc_err;
   for (int l = 0; l < 4 && ok; ++l) {
     size_t sz = (size_t)(l == 3 ? 16 : NET_CP[l + 1]) * 9 * 32;
     n->wf[l] = nalloc<bf16>(n, sz);
@@ -429,6 +456,12 @@ iga_status iga_net_create(unsigned long long seed, iga_net** out) {
     ok = n->wf[l] && n->wb[l];
   }
   if (!ok) { delete n; return IGA_E_OOM; }
+  cudaMemset(n->tc_err, 0, sizeof(int));
+  {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  }
   cudaMemset(n->m, 0, sizeof(float) * k);
   cudaMemset(n->v, 0, sizeof(float) * k);
   cudaMemset(n->grad, 0, sizeof(float) * k);
@@ -497,7 +530,7 @@ iga_status iga_net_grad(iga_net* n, const void* x, const float* t, int B, int H,
     return IGA_E_CUDA;
   if (loss_host && cudaMemcpyAsync(loss_host, n->lossbuf + 2 * B, sizeof(float), cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return IGA_E_CUDA;
-  return cudaStreamSynchronize(st) == cudaSuccess ? IGA_OK : IGA_E_CUDA;
+  return net_check_tc(n, st);
 }
 
 // One Adam step (FP32 master weights) on the batch; loss_host (HOST, may be
@@ -519,7 +552,7 @@ iga_status iga_net_train_step(iga_net* n, const void* x, const float* t, int B, 
   if (loss_host) {
     if (cudaMemcpyAsync(loss_host, n->lossbuf + 2 * B, sizeof(float), cudaMemcpyDeviceToHost, st) != cudaSuccess)
       return IGA_E_CUDA;
-    if (cudaStreamSynchronize(st) != cudaSuccess) return IGA_E_CUDA;
+    return net_check_tc(n, st);
   }
   return cudaGetLastError() == cudaSuccess ? IGA_OK : IGA_E_CUDA;
 }

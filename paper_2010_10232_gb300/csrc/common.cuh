@@ -263,9 +263,15 @@ iga_status op_apply_bands(iga_ctx* ctx, int P, int nx, int ny, const double* K, 
 // op "which": 0 = A (c = -1), 1 = M_beta (c = -sigma)
 enum { OP_A = 0, OP_MB = 1 };
 // epilogues
-enum { EPI_Y = 0, EPI_ZMINUS = 1, EPI_JACOBI = 2 };
+enum { EPI_Y = 0, EPI_ZMINUS = 1, EPI_JACOBI = 2, EPI_JACOBI_OUT64 = 3 /* FP32 sweep, FP64 output (sweep32.cu) */ };
 // mg.cu
 template <typename T> iga_status mg_vcycle(iga_ctx* ctx, const typename cplx<T>::t* r, typename cplx<T>::t* z);
+// FP32 V-cycle with complex128 input and output (conversions fused into the
+// first and last finest-level kernels where the register-stencil sweep runs)
+iga_status mg_vcycle32_c128(iga_ctx* ctx, const double2* r, double2* z);
+// sweep32.cu: one FP32 damped Jacobi sweep of M_beta on `level` writing its
+// result in complex128 (the V-cycle's last post-sweep)
+iga_status sweep32_jacobi_out64(iga_ctx* ctx, int level, const float2* x, double2* y64, const float2* b);
 template <typename T> iga_status mg_restrict(iga_ctx* ctx, int l, const typename cplx<T>::t* f, typename cplx<T>::t* c);
 template <typename T> iga_status mg_prolong_add(iga_ctx* ctx, int l, const typename cplx<T>::t* c, typename cplx<T>::t* f);
 template <typename T> iga_status mg_coarse(iga_ctx* ctx, const typename cplx<T>::t* b, typename cplx<T>::t* x);

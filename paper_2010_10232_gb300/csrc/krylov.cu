@@ -669,6 +669,7 @@ static iga_status precond(iga_ctx* ctx, const double2* r, double2* z) {
     return IGA_OK;
   }
   if (ctx->prm.precision == 0) return mg_vcycle<double>(ctx, r, z);
+  if (!ctx->net) return mg_vcycle32_c128(ctx, r, z);
   launch_convert_d2f(r, ctx->fin, L.n, ctx->st);
   TRY(mg_vcycle<float>(ctx, ctx->fin, ctx->fout));
   if (ctx->net) TRY(net_correct(ctx, ctx->fin, ctx->fout));

@@ -35,6 +35,24 @@ __global__ void k_jacobi0(int nx, int ny, int p, const T* K, const T* M, typenam
   x[i] = omega * cmul(di, b[i]);
 }
 
+// The same first sweep on the finest FP32 level of a constant-k 2D problem,
+// fed by the complex128 right-hand side: b32 = (float) b is stored for the
+// later sweeps and x = omega D^{-1} b32 (the conversion and the sweep in one
+// pass; results equal to converting first).
+__global__ void k_jacobi0_in128(int nx, int ny, int p, const float* K, const float* M, float2 c, const double2* b,
+                                float2* b32, float2* x, float omega) {
+  const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (unsigned)nx * (unsigned)ny) return;
+  const int W = 2 * p + 1;
+  const int iy = (int)(i / (unsigned)nx), ix = (int)(i - (unsigned)iy * nx);
+  const float kx = K[(size_t)ix * W + p], mx = M[(size_t)ix * W + p];
+  const float ky = K[(size_t)iy * W + p], my = M[(size_t)iy * W + p];
+  const float2 d = my * (mkc(kx, 0.f) + mx * c) + mkc(ky * mx, 0.f);
+  const float2 bv = tof(b[i]);
+  b32[i] = bv;
+  x[i] = omega * cmul(cinv(d), bv);
+}
+
 // coarse = P^T fine  (2D: tensor product of the 1D restriction rows)
 // With xc != nullptr the same kernel also performs the coarse level's first
 // damped Jacobi sweep from zero, xc = omega D_c^{-1} c (D_c from the coarse 1D
@@ -660,6 +678,49 @@ iga_status mg_vcycle(iga_ctx* ctx, const typename cplx<T>::t* r, typename cplx<T
     CKL();
   }
   return IGA_OK;
+}
+
+// FP32 V-cycle z ~ M_beta^{-1} r with complex128 r and z.  Where the finest
+// level's FP32 sweeps run on the register-stencil kernel (2D, constant k, one
+// pre-sweep, one V-cycle, per-operation V-cycle) the conversions are folded
+// into the first and last finest-level kernels: the pre-sweep from zero reads
+// r and also stores its FP32 copy, the last post-sweep writes z in
+// complex128.  The operations and their rounding are those of converting, the
+// FP32 V-cycle and converting back; otherwise that is what runs.
+iga_status mg_vcycle32_c128(iga_ctx* ctx, const double2* r, double2* z) {
+  LevelData& L = ctx->lv[0];
+  const int nu2 = ctx->prm.nu_post;
+  const bool fold = ctx->dim == 2 && !ctx->vark && !ctx->vc_fused && ctx->L > 1 && ctx->prm.nu_pre == 1 &&
+                    nu2 >= 1 && ctx->prm.n_vcycles == 1 && ctx->tile[0][1] == 6;
+  if (!fold) {
+    launch_convert_d2f(r, ctx->fin, L.n, ctx->st);
+    TRY(mg_vcycle<float>(ctx, ctx->fin, ctx->fout));
+    launch_convert_f2d(ctx->fout, z, L.n, ctx->st);
+    CKL();
+    return IGA_OK;
+  }
+  float2* b32 = ctx->fin;
+  float2* bufs[2] = {ctx->fout, L.fy};
+  int cur = 0;
+  const double2 cm = make_double2(-ctx->sig.x * ctx->k2const, -ctx->sig.y * ctx->k2const);
+  k_jacobi0_in128<<<cdiv(L.n, 256), 256, 0, ctx->st>>>(L.nx, L.ny, ctx->p, L.Kf, L.Mf, tof(cm), r, b32, bufs[cur],
+                                                       (float)ctx->prm.omega); iga_count_launch();
+  TRY(op_apply<float>(ctx, 0, OP_MB, bufs[cur], L.fr, b32, EPI_ZMINUS, nullptr, 0.0));
+  LevelData& Cl = ctx->lv[1];
+  if (ctx->L > 2) {
+    float2* cstart = start_buffer(ctx) ? Cl.fy : Cl.fx;
+    TRY(mg_restrict_j0<float>(ctx, 0, L.fr, Cl.fb, cstart));
+    TRY(vcycle_level<float>(ctx, 1, Cl.fb, Cl.fx, Cl.fy, true));
+  } else {
+    TRY(mg_restrict<float>(ctx, 0, L.fr, Cl.fb));
+    TRY(vcycle_level<float>(ctx, 1, Cl.fb, Cl.fx, Cl.fy));
+  }
+  TRY(mg_prolong_add<float>(ctx, 0, Cl.fx, bufs[cur]));
+  for (int s = 0; s + 1 < nu2; ++s) {
+    TRY(op_apply<float>(ctx, 0, OP_MB, bufs[cur], bufs[cur ^ 1], nullptr, EPI_JACOBI, b32, ctx->prm.omega));
+    cur ^= 1;
+  }
+  return sweep32_jacobi_out64(ctx, 0, bufs[cur], z, b32);
 }
 
 template iga_status mg_vcycle<double>(iga_ctx*, const double2*, double2*);

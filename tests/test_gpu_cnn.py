@@ -32,8 +32,10 @@ def _to_dev(x, t):
     return xb, tt
 
 
-@pytest.mark.parametrize("B,H,Wd", [(2, 12, 20), (1, 37, 33)])
+@pytest.mark.parametrize("B,H,Wd", [(2, 12, 20), (1, 37, 33), (4, 128, 200)])
 def test_forward_matches_oracle(B, H, Wd):
+    """Forward pass of the tensor-core (tcgen05) convolutions: ragged 8 x 16
+    tiles, and more tiles than resident blocks (the persistent tile loop)."""
     net = Net(seed=7)
     theta = net.get_params()
     params = ocnn.unflatten(theta.astype(np.float64))
@@ -54,12 +56,15 @@ def test_gradient_matches_oracle():
     lo, go = ocnn.loss_and_grad(params, ocnn.bf16_round(x)[..., :3], t.astype(np.float32).astype(np.float64), bf16=True)
     assert abs(loss - lo) <= 1e-3 * abs(lo)
     gref = ocnn.flatten(go)
-    # per layer (weights and biases separately)
+    # per layer (weights and biases separately): FP32 accumulation against the
+    # oracle's FP64 with the same bf16 roundings of the stored tensors
     k = 0
     for ws, bs in ocnn.param_shapes():
         for shp in (ws, bs):
             nn_ = int(np.prod(shp))
-            assert rel_err(g[k:k + nn_], gref[k:k + nn_]) <= 2e-2, shp
+            e = rel_err(g[k:k + nn_], gref[k:k + nn_])
+            print(f"gradient {shp}: rel err {e:.2e}")
+            assert e <= 5e-3, shp
             k += nn_
 
 
@@ -106,3 +111,40 @@ def test_learned_fgmres_converges_and_falls_back():
     x2, it2, *_ = h.solve(torch.from_numpy(f).cuda(), tol=1e-9)
     assert it2 == it0 and rel_err(x2.cpu().numpy(), x0.cpu().numpy()) <= 1e-12
     h.attach(None)
+
+
+@pytest.mark.parametrize("k,n_el", [(80.0, 128), (150.0, 240)])
+def test_trained_network_saves_iterations(k, n_el):
+    """What the shipped network (weights/cslp_correction.npz, trained on
+    residual/error pairs of the FP32 V-cycle at k ~ U[50, 400]) gains: on
+    problems it was not trained on (these meshes and wave numbers, centre
+    source), FGMRES with the learned correction needs at least two
+    iterations fewer than the same FP32-V-cycle FGMRES without it, and
+    reaches the same solution.  Wall times of both are printed."""
+    import os
+    wpath = os.path.join(os.path.dirname(os.path.dirname(__file__)), "paper_2010_10232_gb300", "weights",
+                         "cslp_correction.npz")
+    d = np.load(wpath)
+    net = Net(seed=0)
+    net.set_params(d["params"])
+    pr = W.Problem(dim=2, p=3, n_el=n_el, kfield=W.constant_k(k), sources=[(0.5, 0.5)])
+    h = from_problem(pr, precision=1)
+    f = h.point_source(0.5, 0.5)
+
+    def timed():
+        x, it, hist, tr, st = h.solve(f, tol=1e-7)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        x, it, hist, tr, st = h.solve(f, tol=1e-7)
+        b.record()
+        torch.cuda.synchronize()
+        return x.cpu().numpy(), it, st, a.elapsed_time(b)
+
+    x0, it0, st0, ms0 = timed()
+    h.attach(net, float(d["gamma"]))
+    x1, it1, st1, ms1 = timed()
+    h.attach(None)
+    print(f"k={k} n_el={n_el}: iterations {it0} -> {it1} with the network; ms {ms0:.2f} -> {ms1:.2f}")
+    assert st0 == 0 and st1 == 0
+    assert it1 <= it0 - 2
+    assert rel_err(x1, x0) <= 1e-5

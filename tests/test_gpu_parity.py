@@ -592,3 +592,26 @@ def test_fp32_operator_and_sweep_every_tile(n_el, p, k, tile):
         xo = h.jacobi32(l, bt, xt)
         refj = hier.jacobi(lvl, x.astype(np.complex128), b.astype(np.complex128), 1)
         assert rel_err(to_n(xo).astype(np.complex128), refj) <= 2e-6, l
+
+
+@pytest.mark.parametrize("n_el,p,k", [(256, 3, 150.0), (128, 2, 70.0), (40, 5, 20.0)])
+def test_fp32_vcycle_folded_conversions_are_exact(n_el, p, k):
+    """The FP32 V-cycle with complex128 input and output folds the two
+    conversions into its first and last finest-level kernels when the finest
+    level runs the register-stencil sweep.  The result must be bit-identical
+    to converting, running the FP32 V-cycle and converting back: that path is
+    taken when a network is attached, and a network whose output is NaN is
+    dropped, so it adds nothing."""
+    from paper_2010_10232_gb300.learned import Net
+    pr = W.small_2d(n_el=n_el, p=p, k=k)
+    h = from_problem(pr, precision=1, skip_deflation=1)
+    h.set_tile(0, 1, 6)
+    r = to_t(rvec(h.n, 85))
+    z_fold = to_n(h.vcycle(r))
+    net = Net(seed=1)
+    net.set_params(np.full(net.num_params, np.nan, dtype=np.float32))
+    h.attach(net, 1.0)
+    z_conv = to_n(h.vcycle(r))
+    h.attach(None)
+    assert np.array_equal(z_fold, z_conv)
+    assert rel_err(z_fold, mg.MGHierarchy(2, p, n_el, pr.kfield, 1.0, 0.5).apply(rvec(h.n, 85), 1)) <= 1e-3

@@ -5,6 +5,7 @@
     python -m measure.profile_cases solve   # one bench solve
     python -m measure.profile_cases solve_host  # same, iterations launched from the host
     python -m measure.profile_cases sweep32     # FP32 Jacobi sweep on level 0, 4097^2 dofs
+    python -m measure.profile_cases cnn         # network forward pass, 1281^2 pixels
 
 The solve cases open a profiler range around the solve only (capture them
 with `ncu --profile-from-start off`).
@@ -46,6 +47,19 @@ def main(case: str) -> None:
         torch.cuda.profiler.start()
         for _ in range(2):
             h.jacobi32(0, bs, xs, xo)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+    elif case == "cnn":
+        # one forward pass of the correction network at 1281^2 pixels (the
+        # 1280^2-element grid) inside the profiler range
+        from paper_2010_10232_gb300.learned import Net
+        net = Net(seed=0)
+        x = torch.zeros(1, 1281, 1281, 16, dtype=torch.bfloat16, device="cuda")
+        x[..., :3] = torch.randn(1, 1281, 1281, 3, device="cuda").to(torch.bfloat16)
+        net.forward(x)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        net.forward(x)
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
     elif case in ("solve", "solve_host"):

@@ -157,24 +157,52 @@ def interior_2d(mat, nb: int):
 # ---------------------------------------------------------------- operators
 class Discretization:
     """Interior (Dirichlet-eliminated) S, M, M^{k^2} and A = S - M^{k^2} for one
-    problem description (dim, p, n_el, kfield)."""
+    problem description (dim, p, n_el, kfield).
 
-    def __init__(self, dim: int, p: int, n_el: int, kfield):
+    robin=True (1D only): the Sommerfeld condition u' - i k u = 0 at x = 1 of
+    MP 1-A (Section 2.1): the last basis function stays an unknown and the weak
+    form adds the boundary mass, A = S - M^{k^2} - i k N with N = phi_last(1)^2
+    at x = 1 (Section 2.3, Eq. linearsystem1's N term, read with the sign of the
+    model problem); x = 0 keeps its Dirichlet condition, whose data enter the
+    right-hand side through `dirichlet_lift`.  Pins: tests/test_oracle_robin.py."""
+
+    def __init__(self, dim: int, p: int, n_el: int, kfield, robin: bool = False):
         self.dim, self.p, self.n_el, self.kfield = dim, p, n_el, kfield
+        self.robin = bool(robin)
+        if self.robin and dim != 1:
+            raise ValueError("the Sommerfeld boundary is built for the 1D problem (MP 1-A)")
         self.nb = n_el + p
-        self.n_x = n_el + p - 2
+        self.n_x = n_el + p - 2 + (1 if self.robin else 0)
         if dim == 1:
             k2 = (lambda x: k_of(kfield, x) ** 2)
             K, M, Mk = assemble_1d(n_el, p, k2)
-            self.S = interior_1d(K)
-            self.M = interior_1d(M)
-            self.Mk = interior_1d(Mk)
+            if self.robin:
+                cut = lambda mat: mat[1:, :][:, 1:].tocsr()
+                self.S, self.M, self.Mk = cut(K), cut(M), cut(Mk)
+                # coupling of the unknowns to the Dirichlet function at x = 0
+                self.col0 = np.asarray((K - Mk)[1:, 0].toarray()).reshape(-1).astype(np.complex128)
+                self.k_boundary = float(k_of(kfield, np.array([1.0]))[0])
+                nb = self.S.shape[0]
+                self.N = sp.csr_matrix(([1.0], ([nb - 1], [nb - 1])), shape=(nb, nb))
+            else:
+                self.S = interior_1d(K)
+                self.M = interior_1d(M)
+                self.Mk = interior_1d(Mk)
         else:
             S, M, Mk = assemble_2d(n_el, p, kfield)
             self.S = interior_2d(S, self.nb)
             self.M = interior_2d(M, self.nb)
             self.Mk = interior_2d(Mk, self.nb)
         self.A = (self.S - self.Mk).astype(np.complex128).tocsr()
+        if self.robin:
+            self.A = (self.A - 1j * self.k_boundary * self.N).tocsr()
+
+    def dirichlet_lift(self, g0) -> np.ndarray:
+        """Right-hand side of the inhomogeneous Dirichlet value u(0) = g0 (the
+        first, interpolatory coefficient is g0): f = -g0 A[unknowns, 0]."""
+        if not self.robin:
+            raise ValueError("the lift is defined for the MP 1-A discretisation")
+        return -complex(g0) * self.col0
 
     @property
     def n(self) -> int:
@@ -193,7 +221,10 @@ class Discretization:
         Pins: tests/test_oracle_cslp.py (1D p = 1 closed-form eigenvalues of
         both forms; the paper's Table 2 C_ex counts, met by the mass form only)."""
         if uses_mass:
-            return (self.S - (beta1 - 1j * beta2) * self.Mk).astype(np.complex128).tocsr()
+            out = (self.S - (beta1 - 1j * beta2) * self.Mk).astype(np.complex128).tocsr()
+            if self.robin:      # the boundary term is not shifted
+                out = (out - 1j * self.k_boundary * self.N).tocsr()
+            return out
         if len(self.kfield.lines) != 0:
             raise ValueError("identity-shift CSLP is defined for constant k only")
         k2 = float(self.kfield.values[0]) ** 2
@@ -201,10 +232,11 @@ class Discretization:
         return (self.S - beta1 * self.Mk + 1j * beta2 * k2 * ident).astype(np.complex128).tocsr()
 
 
-def point_source(dim: int, p: int, n_el: int, pos) -> np.ndarray:
-    """Load vector of a unit point source: f_i = Phi_i(pos), interior functions."""
+def point_source(dim: int, p: int, n_el: int, pos, robin: bool = False) -> np.ndarray:
+    """Load vector of a unit point source: f_i = Phi_i(pos), interior functions
+    (with robin, every function but the first)."""
     t = bspline.open_uniform_knots(n_el, p)
-    vx = bspline.basis_all(t, p, [pos[0]])[:, 0][1:-1]
+    vx = bspline.basis_all(t, p, [pos[0]])[:, 0][1:] if robin else bspline.basis_all(t, p, [pos[0]])[:, 0][1:-1]
     if dim == 1:
         return vx.astype(np.complex128)
     vy = bspline.basis_all(t, p, [pos[1]])[:, 0][1:-1]

@@ -70,12 +70,13 @@ def prolongation_1d(n_el_coarse: int, p: int) -> np.ndarray:
     return C
 
 
-def prolongation_interior_1d(n_el_coarse: int, p: int) -> np.ndarray:
+def prolongation_interior_1d(n_el_coarse: int, p: int, robin: bool = False) -> np.ndarray:
     """Interior rows/columns of the knot-insertion matrix.  A coarse spline
     with zero end coefficients refines to a fine spline with zero end
-    coefficients, so the Dirichlet-eliminated transfer is the submatrix."""
+    coefficients, so the Dirichlet-eliminated transfer is the submatrix (with
+    the Sommerfeld end at x = 1, only the first row and column are dropped)."""
     P = prolongation_1d(n_el_coarse, p)
-    return P[1:-1, 1:-1]
+    return P[1:, 1:] if robin else P[1:-1, 1:-1]
 
 
 class Level:
@@ -89,16 +90,16 @@ class MGHierarchy:
     """Rediscretised CSLP levels plus transfers for one problem description."""
 
     def __init__(self, dim, p, n_el, kfield, beta1, beta2, omega=0.6, nu_pre=1, nu_post=1,
-                 fine_disc: Discretization | None = None, uses_mass: bool = True):
+                 fine_disc: Discretization | None = None, uses_mass: bool = True, robin: bool = False):
         self.sizes = level_sizes(n_el)
         self.omega, self.nu_pre, self.nu_post = omega, nu_pre, nu_post
         self.levels = []
         self.P = []
         for li, ne in enumerate(self.sizes):
-            disc = fine_disc if (li == 0 and fine_disc is not None) else Discretization(dim, p, ne, kfield)
+            disc = fine_disc if (li == 0 and fine_disc is not None) else Discretization(dim, p, ne, kfield, robin)
             self.levels.append(Level(disc, beta1, beta2, uses_mass))
             if li > 0:
-                P1 = sp.csr_matrix(prolongation_interior_1d(ne, p))
+                P1 = sp.csr_matrix(prolongation_interior_1d(ne, p, robin))
                 self.P.append(P1 if dim == 1 else sp.kron(P1, P1).tocsr())
         self.coarse_dense = self.levels[-1].Mb.toarray()
 

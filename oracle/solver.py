@@ -42,7 +42,8 @@ class Solver:
     def __init__(self, problem, disc: Discretization | None = None):
         pr = problem
         self.problem = pr
-        self.disc = disc or Discretization(pr.dim, pr.p, pr.n_el, pr.kfield)
+        robin = bool(getattr(pr, "robin", False))
+        self.disc = disc or Discretization(pr.dim, pr.p, pr.n_el, pr.kfield, robin)
         b1, b2 = pr.shift
         uses_mass = getattr(pr, "shift_uses_mass", True)
         kind = getattr(pr, "precond", "mg")
@@ -56,7 +57,7 @@ class Solver:
         if kind == "mg":
             self.mg = MGHierarchy(pr.dim, pr.p, pr.n_el, pr.kfield, b1, b2, omega=pr.omega,
                                   nu_pre=pr.nu_pre, nu_post=pr.nu_post, fine_disc=self.disc,
-                                  uses_mass=uses_mass)
+                                  uses_mass=uses_mass, robin=robin)
         elif kind == "exact":
             self.cslp = self.disc.shifted(b1, b2, uses_mass).tocsc()
             self.cslp_lu = spla.splu(self.cslp)
@@ -79,8 +80,12 @@ class Solver:
         return self.precond(self.defl.P(self.A @ v))
 
     def load(self, k: int = 0) -> np.ndarray:
+        """Right-hand side: the k-th point source; for MP 1-A (robin, no
+        sources) the lift of the Dirichlet value u(0) = 1."""
         pr = self.problem
-        return point_source(pr.dim, pr.p, pr.n_el, pr.sources[k])
+        if self.disc.robin and not pr.sources:
+            return self.disc.dirichlet_lift(1.0)
+        return point_source(pr.dim, pr.p, pr.n_el, pr.sources[k], self.disc.robin)
 
     def solve(self, f, tol=1e-7, maxit=100, variant='def1', flexible=False, x_at=None):
         f = np.asarray(f, dtype=np.complex128)

@@ -3,14 +3,10 @@
 // 3 -> 32 -> 32 -> 32 -> 2, ReLU after the first three, BF16 weights and
 // activations with FP32 accumulation.
 //
-// Convolutions are implicit GEMMs on the tensor cores (mma.sync m16n8k16
-// bf16 -> f32): a warp computes 16 consecutive pixels of one grid row times
-// all output channels, K = 9 taps x C_in.  The input tile (4 rows x 16 pixels
-// plus a one-pixel halo) and all weights are staged in shared memory with
-// padded strides (conflict-free 32-bit fragment loads).  The input gradient is
-// the same kernel with flipped, channel-transposed weights and the ReLU mask
-// of the forward activation; the weight gradient is an FP32 reduction over
-// pixels; Adam keeps FP32 master weights.
+// The convolutions (forward, and the input gradient as the same convolution
+// with flipped, channel-transposed weights and the ReLU mask of the forward
+// activation) run on the tcgen05 tensor cores, conv_tc.cu.  The weight
+// gradient is an FP32 reduction over pixels; Adam keeps FP32 master weights.
 //
 // Layouts: activations NHWC bf16 [B][H][W][C] with C padded to 16 (network
 // input: Re r, Im r, kappa) or 32; network output FP32 [B][H][W][2];
@@ -86,126 +82,6 @@ __global__ void k_init_params(float* p, int n, unsigned long long seed, int off_
   else if (i >= off_w2 && i < off_w2 + n2) s = s2;
   else if (i >= off_w3 && i < off_w3 + n3) s = s3;
   p[i] = (float)(g * s);          // biases start at zero
-}
-
-// ------------------------------------------------------------------ tensor-core convolution
-__device__ __forceinline__ void mma_bf16(float* d, const unsigned* a, const unsigned* b) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-constexpr int CV_TX = 16, CV_TY = 16, CV_RPW = CV_TY / 4;   // 4 warps, CV_RPW pixel rows each (weights reused across rows)
-
-template <int CIN, int COUT>
-constexpr size_t conv_smem() {
-  return sizeof(bf16) * ((size_t)(CV_TY + 2) * (CV_TX + 2) * (CIN + 8) + (size_t)COUT * (9 * CIN + 8));
-}
-
-// EPI 0: + bias, ReLU, bf16 out [px][COUT]; 1: + bias, FP32 out [px][2];
-// 2: times (mask > 0), bf16 out [px][COUT] (input gradient through ReLU)
-template <int CIN, int COUT, int EPI>
-__global__ void __launch_bounds__(128) k_conv3x3(const bf16* __restrict__ X, const bf16* __restrict__ Wt,
-                                                 const float* __restrict__ bias, const bf16* __restrict__ mask,
-                                                 void* Yout, int H, int W) {
-  extern __shared__ __align__(16) unsigned char sm_raw[];
-  constexpr int XS = CIN + 8, WS = 9 * CIN + 8, HX = CV_TX + 2;
-  bf16* Xs = (bf16*)sm_raw;                                  // [CV_TY+2][HX][XS]
-  bf16* Ws = Xs + (CV_TY + 2) * HX * XS;                     // [COUT][WS]
-  const int b = blockIdx.z;
-  const int x0 = blockIdx.x * CV_TX, y0 = blockIdx.y * CV_TY;
-  const size_t img = (size_t)b * H * W;
-  // stage the input tile (with zero halo) as 32-bit pairs
-  for (int idx = threadIdx.x; idx < (CV_TY + 2) * HX * (CIN / 2); idx += 128) {
-    int c2 = idx % (CIN / 2), pix = idx / (CIN / 2);
-    int hx = pix % HX, hy = pix / HX;
-    int gy = y0 - 1 + hy, gx = x0 - 1 + hx;
-    unsigned v = 0u;
-    if (gy >= 0 && gy < H && gx >= 0 && gx < W) v = ((const unsigned*)(X + (img + (size_t)gy * W + gx) * CIN))[c2];
-    ((unsigned*)(Xs + (hy * HX + hx) * XS))[c2] = v;
-  }
-  for (int idx = threadIdx.x; idx < COUT * 9 * (CIN / 2); idx += 128) {
-    int c2 = idx % (9 * CIN / 2), co = idx / (9 * CIN / 2);
-    ((unsigned*)(Ws + co * WS))[c2] = ((const unsigned*)(Wt + (size_t)co * 9 * CIN))[c2];
-  }
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int g = lane >> 2, tig = lane & 3;
-  constexpr int NT = COUT / 8;
-  float acc[CV_RPW][NT][4];
-#pragma unroll
-  for (int r = 0; r < CV_RPW; ++r)
-#pragma unroll
-    for (int nt = 0; nt < NT; ++nt) acc[r][nt][0] = acc[r][nt][1] = acc[r][nt][2] = acc[r][nt][3] = 0.f;
-#pragma unroll
-  for (int t = 0; t < 9; ++t) {
-    const int dy = t / 3, dx = t % 3;           // halo offsets 0..2
-#pragma unroll
-    for (int kc = 0; kc < CIN / 16; ++kc) {
-      unsigned bb[NT][2];                       // weight fragments, reused by every row of the warp
-#pragma unroll
-      for (int nt = 0; nt < NT; ++nt) {
-        const bf16* wp = Ws + (nt * 8 + g) * WS + t * CIN + kc * 16 + 2 * tig;
-        bb[nt][0] = *(const unsigned*)wp;
-        bb[nt][1] = *(const unsigned*)(wp + 8);
-      }
-#pragma unroll
-      for (int r = 0; r < CV_RPW; ++r) {
-        const int row = warp * CV_RPW + r;
-        const bf16* r0 = Xs + ((row + dy) * HX + (g + dx)) * XS + kc * 16 + 2 * tig;
-        const bf16* r1 = r0 + 8 * XS;           // pixel g + 8
-        unsigned a[4];
-        a[0] = *(const unsigned*)r0;
-        a[1] = *(const unsigned*)r1;
-        a[2] = *(const unsigned*)(r0 + 8);
-        a[3] = *(const unsigned*)(r1 + 8);
-#pragma unroll
-        for (int nt = 0; nt < NT; ++nt) mma_bf16(acc[r][nt], a, bb[nt]);
-      }
-    }
-  }
-#pragma unroll
-  for (int r = 0; r < CV_RPW; ++r) {
-  const int gy = y0 + warp * CV_RPW + r;
-  if (gy >= H) break;
-#pragma unroll
-  for (int nt = 0; nt < NT; ++nt) {
-    const int co = nt * 8 + 2 * tig;
-#pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      const int gx = x0 + g + 8 * half;
-      if (gx >= W) continue;
-      const size_t p = img + (size_t)gy * W + gx;
-      float v0 = acc[r][nt][2 * half], v1 = acc[r][nt][2 * half + 1];
-      if (EPI == 0) {
-        v0 = fmaxf(v0 + bias[co], 0.f);
-        v1 = fmaxf(v1 + bias[co + 1], 0.f);
-        *(__nv_bfloat162*)((bf16*)Yout + p * COUT + co) = __floats2bfloat162_rn(v0, v1);
-      } else if (EPI == 1) {
-        if (co < 2) *(float2*)((float*)Yout + p * 2 + co) = make_float2(v0 + bias[co], v1 + bias[co + 1]);
-      } else {
-        __nv_bfloat162 mk = *(const __nv_bfloat162*)(mask + p * COUT + co);
-        v0 = __bfloat162float(mk.x) > 0.f ? v0 : 0.f;
-        v1 = __bfloat162float(mk.y) > 0.f ? v1 : 0.f;
-        *(__nv_bfloat162*)((bf16*)Yout + p * COUT + co) = __floats2bfloat162_rn(v0, v1);
-      }
-    }
-  }
-  }
-}
-
-template <int CIN, int COUT, int EPI>
-static void launch_conv(const bf16* X, const bf16* Wt, const float* bias, const bf16* mask, void* Y, int B, int H,
-                        int W, cudaStream_t st) {
-  constexpr size_t sm = conv_smem<CIN, COUT>();
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_conv3x3<CIN, COUT, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    attr = true;
-  }
-  dim3 grid(cdiv(W, CV_TX), cdiv(H, CV_TY), B);
-  k_conv3x3<CIN, COUT, EPI><<<grid, 128, sm, st>>>(X, Wt, bias, mask, Y, H, W); iga_count_launch();
 }
 
 // ------------------------------------------------------------------ weight gradient (FP32)

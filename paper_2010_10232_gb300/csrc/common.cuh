@@ -98,6 +98,10 @@ struct LevelData {
   double* K = nullptr;           // band [nx][2p+1]
   double* M = nullptr;
   float* Kf = nullptr;
+  // FP32 interior stencil of K and M (uniform knots: every band row at least
+  // 2p from either end), copied to the host at setup (kernel parameters)
+  float sK[2 * IGA_MAXP + 1] = {}, sM[2 * IGA_MAXP + 1] = {};
+  bool has_stencil = false;
   float* Mf = nullptr;
   // transfer to the next coarser level (absent on the coarsest)
   int wP = 0, wR = 0;

@@ -495,8 +495,8 @@ static void launch_kron_pair(const OpArgs<double>& a, cudaStream_t st, int tile)
   else launch_kron_pair_tile<P, EPI, 8, 4, 128>(a, st);
 }
 
-void sweep32_launch(int p, int epi, int nx, int ny, const float* K, const float* M, float2 cm, const float2* x,
-                    float2* y, const float2* z, float omega, int num_sms, cudaStream_t st);
+void sweep32_launch(const LevelData& L, int p, int epi, const float2* x, float2* y, const float2* z, float2 cm,
+                    float omega, cudaStream_t st);
 
 template <int P, typename T, int EPI>
 static void launch_op(iga_ctx* ctx, const OpArgs<T>& a, int level) {
@@ -513,7 +513,7 @@ static void launch_op(iga_ctx* ctx, const OpArgs<T>& a, int level) {
     }
     if constexpr (sizeof(T) == 4) {
       if (tile == 6) {
-        sweep32_launch(P, EPI, a.nx, a.ny, a.K, a.M, a.c, a.x, a.y, a.z, a.omega, ctx->num_sms, st);
+        sweep32_launch(ctx->lv[level], P, EPI, a.x, a.y, a.z, a.c, a.omega, st);
         return;
       }
     }

@@ -206,6 +206,13 @@ iga_status setup_levels(iga_ctx* ctx) {
     CKL();
     TRY(to_float(ctx, L.K, &L.Kf, (size_t)L.nx * W));
     TRY(to_float(ctx, L.M, &L.Mf, (size_t)L.nx * W));
+    if (L.nx > 4 * p + 1) {   // the interior stencil (every row >= 2p from the ends), FP32, on the host
+      const size_t ci = (size_t)(L.nx / 2) * W;
+      CK(cudaMemcpyAsync(L.sK, L.Kf + ci, sizeof(float) * W, cudaMemcpyDeviceToHost, ctx->st));
+      CK(cudaMemcpyAsync(L.sM, L.Mf + ci, sizeof(float) * W, cudaMemcpyDeviceToHost, ctx->st));
+      CK(cudaStreamSynchronize(ctx->st));
+      L.has_stencil = true;
+    }
     TRY(to_float(ctx, L.B, &L.Bf, (size_t)L.n_el * Q * Q));
     TRY(to_float(ctx, L.wq, &L.wqf, (size_t)L.n_el * Q));
   }

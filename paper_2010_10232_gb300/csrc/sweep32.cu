@@ -70,6 +70,13 @@ template <int P> struct SwGeom {
 
 }  // namespace
 
+// The level's interior stencil (band row at least 2p from either end), passed
+// by value so that it comes from the constant bank, not from global memory.
+struct SwStencil {
+  float k[2 * IGA_MAXP + 1], m[2 * IGA_MAXP + 1];
+  int valid;       // the level has interior rows (n_x > 4p + 1)
+};
+
 // First pass for 8 output rows of one x-tile column (sliding window down the
 // column): EDGE takes the (M, K) band pair of every output row from the tile
 // table cy, otherwise the interior stencil creg.
@@ -149,7 +156,7 @@ __global__ void __launch_bounds__(SW_NT, 3) k_sweep32(int nx, int ny, const floa
                                                       const float* __restrict__ M, float2 cm,
                                                       const float2* __restrict__ x, float2* __restrict__ y,
                                                       const float2* __restrict__ z, float omega,
-                                                      double2* __restrict__ y64) {
+                                                      double2* __restrict__ y64, const SwStencil stn) {
   using G = SwGeom<P>;
   constexpr int W = G::W, TX = G::TX, SY = G::SY, RSU = G::RSU, TY = SW_TY, SX = SW_SX, NE = G::NE;
   constexpr int RSTEP = SW_NT / 64;                   // tile rows loaded per round (one thread per column)
@@ -165,7 +172,7 @@ __global__ void __launch_bounds__(SW_NT, 3) k_sweep32(int nx, int ny, const floa
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   // interior stencil rows: at least 2p from either end (uniform B-splines only)
-  const bool inner_ok = nx > 4 * P + 1 && ny > 4 * P + 1;
+  const bool inner_ok = stn.valid && nx > 4 * P + 1 && ny > 4 * P + 1;
   const bool yedge = !inner_ok || y0 < 2 * P || y0 + TY - 1 > ny - 1 - 2 * P;
   const bool xedge = !inner_ok || x0 < 2 * P || x0 + TX - 1 > nx - 1 - 2 * P;
 
@@ -235,9 +242,8 @@ __global__ void __launch_bounds__(SW_NT, 3) k_sweep32(int nx, int ny, const floa
   {
     u64 creg[W];
     if (!yedge) {
-      const int ci = ny >> 1;
 #pragma unroll
-      for (int d = 0; d < W; ++d) creg[d] = pk2(M[(size_t)ci * W + d], K[(size_t)ci * W + d]);
+      for (int d = 0; d < W; ++d) creg[d] = pk2(stn.m[d], stn.k[d]);
       sweep_ypass<P, false>(xs, uw, cy, creg, cm, tid);
     } else {
       sweep_ypass<P, true>(xs, uw, cy, creg, cm, tid);
@@ -251,9 +257,8 @@ __global__ void __launch_bounds__(SW_NT, 3) k_sweep32(int nx, int ny, const floa
   {
     u64 creg[W];
     if (!xedge) {
-      const int ci = nx >> 1;
 #pragma unroll
-      for (int d = 0; d < W; ++d) creg[d] = pk2(K[(size_t)ci * W + d], M[(size_t)ci * W + d]);
+      for (int d = 0; d < W; ++d) creg[d] = pk2(stn.k[d], stn.m[d]);
       sweep_xpass<P, false>(uw, cx, creg, tid, res);
     } else {
       sweep_xpass<P, true>(uw, cx, creg, tid, res);
@@ -270,8 +275,7 @@ __global__ void __launch_bounds__(SW_NT, 3) k_sweep32(int nx, int ny, const floa
   // buffers), only the store is predicated
   float2 dint = make_float2(0.f, 0.f);
   if (JAC && !(yedge || xedge)) {
-    const int ci = nx >> 1;
-    const float kd = K[(size_t)ci * W + P], md = M[(size_t)ci * W + P];
+    const float kd = stn.k[P], md = stn.m[P];
     const float2 diag = md * (make_float2(kd, 0.f) + md * cm) + make_float2(kd * md, 0.f);
     dint = cinv(diag);
   }
@@ -315,7 +319,7 @@ __global__ void __launch_bounds__(SW_NT, 3) k_sweep32(int nx, int ny, const floa
 
 template <int P, int EPI>
 static void launch_sweep(int nx, int ny, const float* K, const float* M, float2 cm, const float2* x, float2* y,
-                         const float2* z, float omega, double2* y64, cudaStream_t st) {
+                         const float2* z, float omega, double2* y64, const SwStencil& stn, cudaStream_t st) {
   using G = SwGeom<P>;
   static bool attr = false;
   if (!attr) {
@@ -325,42 +329,51 @@ static void launch_sweep(int nx, int ny, const float* K, const float* M, float2 
     attr = true;
   }
   dim3 grid(cdiv(nx, G::TX), cdiv(ny, SW_TY));
-  k_sweep32<P, EPI><<<grid, SW_NT, G::smem, st>>>(nx, ny, K, M, cm, x, y, z, omega, y64);
+  k_sweep32<P, EPI><<<grid, SW_NT, G::smem, st>>>(nx, ny, K, M, cm, x, y, z, omega, y64, stn);
   iga_count_launch();
 }
 
 template <int P>
 static void launch_sweep_epi(int epi, int nx, int ny, const float* K, const float* M, float2 cm, const float2* x,
-                             float2* y, const float2* z, float omega, double2* y64, cudaStream_t st) {
-  if (epi == EPI_Y) launch_sweep<P, EPI_Y>(nx, ny, K, M, cm, x, y, z, omega, y64, st);
-  else if (epi == EPI_ZMINUS) launch_sweep<P, EPI_ZMINUS>(nx, ny, K, M, cm, x, y, z, omega, y64, st);
-  else if (epi == EPI_JACOBI) launch_sweep<P, EPI_JACOBI>(nx, ny, K, M, cm, x, y, z, omega, y64, st);
-  else launch_sweep<P, EPI_JACOBI_OUT64>(nx, ny, K, M, cm, x, y, z, omega, y64, st);
+                             float2* y, const float2* z, float omega, double2* y64, const SwStencil& stn, cudaStream_t st) {
+  if (epi == EPI_Y) launch_sweep<P, EPI_Y>(nx, ny, K, M, cm, x, y, z, omega, y64, stn, st);
+  else if (epi == EPI_ZMINUS) launch_sweep<P, EPI_ZMINUS>(nx, ny, K, M, cm, x, y, z, omega, y64, stn, st);
+  else if (epi == EPI_JACOBI) launch_sweep<P, EPI_JACOBI>(nx, ny, K, M, cm, x, y, z, omega, y64, stn, st);
+  else launch_sweep<P, EPI_JACOBI_OUT64>(nx, ny, K, M, cm, x, y, z, omega, y64, stn, st);
 }
 
 static void sweep_dispatch(int p, int epi, int nx, int ny, const float* K, const float* M, float2 cm,
-                           const float2* x, float2* y, const float2* z, float omega, double2* y64, cudaStream_t st) {
+                           const float2* x, float2* y, const float2* z, float omega, double2* y64, const SwStencil& stn, cudaStream_t st) {
   switch (p) {
-    case 1: launch_sweep_epi<1>(epi, nx, ny, K, M, cm, x, y, z, omega, y64, st); break;
-    case 2: launch_sweep_epi<2>(epi, nx, ny, K, M, cm, x, y, z, omega, y64, st); break;
-    case 3: launch_sweep_epi<3>(epi, nx, ny, K, M, cm, x, y, z, omega, y64, st); break;
-    case 4: launch_sweep_epi<4>(epi, nx, ny, K, M, cm, x, y, z, omega, y64, st); break;
-    default: launch_sweep_epi<5>(epi, nx, ny, K, M, cm, x, y, z, omega, y64, st); break;
+    case 1: launch_sweep_epi<1>(epi, nx, ny, K, M, cm, x, y, z, omega, y64, stn, st); break;
+    case 2: launch_sweep_epi<2>(epi, nx, ny, K, M, cm, x, y, z, omega, y64, stn, st); break;
+    case 3: launch_sweep_epi<3>(epi, nx, ny, K, M, cm, x, y, z, omega, y64, stn, st); break;
+    case 4: launch_sweep_epi<4>(epi, nx, ny, K, M, cm, x, y, z, omega, y64, stn, st); break;
+    default: launch_sweep_epi<5>(epi, nx, ny, K, M, cm, x, y, z, omega, y64, stn, st); break;
   }
 }
 
+static SwStencil level_stencil(const LevelData& L, int p) {
+  SwStencil s{};
+  for (int d = 0; d < 2 * p + 1; ++d) {
+    s.k[d] = L.sK[d];
+    s.m[d] = L.sM[d];
+  }
+  s.valid = L.has_stencil ? 1 : 0;
+  return s;
+}
+
 // operator.cu: tile code 6 of the FP32 constant-k operator
-void sweep32_launch(int p, int epi, int nx, int ny, const float* K, const float* M, float2 cm, const float2* x,
-                    float2* y, const float2* z, float omega, int num_sms, cudaStream_t st) {
-  (void)num_sms;
-  sweep_dispatch(p, epi, nx, ny, K, M, cm, x, y, z, omega, nullptr, st);
+void sweep32_launch(const LevelData& L, int p, int epi, const float2* x, float2* y, const float2* z, float2 cm,
+                    float omega, cudaStream_t st) {
+  sweep_dispatch(p, epi, L.nx, L.ny, L.Kf, L.Mf, cm, x, y, z, omega, nullptr, level_stencil(L, p), st);
 }
 
 iga_status sweep32_jacobi_out64(iga_ctx* ctx, int level, const float2* x, double2* y64, const float2* b) {
   const LevelData& L = ctx->lv[level];
   double2 c = make_double2(-ctx->sig.x * ctx->k2const, -ctx->sig.y * ctx->k2const);   // M_beta mass coefficient
   sweep_dispatch(ctx->p, EPI_JACOBI_OUT64, L.nx, L.ny, L.Kf, L.Mf, tof(c), x, nullptr, b, (float)ctx->prm.omega, y64,
-                 ctx->st);
+                 level_stencil(L, ctx->p), ctx->st);
   CKL();
   return IGA_OK;
 }

@@ -79,6 +79,14 @@ class Problem:
     precond: str = "mg"               # "mg": n_vcycles V-cycles (0 = no CSLP); "exact": CSLP inverted exactly
     deflation: bool = True            # ADP deflation on (D...) or off (C_ex alone)
     shift_uses_mass: bool = True      # CSLP shift on the mass matrix (True) or the identity (False)
+    robin: bool = False               # 1D: Sommerfeld u' - i k u = 0 at x = 1 (MP 1-A); u(0) = 1 lifted
+
+
+def mp1a(k: float, p: int, n_el: int) -> "Problem":
+    """MP 1-A (Section 2.1): -u'' - k^2 u = 0 on [0, 1], u(0) = 1, u'(1) - i k u(1)
+    = 0; exact solution exp(i k x).  The right-hand side is the lift of u(0)."""
+    return Problem(dim=1, p=p, n_el=n_el, kfield=constant_k(k), robin=True, sources=[],
+                   name=f"mp1a_k{k:g}_p{p}_nel{n_el}")
 
     @property
     def n_x(self) -> int:

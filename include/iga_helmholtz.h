@@ -100,6 +100,13 @@ typedef struct {
                               3's deflated system); 0: no deflation (GMRES on M~^{-1} A,
                               C_ex / C_MG alone); 2: the literal ordering P^T M~^{-1} A u =
                               P^T M~^{-1} f, iterate used as u (precision 0, flexible 0) */
+  int robin;               /* 1D only.  0 (default): homogeneous Dirichlet at both ends;
+                              1: MP 1-A (Section 2.1): Sommerfeld u' - i k u = 0 at x = 1
+                              (the last basis function is an unknown, A = S - k^2 M -
+                              i k N with the boundary mass N of Section 2.3; the CSLP
+                              levels carry the same boundary term), Dirichlet at x = 0
+                              with its value entered by iga_load_dirichlet.  Needs
+                              precond 0.                                                  */
 } iga_params;
 
 typedef struct iga_ctx iga_ctx;
@@ -192,6 +199,12 @@ iga_status iga_zt(iga_ctx* ctx, const iga_c128* x, iga_c128* c);
 iga_status iga_z(iga_ctx* ctx, const iga_c128* c, iga_c128* x);
 iga_status iga_esolve(iga_ctx* ctx, const iga_c128* t, iga_c128* s);
 iga_status iga_deflate(iga_ctx* ctx, const iga_c128* x, iga_c128* y);
+
+/* Right-hand side of the inhomogeneous Dirichlet value u(0) = g (context
+   with robin = 1; Section 2.1, MP 1-A): f = -g A[unknowns, first basis
+   function], non-zero in the first p entries (the first, interpolatory
+   coefficient of the solution is g).  f: n complex128, overwritten. */
+iga_status iga_load_dirichlet(iga_ctx* ctx, double g_re, double g_im, iga_c128* f);
 
 /* Unit load vector of a point source at (x0, y0): f_i = Phi_i(x0, y0)
    (y0 ignored in 1D).  f: n complex128. */

@@ -40,6 +40,7 @@ class IgaParams(C.Structure):
         ("stream", C.c_void_p),
         ("precond", C.c_int),
         ("deflation", C.c_int),
+        ("robin", C.c_int),
     ]
 
 
@@ -93,6 +94,7 @@ _SIG = {
     "iga_esolve": (C.c_int, [_VP, _VP, _VP]),
     "iga_deflate": (C.c_int, [_VP, _VP, _VP]),
     "iga_load_point_source": (C.c_int, [_VP, C.c_double, C.c_double, _VP]),
+    "iga_load_dirichlet": (C.c_int, [_VP, C.c_double, C.c_double, _VP]),
     "iga_mgs": (C.c_int, [_VP, _VP, C.c_size_t, C.c_int, _VP, _VP]),
     "iga_solve": (C.c_int, [_VP, _VP, _VP, C.c_double, C.c_int, C.POINTER(C.c_int), _VP, C.POINTER(C.c_double)]),
     "iga_solve_host": (C.c_int, [_VP, _VP, _VP, C.c_double, C.c_int, C.POINTER(C.c_int), _VP,

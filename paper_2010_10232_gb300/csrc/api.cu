@@ -38,6 +38,7 @@ void iga_default_params(iga_params* prm) {
   d.stream = nullptr;
   d.precond = 0;
   d.deflation = 1;
+  d.robin = 0;
   *prm = d;
 }
 
@@ -90,6 +91,8 @@ iga_status iga_setup(const iga_params* prm, iga_ctx** out) {
   if (P.precond == 0 && P.n_vcycles < 1 && P.deflation == 0) return IGA_E_INVALID;   // nothing left to solve with
   if (P.deflation == 2 && (P.precision != 0 || P.flexible != 0)) return IGA_E_INVALID;
   if (P.precond == 1 && P.n_lines > 0) return IGA_E_UNSUPPORTED;
+  if (P.robin < 0 || P.robin > 1) return IGA_E_INVALID;
+  if (P.robin && (P.dim != 1 || P.precond == 1)) return IGA_E_UNSUPPORTED;
   if (P.precision < 0 || P.precision > 1) return IGA_E_INVALID;
   if (P.arnoldi < 0 || P.arnoldi > 1) return IGA_E_INVALID;
   if (P.fused_vcycle < 0 || P.fused_vcycle > 1) return IGA_E_INVALID;
@@ -108,6 +111,7 @@ iga_status iga_setup(const iga_params* prm, iga_ctx** out) {
     for (int c = 0; c < 3; ++c) ctx->kf.lines[l][c] = l < P.n_lines ? P.lines[l][c] : 0.0;
   for (int l = 0; l <= IGA_MAX_LINES; ++l) ctx->kf.k2[l] = l <= P.n_lines ? P.k_values[l] * P.k_values[l] : 0.0;
   ctx->k2const = P.k_values[0] * P.k_values[0];
+  ctx->robin_k = P.robin ? P.k_values[0] : 0.0;     // 1D: k at x = 1
   ctx->sig = make_double2(P.beta1, -P.beta2);
   ctx->use_graph = P.host_loop == 0;
   ctx->arnoldi_cgs = P.arnoldi == 1;
@@ -121,6 +125,7 @@ iga_status iga_setup(const iga_params* prm, iga_ctx** out) {
       for (int l = 0; l < ctx->L && s == IGA_OK; ++l) s = setup_vark_diag(ctx, l);
     if (s != IGA_OK) break;
     if ((s = setup_const_dinv(ctx)) != IGA_OK) break;
+    if ((s = setup_robin_dinv(ctx)) != IGA_OK) break;
     if ((s = setup_tiled_transfers(ctx)) != IGA_OK) break;
     if ((s = alloc_level_vectors(ctx)) != IGA_OK) break;
     if ((s = autotune_tiles(ctx)) != IGA_OK) break;
@@ -139,6 +144,7 @@ iga_status iga_setup(const iga_params* prm, iga_ctx** out) {
       break;
     }
     if (!P.skip_deflation && P.deflation != 0 && (s = setup_deflation(ctx)) != IGA_OK) break;
+    if (!P.skip_deflation && P.deflation != 0 && P.robin && (s = setup_robin_deflation(ctx)) != IGA_OK) break;
     if (P.precond == 1 && (s = setup_exact_cslp(ctx)) != IGA_OK) break;
     cudaError_t e = cudaStreamSynchronize(ctx->st);
     if (e != cudaSuccess) { s = set_err(ctx, IGA_E_CUDA, "setup: %s", cudaGetErrorString(e)); break; }
@@ -320,6 +326,35 @@ iga_status iga_deflate(iga_ctx* ctx, const iga_c128* x, iga_c128* y) {
 
 __global__ void k_point_source(const double* t, int n_el, int p, int nx, int dim, double x0, double y0,
                                double2* f);
+
+// f_i = -g A[i][first function] for the unknowns i = 0 .. p-1 (full index i + 1;
+// only element 0 couples them to function 0): stiffness and k^2-mass entries
+// from the element-0 Gauss tables.
+__global__ void k_dirichlet_lift(int p, int nx, const double* wq, const double* B, const double* D, double k2,
+                                 double2 g, double2* f) {
+  const int i = threadIdx.x;
+  if (i >= p || i >= nx) return;
+  const int a = i + 1, Q = p + 1;
+  double ks = 0.0, ms = 0.0;
+  for (int q = 0; q < Q; ++q) {
+    const size_t o = (size_t)q * (p + 1);
+    ks += wq[q] * D[o + a] * D[o];
+    ms += wq[q] * B[o + a] * B[o];
+  }
+  const double v = ks - k2 * ms;
+  f[i] = make_double2(-g.x * v, -g.y * v);
+}
+
+iga_status iga_load_dirichlet(iga_ctx* ctx, double g_re, double g_im, iga_c128* f) {
+  CHECK_CTX(); CHECK_PTR(f);
+  if (!ctx->prm.robin) return set_err(ctx, IGA_E_INVALID, "iga_load_dirichlet needs a context with robin = 1");
+  const LevelData& L = ctx->lv[0];
+  CK(cudaMemsetAsync(f, 0, sizeof(double2) * L.n, ctx->st));
+  k_dirichlet_lift<<<1, 32, 0, ctx->st>>>(ctx->p, L.nx, L.wq, L.B, L.D, ctx->k2const, make_double2(g_re, g_im),
+                                          (double2*)f); iga_count_launch();
+  CKL();
+  return IGA_OK;
+}
 
 iga_status iga_load_point_source(iga_ctx* ctx, double x0, double y0, iga_c128* f) {
   CHECK_CTX(); CHECK_PTR(f);

@@ -132,6 +132,14 @@ struct iga_ctx {
   bool vark = false;
   KFieldDev kf{};
   double k2const = 0.0;              // k^2 when constant
+  double robin_k = 0.0;              // 1D Sommerfeld end at x = 1: the -i k N coefficient (0: none)
+  // rank-one correction of the deflation solve for the Sommerfeld term:
+  // E = E0 - i k u u^T, u = Z^T e_last; E^{-1} t = E0^{-1} t + g (u^T E0^{-1} t) E0^{-1} u
+  double2 sm_gamma{};                // i k / (1 - i k u^T E0^{-1} u)
+  double2* sm_w = nullptr;           // E0^{-1} u (m)
+  double2* sm_dot = nullptr;         // scratch for u^T s
+  int sm_j[2] = {-1, -1};            // the (at most two) non-zero entries of u
+  double sm_u[2] = {0.0, 0.0};
   double2 sig{};                     // beta1 - i beta2
   LevelData lv[IGA_MAX_LEVELS];
   int tile[IGA_MAX_LEVELS][2];       // operator tile shape per level and precision (-1: heuristic)
@@ -296,6 +304,8 @@ iga_status defl_q(iga_ctx* ctx, const double2* x, double2* y);            // y =
 iga_status defl_apply_T(iga_ctx* ctx, const double2* x, double2* y, double2* tmp1, double2* tmp2);
 // exact CSLP (constant k): z = M_beta^{-1} r on the finest level
 iga_status setup_exact_cslp(iga_ctx* ctx);
+iga_status setup_robin_deflation(iga_ctx* ctx);
+iga_status setup_robin_dinv(iga_ctx* ctx);         // mg.cu
 iga_status cslp_exact_solve(iga_ctx* ctx, const double2* r, double2* z);
 // ecoarse.cu (variable k)
 iga_status setup_block_E(iga_ctx* ctx);

@@ -619,14 +619,13 @@ static iga_status fdm_solve32(iga_ctx* ctx, const FdmData& F, const double2* t, 
   return IGA_OK;
 }
 
-// s = E^{-1} t.  Constant k: fast diagonalisation with FP32 transforms and
-// FP64 eigenvalue denominators, followed by fdmE.refine steps of iterative
-// refinement s += FDM(t - E s) with the residual in FP64 (E applied by the
-// banded tensor-product kernel on the coarse grid).  Two steps bring the
-// solve to ~1e-11 of a sparse LU even where lambda_i + lambda_j ~ k^2 nearly
-// cancels.  Variable k: block LU.
-iga_status defl_esolve(iga_ctx* ctx, const double2* t, double2* s, const float2* tf) {
-  if (ctx->vark) return block_E_solve(ctx, t, s);
+// s = E0^{-1} t for the Kronecker-structured part E0 = Z^T (S - k^2 M) Z:
+// fast diagonalisation with FP32 transforms and FP64 eigenvalue denominators,
+// followed by fdmE.refine steps of iterative refinement s += FDM(t - E0 s) with
+// the residual in FP64 (E0 applied by the banded tensor-product kernel on the
+// coarse grid).  Two steps bring the solve to ~1e-11 of a sparse LU even where
+// lambda_i + lambda_j ~ k^2 nearly cancels.
+static iga_status e0_solve(iga_ctx* ctx, const double2* t, double2* s, const float2* tf) {
   TRY(fdm_solve32(ctx, ctx->fdmE, t, s, false, tf));
   const int bw = (ctx->p + 4) / 2;
   const int my = ctx->dim == 2 ? ctx->mx : 1;
@@ -636,6 +635,72 @@ iga_status defl_esolve(iga_ctx* ctx, const double2* t, double2* s, const float2*
     TRY(fdm_solve32(ctx, ctx->fdmE, ctx->ce1, s, true, ctx->dim == 2 ? ctx->cef : nullptr));   // s += FDM(r)
   }
   CKL();
+  return IGA_OK;
+}
+
+// u^T s over the (at most two) entries of u = Z^T e_last
+__global__ void k_sm_dot(const double2* s, int j0, double u0, int j1, double u1, double2* dot) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double2 d = make_double2(0.0, 0.0);
+  if (j0 >= 0) d = d + u0 * s[j0];
+  if (j1 >= 0) d = d + u1 * s[j1];
+  *dot = d;
+}
+// s += g (u^T s) w
+__global__ void k_sm_axpy(double2* s, int m, double2 g, const double2* dot, const double2* w) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  const double2 c = cmul(g, *dot);
+  s[i] = s[i] + cmul(c, w[i]);
+}
+
+// s = E^{-1} t.  Constant k: e0_solve, and with a Sommerfeld end the
+// rank-one correction of the boundary term (Sherman-Morrison):
+// E = E0 - i k u u^T  =>  E^{-1} t = s0 + g (u^T s0) E0^{-1} u,  s0 = E0^{-1} t,
+// g = i k / (1 - i k u^T E0^{-1} u).  Variable k: block LU.
+iga_status defl_esolve(iga_ctx* ctx, const double2* t, double2* s, const float2* tf) {
+  if (ctx->vark) return block_E_solve(ctx, t, s);
+  TRY(e0_solve(ctx, t, s, tf));
+  if (ctx->sm_w) {
+    const int m = (int)ctx->m;
+    k_sm_dot<<<1, 32, 0, ctx->st>>>(s, ctx->sm_j[0], ctx->sm_u[0], ctx->sm_j[1], ctx->sm_u[1], ctx->sm_dot); iga_count_launch();
+    k_sm_axpy<<<cdiv(m, 256), 256, 0, ctx->st>>>(s, m, ctx->sm_gamma, ctx->sm_dot, ctx->sm_w); iga_count_launch();
+    CKL();
+  }
+  return IGA_OK;
+}
+
+// Setup of the rank-one correction (1D, Sommerfeld end at x = 1): u = Z^T e_last
+// is the last row of Z (coarse m_x gets (6 - eps)/8 and m_x - 1 gets 1/8 when
+// n_x is even; m_x gets 1/2 when n_x is odd; 1-based), w = E0^{-1} u.
+iga_status setup_robin_deflation(iga_ctx* ctx) {
+  if (ctx->robin_k == 0.0 || ctx->vark || ctx->dim != 1) return IGA_OK;
+  const int nx = ctx->lv[0].nx, m = (int)ctx->m;
+  const double eps = ctx->prm.eps;
+  if (nx % 2 == 0) {
+    ctx->sm_j[0] = m - 1; ctx->sm_u[0] = (6.0 - eps) / 8.0;
+    if (m >= 2) { ctx->sm_j[1] = m - 2; ctx->sm_u[1] = 1.0 / 8.0; }
+  } else {
+    ctx->sm_j[0] = m - 1; ctx->sm_u[0] = 0.5;
+  }
+  std::vector<double2> hu((size_t)m, make_double2(0.0, 0.0));
+  for (int q = 0; q < 2; ++q)
+    if (ctx->sm_j[q] >= 0) hu[ctx->sm_j[q]] = make_double2(ctx->sm_u[q], 0.0);
+  double2* u = dalloc<double2>(ctx, m);
+  ctx->sm_w = dalloc<double2>(ctx, m);
+  ctx->sm_dot = dalloc<double2>(ctx, 1);
+  if (!u || !ctx->sm_w || !ctx->sm_dot) return set_err(ctx, IGA_E_OOM, "robin deflation");
+  CK(cudaMemcpyAsync(u, hu.data(), sizeof(double2) * m, cudaMemcpyHostToDevice, ctx->st));
+  TRY(e0_solve(ctx, u, ctx->sm_w, nullptr));
+  double2 hw[2] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
+  for (int q = 0; q < 2; ++q)
+    if (ctx->sm_j[q] >= 0) CK(cudaMemcpyAsync(&hw[q], ctx->sm_w + ctx->sm_j[q], sizeof(double2), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  double2 uw = make_double2(0.0, 0.0);
+  for (int q = 0; q < 2; ++q) uw = uw + ctx->sm_u[q] * hw[q];
+  const double2 ik = make_double2(0.0, ctx->robin_k);
+  const double2 den = make_double2(1.0, 0.0) - cmul(ik, uw);
+  ctx->sm_gamma = cmul(ik, cinv(den));
   return IGA_OK;
 }
 

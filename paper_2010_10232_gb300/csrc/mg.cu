@@ -489,12 +489,46 @@ template <> struct LvBuf<float> {
 };
 
 // D^{-1} for the Jacobi sweeps where it is kept in memory: every 2D FP64 level
-// (FP64 division is slow), FP32 only with variable k; else formed on the fly
+// (FP64 division is slow), FP32 only with variable k, and every level of a 1D
+// problem with a Sommerfeld end (its last diagonal entry carries -i k); else
+// formed on the fly
 template <typename T>
 static const typename cplx<T>::t* jac_dinv(iga_ctx* ctx, LevelData& L) {
-  if (ctx->dim != 2) return nullptr;
+  if (ctx->dim != 2) return ctx->robin_k != 0.0 ? LvBuf<T>::dinv(L) : nullptr;
   if (sizeof(T) == 8 || ctx->vark) return LvBuf<T>::dinv(L);
   return nullptr;
+}
+
+// 1D with a Sommerfeld end: D = K_ii + c M_ii (- i k on the last row), inverted
+// in FP64 and, from the FP32 bands, in FP32
+__global__ void k_robin_dinv(int nx, int p, const double* K, const double* M, const float* Kf, const float* Mf,
+                             double2 c, double rk, double2* dinv, float2* dinvf) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nx) return;
+  const int W = 2 * p + 1;
+  double2 d = mkc(K[(size_t)i * W + p], 0.0) + M[(size_t)i * W + p] * c;
+  float2 df = mkc(Kf[(size_t)i * W + p], 0.f) + Mf[(size_t)i * W + p] * tof(c);
+  if (i == nx - 1) {
+    d = d + mkc(0.0, -rk);
+    df = df + mkc(0.f, (float)-rk);
+  }
+  dinv[i] = cinv(d);
+  dinvf[i] = cinv(df);
+}
+
+iga_status setup_robin_dinv(iga_ctx* ctx) {
+  if (ctx->robin_k == 0.0) return IGA_OK;
+  const double2 c = make_double2(-ctx->sig.x * ctx->k2const, -ctx->sig.y * ctx->k2const);
+  for (int l = 0; l < ctx->L; ++l) {
+    LevelData& L = ctx->lv[l];
+    L.dinv = dalloc<double2>(ctx, L.n);
+    L.dinvf = dalloc<float2>(ctx, L.n);
+    if (!L.dinv || !L.dinvf) return set_err(ctx, IGA_E_OOM, "robin dinv");
+    k_robin_dinv<<<cdiv(L.nx, 128), 128, 0, ctx->st>>>(L.nx, ctx->p, L.K, L.M, L.Kf, L.Mf, c, ctx->robin_k, L.dinv,
+                                                       L.dinvf); iga_count_launch();
+    CKL();
+  }
+  return IGA_OK;
 }
 
 template <typename T>
@@ -685,8 +719,9 @@ iga_status mg_vcycle(iga_ctx* ctx, const typename cplx<T>::t* r, typename cplx<T
 // pre-sweep, one V-cycle, per-operation V-cycle) the conversions are folded
 // into the first and last finest-level kernels: the pre-sweep from zero reads
 // r and also stores its FP32 copy, the last post-sweep writes z in
-// complex128.  The operations and their rounding are those of converting, the
-// FP32 V-cycle and converting back; otherwise that is what runs.
+// complex128.  The operations are those of converting, the FP32 V-cycle and
+// converting back (the compiler may contract them differently, so the two
+// agree to FP32 rounding); otherwise that is what runs.
 iga_status mg_vcycle32_c128(iga_ctx* ctx, const double2* r, double2* z) {
   LevelData& L = ctx->lv[0];
   const int nu2 = ctx->prm.nu_post;

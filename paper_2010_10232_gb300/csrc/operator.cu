@@ -27,6 +27,7 @@ template <typename T> struct OpArgs {
   const C* dinv;       // EPI_JACOBI with variable k: precomputed D^{-1}
   float2* yf;          // EPI_ZMINUS: optional FP32 copy of y (nullptr: none)
   T omega;
+  T rk;                // 1D Sommerfeld end: the last row adds -i rk x_last (0: none)
   // variable k
   const T* B;          // [n_el][Q][p+1]
   const T* wq;         // [n_el][Q]
@@ -94,10 +95,16 @@ __global__ void __launch_bounds__(256) k_kron1d(OpArgs<T> a) {
     }
   }
   C acc = s1 + cmul(a.c, s2);
+  const bool bnd = a.rk != (T)0 && i == a.nx - 1;   // boundary mass N at the Sommerfeld end
+  if (bnd) {
+    const C v = a.x[i];
+    acc = acc + mkc(a.rk * v.y, -a.rk * v.x);       // - i rk x_last
+  }
   C diag = czero<C>();
   if (EPI == EPI_JACOBI) {
     T kd = a.K[(size_t)i * W + P], md = a.M[(size_t)i * W + P];
     diag = mkc(kd, (T)0) + md * a.c;
+    if (bnd) diag = diag + mkc((T)0, -a.rk);
   }
   epilogue<T, EPI>(a, i, acc, EPI == EPI_JACOBI ? a.x[i] : czero<C>(), diag);
 }
@@ -578,8 +585,11 @@ iga_status op_apply(iga_ctx* ctx, int level, int which, const typename cplx<T>::
   a.dinv = nullptr;     // D^{-1} from memory: 2D FP64 levels, FP32 with variable k
   if (epi == EPI_JACOBI && ctx->dim == 2) {
     if constexpr (dbl) a.dinv = (const C*)L.dinv; else if (ctx->vark) a.dinv = (const C*)L.dinvf;
+  } else if (epi == EPI_JACOBI && ctx->robin_k != 0.0) {   // 1D, Sommerfeld end: stored D^{-1}
+    if constexpr (dbl) a.dinv = (const C*)L.dinv; else a.dinv = (const C*)L.dinvf;
   }
   a.omega = (T)omega;
+  a.rk = (T)ctx->robin_k;      // the Sommerfeld term belongs to A and to the CSLP levels alike
   switch (ctx->p) {
     case 1: launch_epi<1, T>(ctx, a, level, epi); break;
     case 2: launch_epi<2, T>(ctx, a, level, epi); break;

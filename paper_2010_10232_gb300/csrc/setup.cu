@@ -117,10 +117,12 @@ __device__ double oslo_alpha(const double* tau, const double* t, int p, int j, i
 #define IGA_TWIDE 16
 
 // Prolongation rows: fine interior i -> coarse interior columns Plo[i] + k.
+// keep_last = 1 (a Sommerfeld end at x = 1): the last function of both
+// spaces is an unknown too.
 __global__ void k_prolong_rows(const double* tc, const double* tf, int p, int nbc, int nbf, int wP,
-                               double* Pw, int* Plo, int* err) {
+                               double* Pw, int* Plo, int* err, int keep_last) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  int nxf = nbf - 2;
+  int nxf = nbf - 2 + keep_last;
   if (i >= nxf) return;
   int bi = i + 1;
   int lo = max(0, (bi - 1) / 2 - 4);
@@ -128,7 +130,7 @@ __global__ void k_prolong_rows(const double* tc, const double* tf, int p, int nb
   int k0 = -1;
   for (int k = 0; k < IGA_TWIDE; ++k) {
     int bj = lo + k;
-    a[k] = (bj >= 1 && bj <= nbc - 2) ? oslo_alpha(tc, tf, p, bj, bi) : 0.0;
+    a[k] = (bj >= 1 && bj <= nbc - 2 + keep_last) ? oslo_alpha(tc, tf, p, bj, bi) : 0.0;
     if (a[k] != 0.0 && k0 < 0) k0 = k;
   }
   if (k0 < 0) k0 = 0;
@@ -140,9 +142,9 @@ __global__ void k_prolong_rows(const double* tc, const double* tf, int p, int nb
 
 // Restriction rows: coarse interior j -> fine interior rows Rlo[j] + k.
 __global__ void k_restrict_rows(const double* tc, const double* tf, int p, int nbc, int nbf, int wR,
-                                double* Rw, int* Rlo, int* err) {
+                                double* Rw, int* Rlo, int* err, int keep_last) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
-  int nxc = nbc - 2;
+  int nxc = nbc - 2 + keep_last;
   if (j >= nxc) return;
   int bj = j + 1;
   int lo = max(0, 2 * bj - p - 4);
@@ -150,7 +152,7 @@ __global__ void k_restrict_rows(const double* tc, const double* tf, int p, int n
   int k0 = -1;
   for (int k = 0; k < IGA_TWIDE; ++k) {
     int bi = lo + k;
-    a[k] = (bi >= 1 && bi <= nbf - 2) ? oslo_alpha(tc, tf, p, bj, bi) : 0.0;
+    a[k] = (bi >= 1 && bi <= nbf - 2 + keep_last) ? oslo_alpha(tc, tf, p, bj, bi) : 0.0;
     if (a[k] != 0.0 && k0 < 0) k0 = k;
   }
   if (k0 < 0) k0 = 0;
@@ -180,7 +182,7 @@ iga_status setup_levels(iga_ctx* ctx) {
   while (true) {
     LevelData& L = ctx->lv[ctx->L];
     L.n_el = ne;
-    L.nx = ne + p - 2;
+    L.nx = ne + p - 2 + (ctx->prm.robin ? 1 : 0);   // a Sommerfeld end keeps the last function
     L.ny = ctx->dim == 2 ? L.nx : 1;
     L.n = L.nx * L.ny;
     ctx->L++;
@@ -230,9 +232,12 @@ iga_status setup_levels(iga_ctx* ctx) {
     F.Rw = dalloc<double>(ctx, (size_t)C.nx * F.wR);
     F.Rlo = dalloc<int>(ctx, C.nx);
     if (!F.Pw || !F.Plo || !F.Rw || !F.Rlo) return set_err(ctx, IGA_E_OOM, "transfer alloc");
-    k_prolong_rows<<<cdiv(F.nx, 128), 128, 0, ctx->st>>>(C.knots, F.knots, p, nbc, nbf, F.wP, F.Pw, F.Plo, err); iga_count_launch();
+    const int keep = ctx->prm.robin ? 1 : 0;
+    k_prolong_rows<<<cdiv(F.nx, 128), 128, 0, ctx->st>>>(C.knots, F.knots, p, nbc, nbf, F.wP, F.Pw, F.Plo, err,
+                                                          keep); iga_count_launch();
     CKL();
-    k_restrict_rows<<<cdiv(C.nx, 128), 128, 0, ctx->st>>>(C.knots, F.knots, p, nbc, nbf, F.wR, F.Rw, F.Rlo, err); iga_count_launch();
+    k_restrict_rows<<<cdiv(C.nx, 128), 128, 0, ctx->st>>>(C.knots, F.knots, p, nbc, nbf, F.wR, F.Rw, F.Rlo, err,
+                                                           keep); iga_count_launch();
     CKL();
     TRY(to_float(ctx, F.Pw, &F.Pwf, (size_t)F.nx * F.wP));
     TRY(to_float(ctx, F.Rw, &F.Rwf, (size_t)C.nx * F.wR));

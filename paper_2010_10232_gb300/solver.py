@@ -38,7 +38,7 @@ class Helmholtz:
 
     def __init__(self, dim=2, p=3, n_el=32, kfield=10.0, beta=(1.0, 0.5), eps=0.0, nu_pre=1, nu_post=1,
                  omega=0.6, n_vcycles=1, precision=0, flexible=0, skip_deflation=0, host_loop=0, arnoldi=None,
-                 fused_vcycle=0, stream=None, precond=0, deflation=1):
+                 fused_vcycle=0, stream=None, precond=0, deflation=1, robin=0):
         self._L = _ffi.lib()
         prm = _ffi.IgaParams()
         self._L.iga_default_params(C.byref(prm))
@@ -70,6 +70,7 @@ class Helmholtz:
         prm.fused_vcycle = int(fused_vcycle)
         prm.precond = int(precond)
         prm.deflation = int(deflation)
+        prm.robin = int(robin)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -223,6 +224,13 @@ class Helmholtz:
         self._check(self._L.iga_load_point_source(self._h, float(x0), float(y0), _ptr(f)))
         return f
 
+    def dirichlet_load(self, g=1.0, f=None):
+        """Right-hand side of u(0) = g for an MP 1-A context (robin = 1)."""
+        f = self.vec() if f is None else f
+        g = complex(g)
+        self._check(self._L.iga_load_dirichlet(self._h, g.real, g.imag, _ptr(f)))
+        return f
+
     def mgs(self, V, j, w):
         """V: (k, n) complex128 rows = basis vectors; w updated in place."""
         h = self.vec(j + 2)
@@ -291,6 +299,7 @@ def from_problem(pr, **kw) -> Helmholtz:
     args = dict(dim=pr.dim, p=pr.p, n_el=pr.n_el, kfield=kfield, beta=pr.shift, eps=pr.eps, nu_pre=pr.nu_pre,
                 nu_post=pr.nu_post, omega=pr.omega, n_vcycles=pr.n_vcycles,
                 precond={"mg": 0, "exact": 1}[getattr(pr, "precond", "mg")],
-                deflation=1 if getattr(pr, "deflation", True) else 0)
+                deflation=1 if getattr(pr, "deflation", True) else 0,
+                robin=1 if getattr(pr, "robin", False) else 0)
     args.update(kw)
     return Helmholtz(**args)

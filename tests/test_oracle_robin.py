@@ -23,7 +23,8 @@ def test_robin_discretisation_matches_direct_assembly(p, k):
     u(0) = 1) has the solution of the plain direct assembly."""
     pr = W.mp1a(k, p, 32)
     s = Solver(pr)
-    assert s.disc.n_x == 32 + p - 1
+    assert s.disc.n_x == pr.n_x == 32 + p - 1 and pr.ndof == s.disc.n
+    assert W.small_2d(n_el=32, p=p).n_x == 32 + p - 2
     u = s.direct(s.load())
     np.testing.assert_allclose(u, asm.mp1a_solve(32, p, k)[1:], rtol=0, atol=1e-12 * np.abs(u).max())
 

@@ -62,8 +62,9 @@ def three_layer_field(scale: float = 1.0) -> KField:
 
 @dataclass
 class Problem:
-    """One Helmholtz instance on the unit interval/square with homogeneous
-    Dirichlet data everywhere."""
+    """One Helmholtz instance on the unit interval/square: homogeneous
+    Dirichlet data everywhere, or (robin, 1D) u(0) = 1 and the Sommerfeld
+    condition at x = 1."""
     dim: int
     p: int
     n_el: int
@@ -81,20 +82,22 @@ class Problem:
     shift_uses_mass: bool = True      # CSLP shift on the mass matrix (True) or the identity (False)
     robin: bool = False               # 1D: Sommerfeld u' - i k u = 0 at x = 1 (MP 1-A); u(0) = 1 lifted
 
+    @property
+    def n_x(self) -> int:
+        """Unknowns per direction: the interior functions, plus the last one
+        when the end x = 1 carries the Sommerfeld condition."""
+        return self.n_el + self.p - 2 + (1 if self.robin else 0)
+
+    @property
+    def ndof(self) -> int:
+        return self.n_x ** self.dim
+
 
 def mp1a(k: float, p: int, n_el: int) -> "Problem":
     """MP 1-A (Section 2.1): -u'' - k^2 u = 0 on [0, 1], u(0) = 1, u'(1) - i k u(1)
     = 0; exact solution exp(i k x).  The right-hand side is the lift of u(0)."""
     return Problem(dim=1, p=p, n_el=n_el, kfield=constant_k(k), robin=True, sources=[],
                    name=f"mp1a_k{k:g}_p{p}_nel{n_el}")
-
-    @property
-    def n_x(self) -> int:
-        return self.n_el + self.p - 2
-
-    @property
-    def ndof(self) -> int:
-        return self.n_x ** self.dim
 
 
 def n_el_for_k(k: float, multiple: int = 1) -> int:

@@ -95,11 +95,28 @@ template <int CIN, int N> struct TcGeom {
   static constexpr int CB = CIN / 8;
   static constexpr size_t a_bytes = (size_t)CB * TC_HY * TC_HX * 16;
   static constexpr size_t b_bytes = (size_t)9 * CB * N * 16;
-  static constexpr size_t smem = a_bytes + b_bytes + 16;    // + mbarrier and TMEM address slot
-  static constexpr int TMEM_COLS = 32;                      // allocation unit >= N
+  static constexpr size_t smem = 2 * a_bytes + b_bytes + 32;   // + two mbarriers and the TMEM address slot
+  static constexpr int ACC_COLS = 32;                           // one accumulator (>= N FP32 columns)
+  static constexpr int TMEM_COLS = 2 * ACC_COLS;                // two, alternating between tiles
   static_assert(N == 16 || N == 32, "accumulator width");
   static_assert(CIN % 16 == 0, "K chunks of 16 channels");
 };
+
+__device__ __forceinline__ void cp_async16(unsigned dst, const void* src, unsigned src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// bounded wait on an mbarrier phase; false if the limit ran out
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned a, unsigned parity) {
+  unsigned polls = 0;
+  while (!mbar_try_wait(a, parity)) {
+    if (++polls > TC_WAIT_LIMIT) return false;
+    __nanosleep(32);
+  }
+  return true;
+}
 
 }  // namespace
 
@@ -107,6 +124,13 @@ template <int CIN, int N> struct TcGeom {
 // output channels, rows beyond COUTP read as zero up to N); EPI as in cnn.cu:
 // 0 + bias, ReLU, bf16 [px][N]; 1 + bias, FP32 [px][2]; 2 times (mask > 0),
 // bf16 [px][N].  err: set to 1 if a wait gave up.
+//
+// Persistent blocks take tiles blockIdx.x, blockIdx.x + gridDim.x, ... in a
+// two-stage pipeline: iteration i issues the MMAs of tile i into accumulator
+// i % 2 (from A buffer i % 2), then waits for tile i - 1's MMAs, reads its
+// accumulator, starts the cp.async halo load of tile i + 1 into the A buffer
+// tile i - 1 used, and stores tile i - 1's outputs.  The tensor core works
+// on one tile while the block loads the next and writes the previous.
 template <int CIN, int N, int EPI>
 __global__ void __launch_bounds__(TC_NT) k_conv3x3_tc(const bf16* __restrict__ X, const bf16* __restrict__ Wt,
                                                       int coutp, const float* __restrict__ bias,
@@ -115,10 +139,9 @@ __global__ void __launch_bounds__(TC_NT) k_conv3x3_tc(const bf16* __restrict__ X
   using G = TcGeom<CIN, N>;
   constexpr int CB = G::CB;
   extern __shared__ __align__(128) unsigned char tc_smem[];
-  unsigned char* As = tc_smem;
-  unsigned char* Bs = tc_smem + G::a_bytes;
-  unsigned long long* mbar = reinterpret_cast<unsigned long long*>(tc_smem + G::a_bytes + G::b_bytes);
-  unsigned* tslot = reinterpret_cast<unsigned*>(mbar + 1);
+  unsigned char* Bs = tc_smem + 2 * G::a_bytes;
+  unsigned long long* mbar = reinterpret_cast<unsigned long long*>(Bs + G::b_bytes);
+  unsigned* tslot = reinterpret_cast<unsigned*>(mbar + 2);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (warp == 0) {
@@ -129,6 +152,7 @@ __global__ void __launch_bounds__(TC_NT) k_conv3x3_tc(const bf16* __restrict__ X
   }
   if (tid == 0) {
     mbar_init(smem_u32(mbar), 1);
+    mbar_init(smem_u32(mbar + 1), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   // weights into the B layout: chunk (t, cb, n) = Wt[n][t][8 cb .. 8 cb + 7]
@@ -138,108 +162,133 @@ __global__ void __launch_bounds__(TC_NT) k_conv3x3_tc(const bf16* __restrict__ X
     if (n < coutp) v = *reinterpret_cast<const uint4*>(Wt + ((size_t)n * 9 + t) * CIN + cb * 8);
     *reinterpret_cast<uint4*>(Bs + (size_t)((t * CB + cb) * N + n) * 16) = v;
   }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const unsigned tmem = *tslot;
-  const unsigned a_base = smem_u32(As), b_base = smem_u32(Bs), mb = smem_u32(mbar);
+  const unsigned a_base0 = smem_u32(tc_smem), b_base = smem_u32(Bs);
   constexpr unsigned idesc = umma_idesc_bf16(128, N);
   constexpr unsigned A_LBO = TC_HY * TC_HX * 16, A_SBO = TC_HX * 16, B_LBO = N * 16, B_SBO = 8 * 16;
 
   const int tiles_x = (W + TC_TX - 1) / TC_TX, tiles_y = (H + TC_TY - 1) / TC_TY;
-  const int ntiles = tiles_x * tiles_y * B;
-  unsigned phase = 0;
-  bool failed = false;
-  for (int tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
-    const int b = tile / (tiles_x * tiles_y), rem = tile - b * tiles_x * tiles_y;
+  const int per_img = tiles_x * tiles_y, ntiles = per_img * B;
+
+  // input halo tile into the A layout (16-byte chunks of 8 channels, zero-filled outside the image)
+  auto load_tile = [&](int tile, unsigned a_dst) {
+    const int b = tile / per_img, rem = tile - b * per_img;
     const int ty = rem / tiles_x, tx = rem - ty * tiles_x;
     const int x0 = tx * TC_TX, y0 = ty * TC_TY;
     const size_t img = (size_t)b * H * W;
-    // input halo tile into the A layout (16-byte chunks of 8 channels, zero outside)
     for (int i = tid; i < CB * TC_HY * TC_HX; i += TC_NT) {
       const int hx = i % TC_HX, r = i / TC_HX, hy = r % TC_HY, cb = r / TC_HY;
       const int gy = y0 - 1 + hy, gx = x0 - 1 + hx;
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (gy >= 0 && gy < H && gx >= 0 && gx < W)
-        v = *reinterpret_cast<const uint4*>(X + (img + (size_t)gy * W + gx) * CIN + cb * 8);
-      *reinterpret_cast<uint4*>(As + (size_t)i * 16) = v;
+      const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
+      const bf16* src = in ? X + (img + (size_t)gy * W + gx) * CIN + cb * 8 : X;
+      cp_async16(a_dst + (unsigned)i * 16u, src, in ? 16u : 0u);
     }
-    // generic-proxy writes of the operands become visible to the tensor core
+  };
+
+  if ((int)blockIdx.x < ntiles) load_tile(blockIdx.x, a_base0);
+  cp_async_commit();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const unsigned tmem = *tslot;
+  const unsigned mb0 = smem_u32(mbar);
+
+  unsigned phase = 0u, pending = 0u;     // bit b: parity to wait for / MMAs outstanding on mbarrier b
+  bool failed = false;
+  for (int it = 0;; ++it) {
+    const int cur = (int)blockIdx.x + it * (int)gridDim.x;
+    const bool have_cur = cur < ntiles;
+    if (!have_cur && it == 0) break;
+    const int s = it & 1;
+    // tile cur's operands landed (the only outstanding cp.async group) and
+    // every thread finished reading the accumulator this tile overwrites
+    cp_async_wait_all();
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
     __syncthreads();
-    if (tid == 0) {
-      tc_fence_after();
+    if (have_cur) {
+      if (tid == 0) {
+        tc_fence_after();
+        const unsigned a_base = a_base0 + (unsigned)(s * G::a_bytes);
+        const unsigned d_tmem = tmem + (unsigned)(s * G::ACC_COLS);
 #pragma unroll
-      for (int t = 0; t < 9; ++t) {
-        const int dy = t / 3, dx = t % 3;
+        for (int t = 0; t < 9; ++t) {
+          const int dy = t / 3, dx = t % 3;
 #pragma unroll
-        for (int kc = 0; kc < CIN / 16; ++kc) {
-          const unsigned a_off = (unsigned)((((2 * kc) * TC_HY + dy) * TC_HX + dx) * 16);
-          const unsigned b_off = (unsigned)((t * CB + 2 * kc) * N * 16);
-          tc_mma(tmem, umma_desc(a_base + a_off, A_LBO, A_SBO), umma_desc(b_base + b_off, B_LBO, B_SBO), idesc,
-                 (t | kc) != 0 ? 1u : 0u);
+          for (int kc = 0; kc < CIN / 16; ++kc) {
+            const unsigned a_off = (unsigned)((((2 * kc) * TC_HY + dy) * TC_HX + dx) * 16);
+            const unsigned b_off = (unsigned)((t * CB + 2 * kc) * N * 16);
+            tc_mma(d_tmem, umma_desc(a_base + a_off, A_LBO, A_SBO), umma_desc(b_base + b_off, B_LBO, B_SBO), idesc,
+                   (t | kc) != 0 ? 1u : 0u);
+          }
         }
+        tc_commit(mb0 + 8u * (unsigned)s);
       }
-      tc_commit(mb);
+      pending |= 1u << s;
     }
-    // bounded wait for the accumulator; the give-up decision is made for the
-    // whole block (every thread leaves the loop together)
-    unsigned polls = 0;
-    bool done = true;
-    while (!mbar_try_wait(mb, phase)) {
-      if (++polls > TC_WAIT_LIMIT) {
-        done = false;
+    const bool have_prev = it > 0;
+    const int q = s ^ 1;
+    float acc[N];
+    if (have_prev) {
+      // the give-up decision is made for the whole block
+      const bool done = mbar_wait_bounded(mb0 + 8u * (unsigned)q, (phase >> q) & 1u);
+      if (__syncthreads_or(!done)) {
+        failed = true;
+        if (tid == 0) atomicExch(err, 1);
         break;
       }
-      __nanosleep(32);
+      phase ^= 1u << q;
+      pending &= ~(1u << q);
+      tc_fence_after();
+      const unsigned trow = tmem + (unsigned)(q * G::ACC_COLS) + ((unsigned)(32 * warp) << 16);
+      tc_ld16(trow, acc);
+      if constexpr (N == 32) tc_ld16(trow + 16, acc + 16);
     }
-    phase ^= 1u;
-    if (__syncthreads_or(!done)) {
-      failed = true;
-      if (tid == 0) atomicExch(err, 1);
-      break;
-    }
-    tc_fence_after();
-    // epilogue: thread <-> TMEM lane 32 warp + lane <-> pixel (m % 8, m / 8)
-    const int m = 32 * warp + lane;
-    const int gx = x0 + (m & 7), gy = y0 + (m >> 3);
-    const unsigned trow = tmem + ((unsigned)(32 * warp) << 16);
-    float acc[N];
-    tc_ld16(trow, acc);
-    if constexpr (N == 32) tc_ld16(trow + 16, acc + 16);
-    if (gx < W && gy < H) {
-      const size_t p = img + (size_t)gy * W + gx;
-      if (EPI == 0) {
-        __nv_bfloat162 o[N / 2];
+    // A buffer q is free once tile cur - gridDim.x's MMAs completed
+    const int nxt = cur + (int)gridDim.x;
+    if (have_cur && nxt < ntiles) load_tile(nxt, a_base0 + (unsigned)(q * G::a_bytes));
+    cp_async_commit();
+    if (have_prev) {
+      // epilogue: thread <-> TMEM lane 32 warp + lane <-> pixel (m % 8, m / 8)
+      const int prev = cur - (int)gridDim.x;
+      const int b = prev / per_img, rem = prev - b * per_img;
+      const int ty = rem / tiles_x, tx = rem - ty * tiles_x;
+      const int m = 32 * warp + lane;
+      const int gx = tx * TC_TX + (m & 7), gy = ty * TC_TY + (m >> 3);
+      if (gx < W && gy < H) {
+        const size_t p = (size_t)b * H * W + (size_t)gy * W + gx;
+        if (EPI == 0) {
+          __nv_bfloat162 o[N / 2];
 #pragma unroll
-        for (int c = 0; c < N; c += 2)
-          o[c / 2] = __floats2bfloat162_rn(fmaxf(acc[c] + bias[c], 0.f), fmaxf(acc[c + 1] + bias[c + 1], 0.f));
+          for (int c = 0; c < N; c += 2)
+            o[c / 2] = __floats2bfloat162_rn(fmaxf(acc[c] + bias[c], 0.f), fmaxf(acc[c + 1] + bias[c + 1], 0.f));
 #pragma unroll
-        for (int q = 0; q < N / 8; ++q)
-          reinterpret_cast<uint4*>((bf16*)Yout + p * N)[q] = reinterpret_cast<const uint4*>(o)[q];
-      } else if (EPI == 1) {
-        *reinterpret_cast<float2*>((float*)Yout + p * 2) = make_float2(acc[0] + bias[0], acc[1] + bias[1]);
-      } else {
-        __nv_bfloat162 o[N / 2];
-        const __nv_bfloat162* mk = reinterpret_cast<const __nv_bfloat162*>(mask + p * N);
+          for (int v = 0; v < N / 8; ++v)
+            reinterpret_cast<uint4*>((bf16*)Yout + p * N)[v] = reinterpret_cast<const uint4*>(o)[v];
+        } else if (EPI == 1) {
+          *reinterpret_cast<float2*>((float*)Yout + p * 2) = make_float2(acc[0] + bias[0], acc[1] + bias[1]);
+        } else {
+          __nv_bfloat162 o[N / 2];
+          const __nv_bfloat162* mk = reinterpret_cast<const __nv_bfloat162*>(mask + p * N);
 #pragma unroll
-        for (int c = 0; c < N; c += 2) {
-          const __nv_bfloat162 q = mk[c / 2];
-          o[c / 2] = __floats2bfloat162_rn(__bfloat162float(q.x) > 0.f ? acc[c] : 0.f,
-                                           __bfloat162float(q.y) > 0.f ? acc[c + 1] : 0.f);
+          for (int c = 0; c < N; c += 2) {
+            const __nv_bfloat162 mv = mk[c / 2];
+            o[c / 2] = __floats2bfloat162_rn(__bfloat162float(mv.x) > 0.f ? acc[c] : 0.f,
+                                             __bfloat162float(mv.y) > 0.f ? acc[c + 1] : 0.f);
+          }
+#pragma unroll
+          for (int v = 0; v < N / 8; ++v)
+            reinterpret_cast<uint4*>((bf16*)Yout + p * N)[v] = reinterpret_cast<const uint4*>(o)[v];
         }
-#pragma unroll
-        for (int q = 0; q < N / 8; ++q)
-          reinterpret_cast<uint4*>((bf16*)Yout + p * N)[q] = reinterpret_cast<const uint4*>(o)[q];
       }
     }
-    tc_fence_before();
-    __syncthreads();     // the next tile overwrites the A tile and the accumulator
+    if (!have_cur) break;
   }
+  cp_async_wait_all();
   // a block that gave up waits (bounded) for its own MMAs before freeing TMEM
   if (failed) {
-    unsigned polls = 0;
-    while (!mbar_try_wait(mb, phase ^ 1u) && ++polls < TC_WAIT_LIMIT) __nanosleep(32);
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+      if ((pending >> b) & 1u) (void)mbar_wait_bounded(mb0 + 8u * (unsigned)b, (phase >> b) & 1u);
   }
   tc_fence_before();
   __syncthreads();
@@ -253,13 +302,25 @@ template <int CIN, int N, int EPI>
 static cudaError_t launch_tc(const bf16* X, const bf16* Wt, int coutp, const float* bias, const bf16* mask, void* Y,
                              int B, int H, int W, int* err, int num_sms, cudaStream_t st) {
   using G = TcGeom<CIN, N>;
-  static bool attr = false;
-  if (!attr) {
+  static int per_sm = 0;
+  if (per_sm == 0) {
     cudaFuncSetAttribute(k_conv3x3_tc<CIN, N, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem);
-    attr = true;
+    // resident blocks per SM: shared memory (plus the 1 KB the runtime
+    // reserves per block), 64 registers x 128 threads, and the SM's 512
+    // tensor-memory columns, TMEM_COLS per block
+    int dev = 0, smem_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    int by_smem = smem_sm / (int)(G::smem + 1024);
+    int n = 512 / G::TMEM_COLS;
+    if (by_smem < n) n = by_smem;
+    if (65536 / (64 * TC_NT) < n) n = 65536 / (64 * TC_NT);
+    per_sm = n < 1 ? 1 : n;
   }
   const long long tiles = (long long)cdiv(W, TC_TX) * cdiv(H, TC_TY) * B;
-  const int grid = (int)(tiles < 4LL * num_sms ? tiles : 4LL * num_sms);
+  const long long cap = (long long)per_sm * num_sms;
+  const int grid = (int)(tiles < cap ? tiles : cap);
+  if (grid == 0) return cudaSuccess;
   k_conv3x3_tc<CIN, N, EPI><<<grid, TC_NT, G::smem, st>>>(X, Wt, coutp, bias, mask, Y, B, H, W, err);
   iga_count_launch();
   return cudaGetLastError();

@@ -172,6 +172,19 @@ def test_vcycle_fp64_variants(nu, cycles):
     assert rel_err(to_n(h.vcycle(to_t(r))), hier.apply(r, cycles)) <= 1e-11
 
 
+def test_twelve_vcycles_large_shift():
+    """The Section 4.3.2 multigrid setting (beta_2 = 4.2, three pre- and
+    post-sweeps, 12 V-cycles as a stationary iteration) at p = 2."""
+    pr = W.small_2d(n_el=64, p=2, k=40.0)
+    pr.nu_pre = pr.nu_post = 3
+    pr.n_vcycles = 12
+    pr.shift = (1.0, 4.2)
+    h = from_problem(pr)
+    hier = mg.MGHierarchy(2, 2, 64, pr.kfield, 1.0, 4.2, nu_pre=3, nu_post=3)
+    r = rvec(h.n, 86)
+    assert rel_err(to_n(h.vcycle(to_t(r))), hier.apply(r, 12)) <= 1e-11
+
+
 @pytest.mark.parametrize("name", ["2d_p3", "2d_var_p3", "1d_p2"])
 def test_vcycle_fp32(name):
     pr = CASES[name]

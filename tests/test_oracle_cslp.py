@@ -16,6 +16,7 @@ import scipy.sparse.linalg as spla
 
 import workloads as W
 from oracle import assembly as asm
+from oracle import multigrid as mg
 from oracle.krylov import gmres
 from oracle.solver import Solver, rel_err
 
@@ -117,3 +118,22 @@ def test_cex_without_deflation_solves():
         K = np.stack([np.linalg.matrix_power(B, i) @ b for i in range(j)], axis=1)
         c, *_ = np.linalg.lstsq(B @ K, b, rcond=None)
         np.testing.assert_allclose(rj.u, K @ c, rtol=1e-8, atol=1e-12 * np.abs(K @ c).max())
+
+
+@pytest.mark.parametrize("p,grows", [(1, False), (2, False), (3, True)])
+def test_twelve_cycle_iteration_with_jacobi_smoother(p, grows):
+    """Section 4.3.2's C_MG^12 setting (beta_2 = 4.2, three pre- and
+    post-sweeps) with Section 3's damped Jacobi (omega = 0.6) as the
+    stationary iteration x <- x + V(b - M_beta x): it contracts for p <= 2
+    and grows for p = 3, where omega times the largest eigenvalue of
+    D^{-1} M_beta on the mass-dominated modes passes 2."""
+    n_el, k = 64, 40.0
+    pr = W.small_2d(n_el=n_el, p=p, k=k)
+    hier = mg.MGHierarchy(2, p, n_el, pr.kfield, 1.0, 4.2, nu_pre=3, nu_post=3)
+    b = W.seeded_complex_vector(pr.n_x ** 2, 1)
+    Mb = hier.levels[0].Mb
+    x = np.zeros_like(b)
+    for _ in range(12):
+        x = x + hier.vcycle(b - Mb @ x)
+    res = np.linalg.norm(b - Mb @ x) / np.linalg.norm(b)
+    assert (res > 1e3) if grows else (res < 1e-3), res

@@ -50,20 +50,29 @@ def local_tables(n_el: int, p: int):
     t = bspline.open_uniform_knots(n_el, p)
     xq, wq, spans = bspline.element_quadrature(t, p)
     assert len(spans) == n_el
-    pts = xq.reshape(-1)
-    phi = bspline.basis_all(t, p, pts)
-    dphi = bspline.basis_deriv_all(t, p, pts)
     nq = p + 1
     B = np.zeros((n_el, nq, p + 1))
     D = np.zeros((n_el, nq, p + 1))
-    for e in range(n_el):
-        cols = slice(e * nq, (e + 1) * nq)
-        # every function outside e..e+p must vanish on span e
-        mask = np.ones(phi.shape[0], bool)
-        mask[e:e + p + 1] = False
-        assert np.all(phi[mask, cols] == 0.0)
-        B[e] = phi[e:e + p + 1, cols].T
-        D[e] = dphi[e:e + p + 1, cols].T
+    if n_el <= 256:
+        pts = xq.reshape(-1)
+        phi = bspline.basis_all(t, p, pts)
+        dphi = bspline.basis_deriv_all(t, p, pts)
+        for e in range(n_el):
+            cols = slice(e * nq, (e + 1) * nq)
+            # every function outside e..e+p must vanish on span e
+            mask = np.ones(phi.shape[0], bool)
+            mask[e:e + p + 1] = False
+            assert np.all(phi[mask, cols] == 0.0)
+            B[e] = phi[e:e + p + 1, cols].T
+            D[e] = dphi[e:e + p + 1, cols].T
+    else:
+        # the functions e..e+p active on span e depend only on the knots
+        # t[e .. e+2p+1]: the same recursion on that window gives the same
+        # values (no Gauss point is a knot) without evaluating all n_el + p
+        # functions at every point
+        tw = np.stack([t[e:e + 2 * p + 2] for e in range(n_el)])
+        B[:] = bspline.basis_windows(tw, p, xq).transpose(0, 2, 1)
+        D[:] = bspline.basis_deriv_windows(tw, p, xq).transpose(0, 2, 1)
     return B, D, xq, wq
 
 
@@ -72,17 +81,17 @@ def assemble_1d(n_el: int, p: int, k2_fn=None):
     k2_fn is given, the weighted mass int k^2 phi_i phi_j, as CSR matrices."""
     B, D, xq, wq = local_tables(n_el, p)
     nb = n_el + p
-    rows, cols, kv, mv, mkv = [], [], [], [], []
     k2 = k2_fn(xq) if k2_fn is not None else None
-    for e in range(n_el):
-        for a in range(p + 1):
-            for c in range(p + 1):
-                rows.append(e + a)
-                cols.append(e + c)
-                kv.append(np.sum(wq[e] * D[e, :, a] * D[e, :, c]))
-                mv.append(np.sum(wq[e] * B[e, :, a] * B[e, :, c]))
-                if k2 is not None:
-                    mkv.append(np.sum(wq[e] * k2[e] * B[e, :, a] * B[e, :, c]))
+    # element e, functions a, c: sum over q of w_q f_a(x_q) g_c(x_q), the
+    # products formed left to right and summed over q in order, for all
+    # (e, a, c) at once; entry (e + a, e + c) (duplicates add up)
+    e_, a_, c_ = np.meshgrid(np.arange(n_el), np.arange(p + 1), np.arange(p + 1), indexing="ij")
+    rows, cols = (e_ + a_).reshape(-1), (e_ + c_).reshape(-1)
+    w4 = wq[:, :, None, None]
+    kv = np.sum(w4 * D[:, :, :, None] * D[:, :, None, :], axis=1).reshape(-1)
+    mv = np.sum(w4 * B[:, :, :, None] * B[:, :, None, :], axis=1).reshape(-1)
+    if k2 is not None:
+        mkv = np.sum(w4 * k2[:, :, None, None] * B[:, :, :, None] * B[:, :, None, :], axis=1).reshape(-1)
     K = sp.csr_matrix((kv, (rows, cols)), shape=(nb, nb))
     M = sp.csr_matrix((mv, (rows, cols)), shape=(nb, nb))
     Mk = sp.csr_matrix((mkv, (rows, cols)), shape=(nb, nb)) if k2 is not None else None

@@ -59,6 +59,46 @@ def basis_all(knots: np.ndarray, p: int, x) -> np.ndarray:
     return phi
 
 
+def basis_windows(tw: np.ndarray, p: int, x: np.ndarray) -> np.ndarray:
+    """basis_all for many knot windows at once: tw[e] holds 2p+2 knots and
+    x[e] points inside its middle span (span p, so no point is a knot and the
+    right-end rule never applies); the same recursion, term by term, as
+    basis_all on each window.  Returns shape (E, p+1, len(x[e]))."""
+    E, nx = x.shape
+    m = tw.shape[1] - 1
+    phi = np.zeros((E, m, nx))
+    for j in range(m):
+        phi[:, j] = (tw[:, j, None] <= x) & (x < tw[:, j + 1, None])
+    with np.errstate(divide="ignore", invalid="ignore"):
+        for q in range(1, p + 1):
+            new = np.zeros((E, m - q, nx))
+            for j in range(m - q):
+                d1 = (tw[:, j + q] - tw[:, j])[:, None]
+                d2 = (tw[:, j + q + 1] - tw[:, j + 1])[:, None]
+                term = np.zeros((E, nx))
+                term = term + np.where(d1 != 0.0, (x - tw[:, j, None]) / d1 * phi[:, j], 0.0)
+                term = term + np.where(d2 != 0.0, (tw[:, j + q + 1, None] - x) / d2 * phi[:, j + 1], 0.0)
+                new[:, j] = term
+            phi = new
+    return phi
+
+
+def basis_deriv_windows(tw: np.ndarray, p: int, x: np.ndarray) -> np.ndarray:
+    """basis_deriv_all for many knot windows at once (as basis_windows)."""
+    E, nx = x.shape
+    if p == 0:
+        return np.zeros((E, 1, nx))
+    low = basis_windows(tw, p - 1, x)
+    d = np.zeros((E, p + 1, nx))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        for j in range(p + 1):
+            d1 = (tw[:, j + p] - tw[:, j])[:, None]
+            d2 = (tw[:, j + p + 1] - tw[:, j + 1])[:, None]
+            d[:, j] = d[:, j] + np.where(d1 != 0.0, p / d1 * low[:, j], 0.0)
+            d[:, j] = d[:, j] - np.where(d2 != 0.0, p / d2 * low[:, j + 1], 0.0)
+    return d
+
+
 def basis_deriv_all(knots: np.ndarray, p: int, x) -> np.ndarray:
     """First derivatives of all degree-p B-splines at x, by differentiating the
     recursion (de Boor): phi'_{j,p} = p/(xi_{j+p}-xi_j) phi_{j,p-1}

@@ -36,47 +36,56 @@ def level_sizes(n_el: int) -> list[int]:
     return out
 
 
-def boehm_insert(knots: np.ndarray, p: int, coef: np.ndarray, u: float):
-    """Insert one knot u (Boehm's algorithm).  coef has one row per basis
-    function (any number of columns).  Returns (new_knots, new_coef)."""
+def boehm_insert(knots: np.ndarray, p: int, rows: list, u: float):
+    """Insert one knot u (Boehm's algorithm).  rows holds one sparse row
+    {column: value} per basis function (the coefficients of any number of
+    splines, one per column).  With t[k] <= u < t[k+1], rows i <= k - p are
+    kept, rows i > k shift by one, and rows k - p < i <= k become
+    (1 - a_i) c_{i-1} + a_i c_i with a_i = (u - t_i) / (t_{i+p} - t_i).
+    Returns (new_knots, new_rows)."""
     t = knots
     k = int(np.searchsorted(t, u, side='right') - 1)      # t[k] <= u < t[k+1]
-    n = coef.shape[0]
-    new = np.zeros((n + 1,) + coef.shape[1:])
-    for i in range(n + 1):
-        if i <= k - p:
-            new[i] = coef[i]
-        elif i <= k:
-            a = (u - t[i]) / (t[i + p] - t[i])
-            new[i] = (1.0 - a) * coef[i - 1] + a * coef[i]
-        else:
-            new[i] = coef[i - 1]
-    return np.insert(t, k + 1, u), new
+    mid = []
+    for i in range(k - p + 1, k + 1):
+        a = (u - t[i]) / (t[i + p] - t[i])
+        lo, hi = rows[i - 1], rows[i]
+        mid.append({c: (1.0 - a) * lo.get(c, 0.0) + a * hi.get(c, 0.0) for c in set(lo) | set(hi)})
+    return np.insert(t, k + 1, u), rows[:k - p + 1] + mid + rows[k:]
 
 
-def prolongation_1d(n_el_coarse: int, p: int) -> np.ndarray:
-    """Dense knot-insertion matrix (full bases): fine coefficients of each
-    coarse basis function, obtained by inserting the midpoints of all coarse
-    spans one at a time."""
+def prolongation_1d_sparse(n_el_coarse: int, p: int) -> sp.csr_matrix:
+    """Knot-insertion matrix (full bases): fine coefficients of each coarse
+    basis function, obtained by inserting the midpoints of all coarse spans
+    one at a time into the identity (one column per coarse function)."""
     tc = bspline.open_uniform_knots(n_el_coarse, p)
     nbc = n_el_coarse + p
-    t, C = tc.copy(), np.eye(nbc)
+    t, rows = tc.copy(), [{j: 1.0} for j in range(nbc)]
     n_f = 2 * n_el_coarse
     for i in range(n_el_coarse):
         u = float(2 * i + 1) / float(n_f)
-        t, C = boehm_insert(t, p, C, u)
+        t, rows = boehm_insert(t, p, rows, u)
     tf = bspline.open_uniform_knots(n_f, p)
     assert np.array_equal(t, tf), "knot insertion did not produce the fine knot vector"
-    return C
+    ri = [i for i, r in enumerate(rows) for _ in r]
+    ci = [c for r in rows for c in r]
+    vals = [v for r in rows for v in r.values()]
+    return sp.csr_matrix((vals, (ri, ci)), shape=(len(rows), nbc))
 
 
-def prolongation_interior_1d(n_el_coarse: int, p: int, robin: bool = False) -> np.ndarray:
+def prolongation_1d(n_el_coarse: int, p: int) -> np.ndarray:
+    """The knot-insertion matrix, dense."""
+    return prolongation_1d_sparse(n_el_coarse, p).toarray()
+
+
+def prolongation_interior_1d(n_el_coarse: int, p: int, robin: bool = False, sparse: bool = False):
     """Interior rows/columns of the knot-insertion matrix.  A coarse spline
     with zero end coefficients refines to a fine spline with zero end
     coefficients, so the Dirichlet-eliminated transfer is the submatrix (with
-    the Sommerfeld end at x = 1, only the first row and column are dropped)."""
-    P = prolongation_1d(n_el_coarse, p)
-    return P[1:, 1:] if robin else P[1:-1, 1:-1]
+    the Sommerfeld end at x = 1, only the first row and column are dropped).
+    Dense unless sparse=True (CSR)."""
+    P = prolongation_1d_sparse(n_el_coarse, p)
+    P = P[1:, 1:] if robin else P[1:-1, 1:-1]
+    return P.tocsr() if sparse else P.toarray()
 
 
 class Level:
@@ -99,7 +108,7 @@ class MGHierarchy:
             disc = fine_disc if (li == 0 and fine_disc is not None) else Discretization(dim, p, ne, kfield, robin)
             self.levels.append(Level(disc, beta1, beta2, uses_mass))
             if li > 0:
-                P1 = sp.csr_matrix(prolongation_interior_1d(ne, p, robin))
+                P1 = prolongation_interior_1d(ne, p, robin, sparse=True)
                 self.P.append(P1 if dim == 1 else sp.kron(P1, P1).tocsr())
         self.coarse_dense = self.levels[-1].Mb.toarray()
 

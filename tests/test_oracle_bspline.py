@@ -67,3 +67,20 @@ def test_knots_are_single_divisions():
     # nested: the coarse knots are every other fine knot, bit for bit
     tf, tc = bspline.open_uniform_knots(640, 3), bspline.open_uniform_knots(320, 3)
     assert np.array_equal(tf[3:-3][::2], tc[3:-3])
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5])
+def test_windowed_basis_equals_global_recursion(p):
+    """The per-span evaluation on knot windows (used for large meshes) gives
+    bit for bit the values and derivatives of the global recursion."""
+    from oracle import assembly as asm
+    n_el = 300
+    B, D, xq, _ = asm.local_tables(n_el, p)
+    t = bspline.open_uniform_knots(n_el, p)
+    pts = xq.reshape(-1)
+    phi, dphi = bspline.basis_all(t, p, pts), bspline.basis_deriv_all(t, p, pts)
+    nq = p + 1
+    for e in range(n_el):
+        cols = slice(e * nq, (e + 1) * nq)
+        assert np.array_equal(B[e], phi[e:e + p + 1, cols].T)
+        assert np.array_equal(D[e], dphi[e:e + p + 1, cols].T)

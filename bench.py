@@ -751,7 +751,46 @@ def other_configs(stream, flush):
     except Exception as e:
         out["cfg5_error"] = str(e)[:300]
     torch.cuda.empty_cache()
+    try:
+        out["scaling_1d_mp1b"] = scaling_1d(stream, flush)
+    except Exception as e:
+        out["scaling_1d_error"] = str(e)[:300]
+    torch.cuda.empty_cache()
     return out
+
+
+def scaling_1d(stream, flush):
+    """Section 4.3.1's 1D scaling (MP 1-B, kh = 0.625, tolerance 1e-7, at most
+    100 iterations): k = 10^4, 10^5, 10^6 (n_el = 16 000 .. 1 600 000), p = 1..5,
+    with DC1 (one V-cycle, beta_2 = 1), D (deflation alone) and C_ex (beta_2 =
+    1/k, no deflation); the paper's counts (Tables 2 and 4) beside them.  E
+    (up to ~800 000 unknowns), C_ex and coarsest levels above 2048 dofs are
+    solved by the band solver."""
+    import torch
+    from paper_2010_10232_gb300.solver import Helmholtz
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "table2_3_mp1b_iterations.json")))
+    forms = (("DC1", dict(beta=(1.0, 1.0)), "dc1"), ("D", dict(n_vcycles=0), "d"), ("C_ex", None, "cex"))
+    rows = {}
+    for k in (1e4, 1e5, 1e6):
+        for p in (1, 2, 3, 4, 5):
+            n_el = int(round(k / 0.625))
+            for name, kw, gkey in forms:
+                if kw is None:
+                    kw = dict(precond=1, deflation=0, beta=(1.0, 1.0 / k))
+                t0 = time.perf_counter()
+                h = Helmholtz(dim=1, p=p, n_el=n_el, kfield=k, **kw)
+                setup_s = time.perf_counter() - t0
+                f = h.point_source(0.5)
+                xx = h.vec()
+                h.solve(f, x=xx, maxit=100)
+                ms, it, tr, st = _time_solves(h, f, xx, stream, flush, 1, maxit=100)
+                g = gold[gkey][str(p)] if gkey == "cex" else gold[gkey][str(int(k))][str(p)]
+                rows[f"k{int(k)}_p{p}_{name}"] = {"n_el": n_el, "n_dof": h.n, "levels": h.levels, "E_dof": h.m,
+                                                  "setup_s": setup_s, "ms": ms, "iterations": it,
+                                                  "converged": st == 0, "true_res": tr, "paper": g}
+                del h
+            torch.cuda.empty_cache()
+    return rows
 
 
 def batched_sharded(ws, rank, dist):

@@ -92,7 +92,8 @@ typedef struct {
                               0 (default): n_vcycles multigrid V-cycles of the CSLP
                                  (C_MG^j); n_vcycles = 0 means no CSLP at all (the
                                  deflation-only D / D_eps of Section 4.3.1);
-                              1: the CSLP matrix inverted exactly (C_ex): 2D/1D constant
+                              1: the CSLP matrix inverted exactly (C_ex).  1D: band LU
+                                 with partial pivoting (any size, any k); 2D: constant
                                  k, n_x <= 2048, by fast diagonalisation of the finest
                                  level with FP64 iterative refinement               */
   int deflation;           /* 1 (default): ADP deflation, GMRES on M~^{-1} P A x^ =
@@ -105,8 +106,8 @@ typedef struct {
                               (the last basis function is an unknown, A = S - k^2 M -
                               i k N with the boundary mass N of Section 2.3; the CSLP
                               levels carry the same boundary term), Dirichlet at x = 0
-                              with its value entered by iga_load_dirichlet.  Needs
-                              precond 0.                                                  */
+                              with its value entered by iga_load_dirichlet.  Constant
+                              k (n_lines = 0).                                            */
 } iga_params;
 
 typedef struct iga_ctx iga_ctx;
@@ -118,7 +119,11 @@ void iga_default_params(iga_params* prm);
 
 /* Build everything the solve needs on the device (Sections 2.3, 3): knots,
    Gauss tables, 1D band matrices and transfer operators per multigrid level,
-   the coarsest-level inverse, Z and the factorised E.  Synchronises.
+   the coarsest-level inverse, Z and the factorised E.  The coarsest level is
+   inverted densely up to 2048 dofs; beyond that 2D setups are refused and 1D
+   ones factorise its band.  1D E is factorised as a band matrix (partitioned
+   LU with partial pivoting), 2D E by fast diagonalisation (constant k) or
+   block LU (variable k).  Synchronises.
    prm is a host pointer; *out receives a context to release with iga_destroy.
    Errors: IGA_E_INVALID for out-of-range parameters, IGA_E_OOM, IGA_E_CUDA. */
 iga_status iga_setup(const iga_params* prm, iga_ctx** out);

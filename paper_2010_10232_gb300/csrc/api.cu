@@ -92,7 +92,7 @@ iga_status iga_setup(const iga_params* prm, iga_ctx** out) {
   if (P.deflation == 2 && (P.precision != 0 || P.flexible != 0)) return IGA_E_INVALID;
   if (P.precond == 1 && P.n_lines > 0) return IGA_E_UNSUPPORTED;
   if (P.robin < 0 || P.robin > 1) return IGA_E_INVALID;
-  if (P.robin && (P.dim != 1 || P.precond == 1)) return IGA_E_UNSUPPORTED;
+  if (P.robin && (P.dim != 1 || P.n_lines > 0)) return IGA_E_UNSUPPORTED;     // 1D, constant k
   if (P.precision < 0 || P.precision > 1) return IGA_E_INVALID;
   if (P.arnoldi < 0 || P.arnoldi > 1) return IGA_E_INVALID;
   if (P.fused_vcycle < 0 || P.fused_vcycle > 1) return IGA_E_INVALID;
@@ -144,7 +144,6 @@ iga_status iga_setup(const iga_params* prm, iga_ctx** out) {
       break;
     }
     if (!P.skip_deflation && P.deflation != 0 && (s = setup_deflation(ctx)) != IGA_OK) break;
-    if (!P.skip_deflation && P.deflation != 0 && P.robin && (s = setup_robin_deflation(ctx)) != IGA_OK) break;
     if (P.precond == 1 && (s = setup_exact_cslp(ctx)) != IGA_OK) break;
     cudaError_t e = cudaStreamSynchronize(ctx->st);
     if (e != cudaSuccess) { s = set_err(ctx, IGA_E_CUDA, "setup: %s", cudaGetErrorString(e)); break; }

@@ -4,6 +4,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <string>
+#include <functional>
 #include <vector>
 
 #include "../../include/iga_helmholtz.h"
@@ -86,6 +87,22 @@ struct FdmData {
   int refine = 2;                    // FP64 iterative refinement steps per solve
 };
 
+// LU factors of a complex band matrix (half bandwidth b <= 5) in P row
+// partitions with spikes and the interface system (banded.cu)
+struct BandLU {
+  int n = 0, b = 0, s = 0, P = 0;
+  double2* lu = nullptr;             // [n][3b+1] U rows of the partition blocks, column c at (c - r + b)
+  double2* lm = nullptr;             // [n][b] multipliers of elimination step j (rows j+1 .. j+b)
+  double2* rdiag = nullptr;          // [n] 1 / U(r, r)
+  int* ipiv = nullptr;               // [n] pivot row of step j
+  double2* V = nullptr;              // [n][b] right spikes A_i^{-1} [0; B_i]
+  double2* Wl = nullptr;             // [n][b] left spikes A_i^{-1} [C_i; 0]
+  double2* y = nullptr;              // [n] partition solutions
+  int nr = 0, br = 0;                // interface system: 2 b P unknowns, half bandwidth 3b
+  double2 *rlu = nullptr, *rlm = nullptr, *rrdiag = nullptr, *rz = nullptr, *rz2 = nullptr;
+  int* ripiv = nullptr;
+};
+
 struct LevelData {
   int n_el = 0, nx = 0, ny = 1, n = 0;
   double* knots = nullptr;       // n_el + 2p + 1
@@ -133,23 +150,23 @@ struct iga_ctx {
   KFieldDev kf{};
   double k2const = 0.0;              // k^2 when constant
   double robin_k = 0.0;              // 1D Sommerfeld end at x = 1: the -i k N coefficient (0: none)
-  // rank-one correction of the deflation solve for the Sommerfeld term:
-  // E = E0 - i k u u^T, u = Z^T e_last; E^{-1} t = E0^{-1} t + g (u^T E0^{-1} t) E0^{-1} u
-  double2 sm_gamma{};                // i k / (1 - i k u^T E0^{-1} u)
-  double2* sm_w = nullptr;           // E0^{-1} u (m)
-  double2* sm_dot = nullptr;         // scratch for u^T s
-  int sm_j[2] = {-1, -1};            // the (at most two) non-zero entries of u
-  double sm_u[2] = {0.0, 0.0};
   double2 sig{};                     // beta1 - i beta2
   LevelData lv[IGA_MAX_LEVELS];
   int tile[IGA_MAX_LEVELS][2];       // operator tile shape per level and precision (-1: heuristic)
   cudaStream_t st = nullptr;
   int device = 0;
   int num_sms = 148;
-  // coarsest level dense inverse
+  // coarsest level: dense inverse, or (1D, more than IGA_MAX_COARSEST dofs) band LU
   int nc = 0;
   double2* cinv = nullptr;
   float2* cinvf = nullptr;
+  bool coarse_banded = false;
+  BandLU bandC;
+  double2* cband_t = nullptr;        // FP32 V-cycle: the coarse right-hand side and solution in FP64
+  double2* cband_x = nullptr;
+  // 1D: band LU of E (deflation) and of the finest M_beta (exact CSLP)
+  BandLU bandE;
+  BandLU bandX;
   // deflation (ADP)
   int mx = 0;
   size_t m = 0;
@@ -304,7 +321,10 @@ iga_status defl_q(iga_ctx* ctx, const double2* x, double2* y);            // y =
 iga_status defl_apply_T(iga_ctx* ctx, const double2* x, double2* y, double2* tmp1, double2* tmp2);
 // exact CSLP (constant k): z = M_beta^{-1} r on the finest level
 iga_status setup_exact_cslp(iga_ctx* ctx);
-iga_status setup_robin_deflation(iga_ctx* ctx);
+iga_status band_setup(iga_ctx* ctx, BandLU& F, const double2* Ab, int n, int b);
+iga_status band_solve(iga_ctx* ctx, const BandLU& F, const double2* t, double2* x);
+iga_status band_probe(iga_ctx* ctx, int n, int b, const std::function<iga_status(const double2*, double2*)>& apply,
+                      double2* x, double2* y, double2* Ab);
 iga_status setup_robin_dinv(iga_ctx* ctx);         // mg.cu
 iga_status cslp_exact_solve(iga_ctx* ctx, const double2* r, double2* z);
 // ecoarse.cu (variable k)

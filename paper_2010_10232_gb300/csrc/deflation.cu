@@ -553,6 +553,23 @@ static iga_status fdm_setup(iga_ctx* ctx) {
   return IGA_OK;
 }
 
+// 1D: E = Z^T A Z is a band matrix of half bandwidth (p + 4) / 2 (a Z column
+// covers at most five fine functions, A has half bandwidth p), whatever k(x)
+// and the boundary terms; its band is probed with 2 (p + 4) / 2 + 1
+// applications of Z^T A Z and factorised by the band solver.
+static iga_status setup_banded_E(iga_ctx* ctx) {
+  const int m = (int)ctx->m, bw = (ctx->p + 4) / 2;
+  double2* Ab = dalloc<double2>(ctx, (size_t)m * (2 * bw + 1));
+  if (!Ab) return set_err(ctx, IGA_E_OOM, "E band");
+  auto apply = [ctx](const double2* c, double2* e) -> iga_status {
+    TRY(defl_z(ctx, c, ctx->w0));
+    TRY(op_apply<double>(ctx, 0, OP_A, ctx->w0, ctx->w1, nullptr, EPI_Y, nullptr, 0.0));
+    return defl_zt(ctx, ctx->w1, e, nullptr);
+  };
+  TRY(band_probe(ctx, m, bw, apply, ctx->cs, ctx->cw, Ab));
+  return band_setup(ctx, ctx->bandE, Ab, m, bw);
+}
+
 iga_status setup_deflation(iga_ctx* ctx) {
   LevelData& L = ctx->lv[0];
   ctx->mx = L.nx / 2;
@@ -566,6 +583,7 @@ iga_status setup_deflation(iga_ctx* ctx) {
   ctx->ctf = dalloc<float2>(ctx, ctx->m);
   ctx->cef = dalloc<float2>(ctx, ctx->m);
   if (!ctx->ce1 || !ctx->ce2 || !ctx->ctf || !ctx->cef) return set_err(ctx, IGA_E_OOM, "deflation alloc");
+  if (ctx->dim == 1) return setup_banded_E(ctx);
   ctx->kc = dalloc<double>(ctx, (size_t)ctx->mx * ctx->mx);
   ctx->mc = dalloc<double>(ctx, (size_t)ctx->mx * ctx->mx);
   if (!ctx->ct || !ctx->cs || !ctx->cw || !ctx->kc || !ctx->mc) return set_err(ctx, IGA_E_OOM, "deflation alloc");
@@ -601,20 +619,13 @@ static iga_status fdm_solve32(iga_ctx* ctx, const FdmData& F, const double2* t, 
   const int mx = F.n;
   const float* V = F.Vf;
   const float* Vt = F.Vtf;
-  if (ctx->dim == 1) {
-    // s^T = ((t^T V) / d) V^T with t as a 1 x m row
-    launch_fdm_gemm<false, true, false>(ctx, V, t, F.w1, 1, mx, F.dinv);
-    if (accumulate) launch_fdm_gemm<false, false, true>(ctx, Vt, F.w1, s, 1, mx, nullptr);
-    else launch_fdm_gemm<false, false, false>(ctx, Vt, F.w1, s, 1, mx, nullptr);
-  } else {
-    // T1 = V^T T; T2 = T1 V / D; T3 = V T2; S = T3 V^T (or s += S)
-    if (tf) launch_fdm_gemm<true, false, false>(ctx, Vt, tf, F.w1, mx, mx, nullptr);
-    else launch_fdm_gemm<true, false, false>(ctx, Vt, t, F.w1, mx, mx, nullptr);
-    launch_fdm_gemm<false, true, false>(ctx, V, F.w1, F.w2, mx, mx, F.dinv);
-    launch_fdm_gemm<true, false, false>(ctx, V, F.w2, F.w1, mx, mx, nullptr);
-    if (accumulate) launch_fdm_gemm<false, false, true>(ctx, Vt, F.w1, s, mx, mx, nullptr);
-    else launch_fdm_gemm<false, false, false>(ctx, Vt, F.w1, s, mx, mx, nullptr);
-  }
+  // (2D) T1 = V^T T; T2 = T1 V / D; T3 = V T2; S = T3 V^T (or s += S)
+  if (tf) launch_fdm_gemm<true, false, false>(ctx, Vt, tf, F.w1, mx, mx, nullptr);
+  else launch_fdm_gemm<true, false, false>(ctx, Vt, t, F.w1, mx, mx, nullptr);
+  launch_fdm_gemm<false, true, false>(ctx, V, F.w1, F.w2, mx, mx, F.dinv);
+  launch_fdm_gemm<true, false, false>(ctx, V, F.w2, F.w1, mx, mx, nullptr);
+  if (accumulate) launch_fdm_gemm<false, false, true>(ctx, Vt, F.w1, s, mx, mx, nullptr);
+  else launch_fdm_gemm<false, false, false>(ctx, Vt, F.w1, s, mx, mx, nullptr);
   CKL();
   return IGA_OK;
 }
@@ -628,80 +639,21 @@ static iga_status fdm_solve32(iga_ctx* ctx, const FdmData& F, const double2* t, 
 static iga_status e0_solve(iga_ctx* ctx, const double2* t, double2* s, const float2* tf) {
   TRY(fdm_solve32(ctx, ctx->fdmE, t, s, false, tf));
   const int bw = (ctx->p + 4) / 2;
-  const int my = ctx->dim == 2 ? ctx->mx : 1;
   for (int it = 0; it < ctx->fdmE.refine; ++it) {
-    TRY(op_apply_bands(ctx, bw, ctx->mx, my, ctx->kcb, ctx->mcb, make_double2(-ctx->k2const, 0.0), s, ctx->ce1, t,
-                       EPI_ZMINUS, ctx->dim == 2 ? ctx->cef : nullptr));
-    TRY(fdm_solve32(ctx, ctx->fdmE, ctx->ce1, s, true, ctx->dim == 2 ? ctx->cef : nullptr));   // s += FDM(r)
+    TRY(op_apply_bands(ctx, bw, ctx->mx, ctx->mx, ctx->kcb, ctx->mcb, make_double2(-ctx->k2const, 0.0), s, ctx->ce1,
+                       t, EPI_ZMINUS, ctx->cef));
+    TRY(fdm_solve32(ctx, ctx->fdmE, ctx->ce1, s, true, ctx->cef));   // s += FDM(r)
   }
   CKL();
   return IGA_OK;
 }
 
-// u^T s over the (at most two) entries of u = Z^T e_last
-__global__ void k_sm_dot(const double2* s, int j0, double u0, int j1, double u1, double2* dot) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double2 d = make_double2(0.0, 0.0);
-  if (j0 >= 0) d = d + u0 * s[j0];
-  if (j1 >= 0) d = d + u1 * s[j1];
-  *dot = d;
-}
-// s += g (u^T s) w
-__global__ void k_sm_axpy(double2* s, int m, double2 g, const double2* dot, const double2* w) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= m) return;
-  const double2 c = cmul(g, *dot);
-  s[i] = s[i] + cmul(c, w[i]);
-}
-
-// s = E^{-1} t.  Constant k: e0_solve, and with a Sommerfeld end the
-// rank-one correction of the boundary term (Sherman-Morrison):
-// E = E0 - i k u u^T  =>  E^{-1} t = s0 + g (u^T s0) E0^{-1} u,  s0 = E0^{-1} t,
-// g = i k / (1 - i k u^T E0^{-1} u).  Variable k: block LU.
+// s = E^{-1} t.  2D: constant k by fast diagonalisation (e0_solve), variable
+// k by block LU; 1D: the band solver.
 iga_status defl_esolve(iga_ctx* ctx, const double2* t, double2* s, const float2* tf) {
+  if (ctx->dim == 1) return band_solve(ctx, ctx->bandE, t, s);
   if (ctx->vark) return block_E_solve(ctx, t, s);
-  TRY(e0_solve(ctx, t, s, tf));
-  if (ctx->sm_w) {
-    const int m = (int)ctx->m;
-    k_sm_dot<<<1, 32, 0, ctx->st>>>(s, ctx->sm_j[0], ctx->sm_u[0], ctx->sm_j[1], ctx->sm_u[1], ctx->sm_dot); iga_count_launch();
-    k_sm_axpy<<<cdiv(m, 256), 256, 0, ctx->st>>>(s, m, ctx->sm_gamma, ctx->sm_dot, ctx->sm_w); iga_count_launch();
-    CKL();
-  }
-  return IGA_OK;
-}
-
-// Setup of the rank-one correction (1D, Sommerfeld end at x = 1): u = Z^T e_last
-// is the last row of Z (coarse m_x gets (6 - eps)/8 and m_x - 1 gets 1/8 when
-// n_x is even; m_x gets 1/2 when n_x is odd; 1-based), w = E0^{-1} u.
-iga_status setup_robin_deflation(iga_ctx* ctx) {
-  if (ctx->robin_k == 0.0 || ctx->vark || ctx->dim != 1) return IGA_OK;
-  const int nx = ctx->lv[0].nx, m = (int)ctx->m;
-  const double eps = ctx->prm.eps;
-  if (nx % 2 == 0) {
-    ctx->sm_j[0] = m - 1; ctx->sm_u[0] = (6.0 - eps) / 8.0;
-    if (m >= 2) { ctx->sm_j[1] = m - 2; ctx->sm_u[1] = 1.0 / 8.0; }
-  } else {
-    ctx->sm_j[0] = m - 1; ctx->sm_u[0] = 0.5;
-  }
-  std::vector<double2> hu((size_t)m, make_double2(0.0, 0.0));
-  for (int q = 0; q < 2; ++q)
-    if (ctx->sm_j[q] >= 0) hu[ctx->sm_j[q]] = make_double2(ctx->sm_u[q], 0.0);
-  double2* u = dalloc<double2>(ctx, m);
-  ctx->sm_w = dalloc<double2>(ctx, m);
-  ctx->sm_dot = dalloc<double2>(ctx, 1);
-  if (!u || !ctx->sm_w || !ctx->sm_dot) return set_err(ctx, IGA_E_OOM, "robin deflation");
-  CK(cudaMemcpyAsync(u, hu.data(), sizeof(double2) * m, cudaMemcpyHostToDevice, ctx->st));
-  TRY(e0_solve(ctx, u, ctx->sm_w, nullptr));
-  double2 hw[2] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
-  for (int q = 0; q < 2; ++q)
-    if (ctx->sm_j[q] >= 0) CK(cudaMemcpyAsync(&hw[q], ctx->sm_w + ctx->sm_j[q], sizeof(double2), cudaMemcpyDeviceToHost, ctx->st));
-  CK(cudaStreamSynchronize(ctx->st));
-  double2 uw = make_double2(0.0, 0.0);
-  for (int q = 0; q < 2; ++q) uw = uw + ctx->sm_u[q] * hw[q];
-  const double2 ik = make_double2(0.0, ctx->robin_k);
-  const double2 den = make_double2(1.0, 0.0) - cmul(ik, uw);
-  ctx->sm_gamma = cmul(ik, cinv(den));
-  return IGA_OK;
+  return e0_solve(ctx, t, s, tf);
 }
 
 // y = Q x = Z E^{-1} Z^T x
@@ -734,8 +686,9 @@ iga_status defl_apply_T(iga_ctx* ctx, const double2* x, double2* y, double2* tmp
 }
 
 // ------------------------------------------------------------------ exact CSLP (C_ex)
-// The finest-level CSLP matrix M_beta = K (x) M + M (x) K - sigma k^2 M (x) M
-// (constant k) is a tensor-product operator like E, so it is inverted by the
+// 1D: the band solver.  2D: the finest-level CSLP matrix
+// M_beta = K (x) M + M (x) K - sigma k^2 M (x) M (constant k) is a
+// tensor-product operator like E, so it is inverted by the
 // same fast diagonalisation: the 1D pencil of the fine band matrices, complex
 // denominators 1 / (lam_i + lam_j - sigma k^2), FP32 transforms and FP64
 // iterative refinement whose residual r = t - M_beta s is the FP64 operator
@@ -743,8 +696,19 @@ iga_status defl_apply_T(iga_ctx* ctx, const double2* x, double2* y, double2* tmp
 constexpr int EXACT_CSLP_MAX_N = 2048;
 
 iga_status setup_exact_cslp(iga_ctx* ctx) {
-  if (ctx->vark) return set_err(ctx, IGA_E_UNSUPPORTED, "exact CSLP: constant k only");
   const LevelData& L = ctx->lv[0];
+  if (ctx->dim == 1) {
+    // 1D: M_beta (any k(x), with the Sommerfeld term where present) is a band
+    // matrix of half bandwidth p; probed and factorised by the band solver
+    double2* Ab = dalloc<double2>(ctx, (size_t)L.n * (2 * ctx->p + 1));
+    if (!Ab) return set_err(ctx, IGA_E_OOM, "exact CSLP band");
+    auto apply = [ctx](const double2* x, double2* y) -> iga_status {
+      return op_apply<double>(ctx, 0, OP_MB, x, y, nullptr, EPI_Y, nullptr, 0.0);
+    };
+    TRY(band_probe(ctx, L.n, ctx->p, apply, ctx->w0, ctx->w1, Ab));
+    return band_setup(ctx, ctx->bandX, Ab, L.n, ctx->p);
+  }
+  if (ctx->vark) return set_err(ctx, IGA_E_UNSUPPORTED, "exact CSLP in 2D: constant k only");
   const int n = L.nx, p = ctx->p;
   if (n > EXACT_CSLP_MAX_N)
     return set_err(ctx, IGA_E_UNSUPPORTED, "exact CSLP: n_x = %d above %d (dense 1D eigenvectors)", n, EXACT_CSLP_MAX_N);
@@ -763,6 +727,7 @@ iga_status setup_exact_cslp(iga_ctx* ctx) {
 
 // z = M_beta^{-1} r (finest level) to FP64 accuracy
 iga_status cslp_exact_solve(iga_ctx* ctx, const double2* r, double2* z) {
+  if (ctx->dim == 1) return band_solve(ctx, ctx->bandX, r, z);
   TRY(fdm_solve32(ctx, ctx->fdmC, r, z, false, nullptr));
   for (int it = 0; it < ctx->fdmC.refine; ++it) {
     TRY(op_apply<double>(ctx, 0, OP_MB, z, ctx->cxr, r, EPI_ZMINUS, nullptr, 0.0));

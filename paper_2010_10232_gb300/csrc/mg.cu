@@ -2,7 +2,8 @@
 // omega = 0.6; Section 4.2: V-cycle with coarse correction between nested
 // spline spaces).  Transfers are knot insertion (B-spline refinement), whose
 // p = 1 case is the paper's linear interpolation; restriction is its
-// transpose.  The coarsest level is solved with a dense inverse built at setup.
+// transpose.  The coarsest level is solved with a dense inverse built at setup
+// (1D above IGA_MAX_COARSEST dofs: the band solver of banded.cu).
 #include "common.cuh"
 #include <algorithm>
 #include <vector>
@@ -433,6 +434,20 @@ iga_status setup_coarse_inverse(iga_ctx* ctx) {
   LevelData& L = ctx->lv[l];
   int n = L.n;
   ctx->nc = n;
+  if (n > IGA_MAX_COARSEST && ctx->dim == 1) {
+    // 1D: M_beta is a band matrix (half bandwidth p); probe its band and
+    // factorise it with the band solver
+    ctx->coarse_banded = true;
+    double2* Ab = dalloc<double2>(ctx, (size_t)n * (2 * ctx->p + 1));
+    ctx->cband_t = dalloc<double2>(ctx, n);
+    ctx->cband_x = dalloc<double2>(ctx, n);
+    if (!Ab || !ctx->cband_t || !ctx->cband_x) return set_err(ctx, IGA_E_OOM, "coarse band alloc");
+    auto apply = [ctx, l](const double2* x, double2* y) -> iga_status {
+      return op_apply<double>(ctx, l, OP_MB, x, y, nullptr, EPI_Y, nullptr, 0.0);
+    };
+    TRY(band_probe(ctx, n, ctx->p, apply, L.vx, L.vy, Ab));
+    return band_setup(ctx, ctx->bandC, Ab, n, ctx->p);
+  }
   // one block inverts the coarsest matrix (a row of it in shared memory)
   if (n > IGA_MAX_COARSEST)
     return set_err(ctx, IGA_E_INVALID,
@@ -623,6 +638,16 @@ iga_status mg_prolong_add(iga_ctx* ctx, int l, const typename cplx<T>::t* c, typ
 template <typename T>
 iga_status mg_coarse(iga_ctx* ctx, const typename cplx<T>::t* b, typename cplx<T>::t* x) {
   using C = typename cplx<T>::t;
+  if (ctx->coarse_banded) {
+    if constexpr (sizeof(T) == 8) return band_solve(ctx, ctx->bandC, b, x);
+    else {
+      launch_convert_f2d(b, ctx->cband_t, ctx->nc, ctx->st);
+      TRY(band_solve(ctx, ctx->bandC, ctx->cband_t, ctx->cband_x));
+      launch_convert_d2f(ctx->cband_x, x, ctx->nc, ctx->st);
+      CKL();
+      return IGA_OK;
+    }
+  }
   k_dense_mv<C><<<cdiv(ctx->nc, 8), 256, 0, ctx->st>>>(ctx->nc, LvBuf<T>::cinv(ctx), b, x); iga_count_launch();
   CKL();
   return IGA_OK;

@@ -14,10 +14,12 @@
 //     x_i = y_i - V_i top(x_{i+1}) - W_i bot(x_{i-1}),
 // top/bot = first/last b entries; evaluated at the partition ends this is a
 // band system of size 2 b P (half bandwidth 3 b) for the interface values,
-// factorised the same way as one partition.  A solve is: a thread per
+// factorised the same way as one partition.  A solve is: a warp per
 // partition for y (forward and back substitution with register windows), one
-// thread for the interface system, and a thread per row for x.  Sequential
-// depth ~ 2 (s + 2 b P) steps with s ~ sqrt(2 b n); setup runs on the device.
+// warp for the interface system, and a thread per row for x.  Sequential
+// depth ~ 2 (s + 2 b P) steps with s ~ sqrt(2 b n), each step reading its
+// coefficients from shared memory (staged chunk by chunk with cp.async);
+// setup runs on the device.
 #include "common.cuh"
 
 #include <cmath>
@@ -151,70 +153,164 @@ __global__ void k_band_reduced(int n, int b, int s, int P, const double2* V, con
   }
 }
 
-// y = A_i^{-1} t for every partition (thread per partition) with register
-// windows: the forward sweep keeps rows j .. j+b, the back sweep the last 2b
-// solution values.  BM >= b.  t, y and rz must not overlap (the loops are
-// unrolled so that the coefficient and right-hand-side loads of several
-// steps are in flight together).  rz (optional): the partition's first and
-// last b solution values, as the interface system's right-hand side.
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void cpa16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cpa4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cpa_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// rows of coefficients staged per chunk (two chunks in flight per warp)
+__host__ __device__ constexpr int band_chunk(int b) { return b <= 5 ? 128 : 64; }
+__host__ __device__ constexpr size_t band_smem(int b) {
+  return 2 * ((size_t)band_chunk(b) * (2 * b + 2) * sizeof(double2) + (size_t)band_chunk(b) * sizeof(int));
+}
+
+// y = A_i^{-1} t for every partition: one warp per partition (one warp per
+// block).  The 32 lanes copy the next chunk of the partition's coefficient
+// rows (multipliers, pivots and entering right-hand sides for the forward
+// sweep; U rows, 1/U(r,r) and forward results for the back sweep) into shared
+// memory with cp.async while lane 0 runs the sequential recurrence on the
+// current chunk with register windows (forward: rows j .. j+b; back: the last
+// 2b solution values).  BM >= b.  t, y and rz must not overlap.  rz
+// (optional): the partition's first and last b solution values, as the
+// interface system's right-hand side.
 template <int BM>
-__global__ void k_band_solve_local(int n, int b, int s, int P, const double2* __restrict__ lu,
-                                   const double2* __restrict__ lm, const double2* __restrict__ rdiag,
-                                   const int* __restrict__ ipiv, const double2* __restrict__ t,
-                                   double2* __restrict__ y, double2* __restrict__ rz) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(32) k_band_solve_local(int n, int b, int s, int P, const double2* __restrict__ lu,
+                                                         const double2* __restrict__ lm,
+                                                         const double2* __restrict__ rdiag,
+                                                         const int* __restrict__ ipiv, const double2* __restrict__ t,
+                                                         double2* __restrict__ y, double2* __restrict__ rz) {
+  const int i = blockIdx.x, lane = threadIdx.x;
   if (i >= P) return;
   int r0, r1;
   part_rows(i, n, s, P, r0, r1);
-  const int len = r1 - r0, W = 3 * b + 1;
+  const int len = r1 - r0, W = 3 * b + 1, CH = band_chunk(b);
+  extern __shared__ __align__(16) unsigned char band_sm[];
+  // buffer q: A [CH][2b] complex, B [CH], C [CH] complex, I [CH] int
+  const size_t buf_bytes = (size_t)CH * (2 * b + 2) * sizeof(double2) + (size_t)CH * sizeof(int);
+  auto bufA = [&](int q) { return reinterpret_cast<double2*>(band_sm + q * buf_bytes); };
+  auto bufB = [&](int q) { return bufA(q) + (size_t)CH * 2 * b; };
+  auto bufC = [&](int q) { return bufB(q) + CH; };
+  auto bufI = [&](int q) { return reinterpret_cast<int*>(bufC(q) + CH); };
+  const int nch = (len + CH - 1) / CH;
+
+  // ---- forward sweep: chunk c = rows j0 .. j0 + CH - 1
+  auto load_fwd = [&](int c, int q) {
+    const int j0 = c * CH, rows = min(CH, len - j0);
+    double2* A = bufA(q);
+    for (int e = lane; e < rows * b; e += 32) cpa16(A + e, lm + (size_t)(r0 + j0) * b + e);
+    double2* Bv = bufB(q);
+    for (int e = lane; e < rows; e += 32) {
+      const int idx = j0 + e + b + 1;
+      if (idx < len) cpa16(Bv + e, t + r0 + idx);
+    }
+    int* I = bufI(q);
+    for (int e = lane; e < rows; e += 32) cpa4(I + e, ipiv + r0 + j0 + e);
+  };
   double2 w[BM + 1];
 #pragma unroll
-  for (int q = 0; q <= BM; ++q) w[q] = (q <= b && q < len) ? t[r0 + q] : bz();
-#pragma unroll 4
-  for (int j = 0; j < len; ++j) {
-    const int g = r0 + j;
-    const int pj = ipiv[g] - g;
-    // interchange rows j and ipiv[j] of the window (selects, no indexing)
-    const double2 w0 = w[0];
-    double2 sel = w0;
+  for (int q = 0; q <= BM; ++q) w[q] = (lane == 0 && q <= b && q < len) ? t[r0 + q] : bz();
+  load_fwd(0, 0);
+  cpa_commit();
+  for (int c = 0; c < nch; ++c) {
+    if (c + 1 < nch) load_fwd(c + 1, (c + 1) & 1);
+    cpa_commit();
+    cpa_wait1();
+    __syncwarp();
+    if (lane == 0) {
+      const int j0 = c * CH, rows = min(CH, len - j0);
+      const double2* A = bufA(c & 1);
+      const double2* Bv = bufB(c & 1);
+      const int* I = bufI(c & 1);
+      for (int jj = 0; jj < rows; ++jj) {
+        const int j = j0 + jj, g = r0 + j;
+        const int pj = I[jj] - g;
+        const double2 w0 = w[0];
+        double2 sel = w0;
 #pragma unroll
-    for (int q = 1; q <= BM; ++q) {
-      const bool hit = q == pj;
-      const double2 wq = w[q];
-      sel = hit ? wq : sel;
-      w[q] = hit ? w0 : wq;
+        for (int q = 1; q <= BM; ++q) {           // interchange rows j and ipiv[j] (selects, no indexing)
+          const bool hit = q == pj;
+          const double2 wq = w[q];
+          sel = hit ? wq : sel;
+          w[q] = hit ? w0 : wq;
+        }
+        w[0] = sel;
+        y[g] = sel;
+#pragma unroll
+        for (int q = 1; q <= BM; ++q)
+          if (q <= b) w[q] = w[q] - cmul(A[jj * b + q - 1], sel);
+#pragma unroll
+        for (int q = 0; q < BM; ++q) w[q] = w[q + 1];
+        w[BM] = bz();
+        const double2 tn = (j + 1 + b < len) ? Bv[jj] : bz();
+#pragma unroll
+        for (int q = 0; q <= BM; ++q) w[q] = q == b ? tn : w[q];
+      }
     }
-    w[0] = sel;
-    y[g] = w[0];
-#pragma unroll
-    for (int q = 1; q <= BM; ++q)
-      if (q <= b) w[q] = w[q] - cmul(lm[(size_t)g * b + q - 1], w[0]);
-#pragma unroll
-    for (int q = 0; q < BM; ++q) w[q] = w[q + 1];
-    w[BM] = bz();
-    const int nxt = j + 1 + b;
-    const double2 tn = nxt < len ? t[r0 + nxt] : bz();
-#pragma unroll
-    for (int q = 0; q <= BM; ++q) w[q] = q == b ? tn : w[q];
+    __syncwarp();                                  // the buffer is refilled two chunks later
   }
+  // forward results are read back by every lane's copies
+  if (lane == 0) __threadfence();
+  __syncwarp();
+
+  // ---- back sweep: chunk c = rows jlo .. jhi, taken from the end
+  auto back_range = [&](int c, int& jlo, int& rows) {
+    const int jhi = len - c * CH - 1;
+    jlo = max(0, jhi - CH + 1);
+    rows = jhi - jlo + 1;
+  };
+  auto load_back = [&](int c, int q) {
+    int jlo, rows;
+    back_range(c, jlo, rows);
+    double2* A = bufA(q);
+    for (int e = lane; e < rows * 2 * b; e += 32) {
+      const int row = e / (2 * b), qq = e - row * 2 * b;
+      cpa16(A + e, lu + (size_t)(r0 + jlo + row) * W + b + 1 + qq);
+    }
+    double2* Bv = bufB(q);
+    double2* Cv = bufC(q);
+    for (int e = lane; e < rows; e += 32) {
+      cpa16(Bv + e, rdiag + r0 + jlo + e);
+      cpa16(Cv + e, y + r0 + jlo + e);
+    }
+  };
   double2 x[2 * BM];
 #pragma unroll
   for (int q = 0; q < 2 * BM; ++q) x[q] = bz();
-#pragma unroll 4
-  for (int j = len - 1; j >= 0; --j) {
-    const int g = r0 + j;
-    double2 acc = y[g];
-    const double2* urow = lu + (size_t)g * W + b + 1;
+  load_back(0, 0);
+  cpa_commit();
+  for (int c = 0; c < nch; ++c) {
+    if (c + 1 < nch) load_back(c + 1, (c + 1) & 1);
+    cpa_commit();
+    cpa_wait1();
+    __syncwarp();
+    if (lane == 0) {
+      int jlo, rows;
+      back_range(c, jlo, rows);
+      const double2* A = bufA(c & 1);
+      const double2* Bv = bufB(c & 1);
+      const double2* Cv = bufC(c & 1);
+      for (int jj = rows - 1; jj >= 0; --jj) {
+        double2 a0 = Cv[jj], a1 = bz();            // two partial sums shorten the dependent chain
 #pragma unroll
-    for (int q = 0; q < 2 * BM; ++q)
-      if (q < 2 * b) acc = acc - cmul(urow[q], x[q]);
-    const double2 xj = cmul(acc, rdiag[g]);
+        for (int q = 0; q < 2 * BM; q += 2) {
+          if (q < 2 * b) a0 = a0 - cmul(A[jj * 2 * b + q], x[q]);
+          if (q + 1 < 2 * b) a1 = a1 - cmul(A[jj * 2 * b + q + 1], x[q + 1]);
+        }
+        const double2 xj = cmul(a0 + a1, Bv[jj]);
 #pragma unroll
-    for (int q = 2 * BM - 1; q > 0; --q) x[q] = x[q - 1];
-    x[0] = xj;
-    y[g] = xj;
+        for (int q = 2 * BM - 1; q > 0; --q) x[q] = x[q - 1];
+        x[0] = xj;
+        y[r0 + jlo + jj] = xj;
+      }
+    }
+    __syncwarp();
   }
-  if (rz)
+  if (rz && lane == 0)
     for (int a = 0; a < b; ++a) {
       rz[2 * b * i + a] = y[r0 + a];
       rz[2 * b * i + b + a] = y[r1 - b + a];
@@ -252,11 +348,33 @@ __global__ void k_probe_scatter(const double2* y, int n, int b, int c, double2* 
 
 // forward and back substitution of every partition (b <= 5: the matrices;
 // b <= 15: the interface system, half bandwidth 3b)
+template <int BM>
+void launch_local(int n, int b, int s, int P, const double2* lu, const double2* lm, const double2* rdiag,
+                  const int* ipiv, const double2* t, double2* y, double2* rz, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_band_solve_local<BM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)band_smem(BM));
+    attr = true;
+  }
+  k_band_solve_local<BM><<<P, 32, band_smem(b), st>>>(n, b, s, P, lu, lm, rdiag, ipiv, t, y, rz);
+  iga_count_launch();
+}
+
+// forward and back substitution of every partition with the narrowest window
+// that holds b (b <= 5: the matrices; 3, 6, 9, 12, 15: interface systems)
 void solve_parts(int n, int b, int s, int P, const double2* lu, const double2* lm, const double2* rdiag,
                  const int* ipiv, const double2* t, double2* y, double2* rz, cudaStream_t st) {
-  if (b <= 5) k_band_solve_local<5><<<cdiv(P, 32), 32, 0, st>>>(n, b, s, P, lu, lm, rdiag, ipiv, t, y, rz);
-  else k_band_solve_local<15><<<cdiv(P, 32), 32, 0, st>>>(n, b, s, P, lu, lm, rdiag, ipiv, t, y, rz);
-  iga_count_launch();
+  switch (b) {
+    case 1: launch_local<1>(n, b, s, P, lu, lm, rdiag, ipiv, t, y, rz, st); break;
+    case 2: launch_local<2>(n, b, s, P, lu, lm, rdiag, ipiv, t, y, rz, st); break;
+    case 3: launch_local<3>(n, b, s, P, lu, lm, rdiag, ipiv, t, y, rz, st); break;
+    case 4: launch_local<4>(n, b, s, P, lu, lm, rdiag, ipiv, t, y, rz, st); break;
+    case 5: launch_local<5>(n, b, s, P, lu, lm, rdiag, ipiv, t, y, rz, st); break;
+    case 6: launch_local<6>(n, b, s, P, lu, lm, rdiag, ipiv, t, y, rz, st); break;
+    case 9: launch_local<9>(n, b, s, P, lu, lm, rdiag, ipiv, t, y, rz, st); break;
+    case 12: launch_local<12>(n, b, s, P, lu, lm, rdiag, ipiv, t, y, rz, st); break;
+    default: launch_local<15>(n, b, s, P, lu, lm, rdiag, ipiv, t, y, rz, st); break;
+  }
 }
 
 }  // namespace

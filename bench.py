@@ -720,7 +720,7 @@ def other_configs(stream, flush):
     try:
         rows = {}
         t0 = time.perf_counter()
-        h5 = Helmholtz(dim=2, p=3, n_el=1280, kfield=800.0)
+        h5 = from_problem(W.config5())
         setup_s = time.perf_counter() - t0
         f5 = h5.point_source(0.5, 0.5)
         xt = h5.vec()
@@ -732,7 +732,7 @@ def other_configs(stream, flush):
         rows["plain_fp64"] = {"setup_s": setup_s, "ms": ms, "iterations": it, "true_res": tr,
                               "rel_gap_to_fp64_tol1e-12": _rel(xx.cpu().numpy(), tight)}
         del h5
-        h5m = Helmholtz(dim=2, p=3, n_el=1280, kfield=800.0, precision=1)
+        h5m = from_problem(W.config5(), precision=1)
         for name, nn in (("mixed_fp32_vcycle", None), ("learned_correction", _load_net())):
             if nn is not None:
                 h5m.attach(nn[0], nn[1])
@@ -767,18 +767,20 @@ def scaling_1d(stream, flush):
     (up to ~800 000 unknowns), C_ex and coarsest levels above 2048 dofs are
     solved by the band solver."""
     import torch
-    from paper_2010_10232_gb300.solver import Helmholtz
+    import workloads as W
+    from paper_2010_10232_gb300.solver import from_problem
     gold = json.load(open(os.path.join(ROOT, "tests", "golden", "table2_3_mp1b_iterations.json")))
     forms = (("DC1", dict(beta=(1.0, 1.0)), "dc1"), ("D", dict(n_vcycles=0), "d"), ("C_ex", None, "cex"))
     rows = {}
     for k in (1e4, 1e5, 1e6):
         for p in (1, 2, 3, 4, 5):
-            n_el = int(round(k / 0.625))
+            pr = W.mp1b(k, p)
+            n_el = pr.n_el
             for name, kw, gkey in forms:
                 if kw is None:
                     kw = dict(precond=1, deflation=0, beta=(1.0, 1.0 / k))
                 t0 = time.perf_counter()
-                h = Helmholtz(dim=1, p=p, n_el=n_el, kfield=k, **kw)
+                h = from_problem(pr, **kw)
                 setup_s = time.perf_counter() - t0
                 f = h.point_source(0.5)
                 xx = h.vec()

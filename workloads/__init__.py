@@ -156,6 +156,23 @@ def config4(n_instances: int = 64) -> list[tuple[Problem, int]]:
     return out
 
 
+def config5(layered: bool = False) -> Problem:
+    """2D, p = 3, 1280 x 1280 elements (1 640 961 dofs), centre point source:
+    constant k = 800 (kh = 0.625), or the three-layer field scaled so that its
+    largest value is 800 (k = 320 / 480 / 800)."""
+    kf = three_layer_field(800.0 / 250.0) if layered else constant_k(800.0)
+    return Problem(dim=2, p=3, n_el=1280, kfield=kf, sources=[(0.5, 0.5)],
+                   name=f"cfg5_2d_{'layers' if layered else 'k800'}_p3_nel1280")
+
+
+def mp1b(k: float, p: int, n_el: int | None = None) -> Problem:
+    """MP 1-B (Section 2.1): 1D, Dirichlet at both ends, point source at x = 1/2;
+    n_el = k / 0.625 unless given (Section 4.3.1 scales k to 10^6)."""
+    n_el = n_el or int(round(k / KH))
+    return Problem(dim=1, p=p, n_el=n_el, kfield=constant_k(k), sources=[(0.5,)],
+                   name=f"mp1b_k{k:g}_p{p}_nel{n_el}")
+
+
 def small_2d(n_el: int = 16, p: int = 2, k: float = 10.0, layered: bool = False) -> Problem:
     """Small 2D case for parity tests (spans several tiles and a ragged tail)."""
     kf = three_layer_field(k / 100.0) if layered else constant_k(k)

@@ -127,6 +127,13 @@ struct LevelData {
   float* Pwf = nullptr; float* Rwf = nullptr;
   float* k2qf = nullptr;                      // (unused unless variable k) reserved
   int vc_fmax = 0, vc_cmax = 0;               // fused V-cycle: fine footprint / coarse patch bounds
+  // uniform-knot interior of the restriction table to the next level (host
+  // copy, 2D tiled transfers): coarse rows j in [rj0, rj1] have
+  // Rlo[j] = 2j + roff and the weights r
+  struct {
+    double r[8] = {};
+    int roff = 0, rj0 = 0, rj1 = -1;
+  } tst;
   int tr_fmax = 0, tp_cmax = 0;               // tiled 2D transfers (0: per-point kernels)
   // variable k: inverse diagonal of M_beta
   double2* dinv = nullptr;

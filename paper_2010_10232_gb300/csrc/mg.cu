@@ -6,6 +6,7 @@
 // (1D above IGA_MAX_COARSEST dofs: the band solver of banded.cu).
 #include "common.cuh"
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 // ------------------------------------------------------------------ kernels
@@ -158,13 +159,34 @@ __host__ __device__ inline size_t tr_smem(int fmax, int wR) {
   return sizeof(C) * ((size_t)fmax * fmax + (size_t)fmax * TR_CT) + sizeof(T) * 2 * TR_CT * wR + sizeof(int) * 2 * TR_CT;
 }
 
-// c = R f on a coarse TR_CT^2 tile; with xc also xc = omega D_c^{-1} c
+// Interior stencil of the restriction table, passed by value (kernel
+// parameter space): weights r with Rlo[j] = 2j + roff for coarse j in
+// [rj0, rj1] (valid = 0: tables only)
+template <typename T> struct TrStencil {
+  T r[8];
+  int roff, rj0, rj1, valid;
+};
+
 template <typename T>
+static TrStencil<T> tr_stencil(const LevelData& F) {
+  TrStencil<T> st{};
+  for (int t = 0; t < 8; ++t) st.r[t] = (T)F.tst.r[t];
+  st.roff = F.tst.roff; st.rj0 = F.tst.rj0; st.rj1 = F.tst.rj1;
+  st.valid = F.tst.rj1 >= F.tst.rj0;
+  return st;
+}
+
+// c = R f on a coarse TR_CT^2 tile; with xc also xc = omega D_c^{-1} c.
+// WR > 0 (= wR): tiles whose coarse columns (rows) lie in the stencil's
+// interior range make the x (y) pass with the interior weights from the
+// parameter space and fixed offsets (no weight loads, no bounds tests).
+template <typename T, int WR>
 __global__ void __launch_bounds__(256) k_restrict_tiled(int nxf, int nyf, int nxc, int nyc, int wR, const T* Rw,
                                                         const int* Rlo, int fmax, const typename cplx<T>::t* f,
                                                         typename cplx<T>::t* c, typename cplx<T>::t* xc,
                                                         const typename cplx<T>::t* dinv, T omega, int p,
-                                                        const T* Kc, const T* Mc, typename cplx<T>::t cm) {
+                                                        const T* Kc, const T* Mc, typename cplx<T>::t cm,
+                                                        TrStencil<T> st) {
   using C = typename cplx<T>::t;
   extern __shared__ __align__(16) unsigned char rsm[];
   C* fs = reinterpret_cast<C*>(rsm);                 // [FY][FX] fine footprint
@@ -180,10 +202,15 @@ __global__ void __launch_bounds__(256) k_restrict_tiled(int nxf, int nyf, int nx
   const int fy0 = max(0, Rlo[cy0]), fy1 = min(nyf, Rlo[cy0 + cyn - 1] + wR);
   const int FX = fx1 - fx0, FY = fy1 - fy0;
   if (FX > fmax || FY > fmax || FX < 1 || FY < 1) return;   // cannot happen: fmax is the maximum over tiles
+  const float rFX = 1.0f / (float)FX;
   for (int i = tid; i < FY * FX; i += 256) {         // flat over the footprint (measured faster than warp rows)
-    const int r = i / FX, q = i - r * FX;
+    // i / FX without a division: (i + 1/2) / FX is at least 1/(2 FX) away from
+    // an integer, far above the float rounding of the product (FX, FY < 2^8)
+    const int r = __float2int_rz(((float)i + 0.5f) * rFX), q = i - r * FX;
     fs[i] = f[(size_t)(fy0 + r) * nxf + fx0 + q];
   }
+  const bool xin = WR > 0 && st.valid && cx0 >= st.rj0 && cx0 + cxn - 1 <= st.rj1;
+  const bool yin = WR > 0 && st.valid && cy0 >= st.rj0 && cy0 + cyn - 1 <= st.rj1;
   for (int i = tid; i < cxn * wR; i += 256) Rwx[i] = Rw[(size_t)cx0 * wR + i];
   for (int i = tid; i < cyn * wR; i += 256) Rwy[i] = Rw[(size_t)cy0 * wR + i];
   if (tid < cxn) Rlox[tid] = Rlo[cx0 + tid] - fx0;
@@ -192,14 +219,25 @@ __global__ void __launch_bounds__(256) k_restrict_tiled(int nxf, int nyf, int nx
   {
     const int jx = tid & (TR_CT - 1);                // a thread per coarse column and every 16th row
     if (jx < cxn) {
-      for (int r = tid / TR_CT; r < FY; r += 256 / TR_CT) {
-        C acc = czero<C>();
-        for (int t = 0; t < wR; ++t) {
-          const T w = Rwx[jx * wR + t];
-          const int q = Rlox[jx] + t;
-          if (w != (T)0 && q >= 0 && q < FX) acc = cfma(w, fs[r * FX + q], acc);
+      if (xin) {
+        const int q0 = 2 * (cx0 + jx) + st.roff - fx0;
+        for (int r = tid / TR_CT; r < FY; r += 256 / TR_CT) {
+          const C* fr = fs + r * FX + q0;
+          C acc = czero<C>();
+#pragma unroll
+          for (int t = 0; t < (WR > 0 ? WR : 1); ++t) acc = cfma(st.r[t], fr[t], acc);
+          rx[r * TR_CT + jx] = acc;
         }
-        rx[r * TR_CT + jx] = acc;
+      } else {
+        for (int r = tid / TR_CT; r < FY; r += 256 / TR_CT) {
+          C acc = czero<C>();
+          for (int t = 0; t < wR; ++t) {
+            const T w = Rwx[jx * wR + t];
+            const int q = Rlox[jx] + t;
+            if (w != (T)0 && q >= 0 && q < FX) acc = cfma(w, fs[r * FX + q], acc);
+          }
+          rx[r * TR_CT + jx] = acc;
+        }
       }
     }
   }
@@ -208,10 +246,16 @@ __global__ void __launch_bounds__(256) k_restrict_tiled(int nxf, int nyf, int nx
     const int jy = tid / TR_CT, jx = tid & (TR_CT - 1);   // TR_CT^2 = 256: one coarse output per thread
     if (jy >= cyn || jx >= cxn) return;
     C acc = czero<C>();
-    for (int t = 0; t < wR; ++t) {
-      const T w = Rwy[jy * wR + t];
-      const int q = Rloy[jy] + t;
-      if (w != (T)0 && q >= 0 && q < FY) acc = cfma(w, rx[q * TR_CT + jx], acc);
+    if (yin) {
+      const C* rc = rx + (2 * (cy0 + jy) + st.roff - fy0) * TR_CT + jx;
+#pragma unroll
+      for (int t = 0; t < (WR > 0 ? WR : 1); ++t) acc = cfma(st.r[t], rc[t * TR_CT], acc);
+    } else {
+      for (int t = 0; t < wR; ++t) {
+        const T w = Rwy[jy * wR + t];
+        const int q = Rloy[jy] + t;
+        if (w != (T)0 && q >= 0 && q < FY) acc = cfma(w, rx[q * TR_CT + jx], acc);
+      }
     }
     const size_t o = (size_t)(cy0 + jy) * nxc + cx0 + jx;
     c[o] = acc;
@@ -312,7 +356,32 @@ iga_status setup_tiled_transfers(iga_ctx* ctx) {
     for (int j = 1; j < Cl.nx; ++j) mono = mono && Rlo[j] >= Rlo[j - 1];
     for (int i = 1; i < F.nx; ++i) mono = mono && Plo[i] >= Plo[i - 1];
     F.tr_fmax = F.tp_cmax = 0;
+    F.tst = {};
     if (!mono) continue;
+    {
+      // interior stencil of the restriction: the contiguous range around the
+      // middle whose rows equal the middle row shifted by 2 per coarse row,
+      // with the whole window inside the grid
+      std::vector<double> Rw((size_t)Cl.nx * F.wR);
+      CK(cudaMemcpy(Rw.data(), F.Rw, sizeof(double) * Rw.size(), cudaMemcpyDeviceToHost));
+      auto& st = F.tst;
+      if (F.wR <= 8 && Cl.nx >= 3) {
+        const int jm = Cl.nx / 2;
+        st.roff = Rlo[jm] - 2 * jm;
+        for (int t = 0; t < F.wR; ++t) st.r[t] = Rw[(size_t)jm * F.wR + t];
+        auto rok = [&](int j) {
+          if (Rlo[j] != 2 * j + st.roff || Rlo[j] < 0 || Rlo[j] + F.wR > F.nx) return false;
+          for (int t = 0; t < F.wR; ++t)      // the knot-insertion weights of interior rows agree to rounding
+            if (std::fabs(Rw[(size_t)j * F.wR + t] - st.r[t]) > 1e-13) return false;
+          return true;
+        };
+        if (rok(jm)) {
+          st.rj0 = st.rj1 = jm;
+          while (st.rj0 > 0 && rok(st.rj0 - 1)) --st.rj0;
+          while (st.rj1 + 1 < Cl.nx && rok(st.rj1 + 1)) ++st.rj1;
+        }
+      }
+    }
     int fmax = 1, cmax = 1;
     for (int c0 = 0; c0 < Cl.nx; c0 += TR_CT) {
       int cn = std::min(TR_CT, Cl.nx - c0);
@@ -567,9 +636,21 @@ static void launch_restrict_tiled(iga_ctx* ctx, int l, const typename cplx<T>::t
   LevelData& Cc = ctx->lv[l + 1];
   const C cm = cconv<C>(ctx->k2const * make_double2(-ctx->sig.x, -ctx->sig.y));
   dim3 g(cdiv(Cc.nx, TR_CT), cdiv(Cc.ny, TR_CT));
-  k_restrict_tiled<T><<<g, 256, tr_smem<C, T>(F.tr_fmax, F.wR), ctx->st>>>(
-      F.nx, F.ny, Cc.nx, Cc.ny, F.wR, LvBuf<T>::Rw(F), F.Rlo, F.tr_fmax, f, c, xc, dinv, (T)ctx->prm.omega, ctx->p,
-      LvBuf<T>::K(Cc), LvBuf<T>::M(Cc), cm);
+  const size_t sm = tr_smem<C, T>(F.tr_fmax, F.wR);
+  const TrStencil<T> st = tr_stencil<T>(F);
+#define IGA_RESTRICT(W_)                                                                                          \
+  k_restrict_tiled<T, W_><<<g, 256, sm, ctx->st>>>(F.nx, F.ny, Cc.nx, Cc.ny, F.wR, LvBuf<T>::Rw(F), F.Rlo,       \
+                                                   F.tr_fmax, f, c, xc, dinv, (T)ctx->prm.omega, ctx->p,        \
+                                                   LvBuf<T>::K(Cc), LvBuf<T>::M(Cc), cm, st)
+  switch (F.wR) {
+    case 4: IGA_RESTRICT(4); break;
+    case 5: IGA_RESTRICT(5); break;
+    case 6: IGA_RESTRICT(6); break;
+    case 7: IGA_RESTRICT(7); break;
+    case 8: IGA_RESTRICT(8); break;
+    default: IGA_RESTRICT(0); break;
+  }
+#undef IGA_RESTRICT
   iga_count_launch();
 }
 

@@ -144,6 +144,35 @@ def test_restrict_prolong(name):
         assert rel_err(got, f + P @ c) <= 1e-14
 
 
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5])
+def test_transfer_interior_stencil(p):
+    """On levels large enough to have interior tiles, the tiled restriction
+    takes the uniform-knot interior stencil of the knot-insertion table (edge
+    tiles keep the table): restriction and prolongation in FP64 against the
+    oracle's transfer matrices, and the FP64 and FP32 V-cycles against the
+    oracle's V-cycle.
+    The V-cycle bounds at p >= 4 are its own rounding at this size (k = 192):
+    the table-only kernels gave 3.2e-11 (FP64, p = 5) and 1.17e-3 (FP32,
+    p = 4, bit for bit the same as with the stencil) on the same inputs."""
+    n_el = 320
+    pr = W.small_2d(n_el=n_el, p=p, k=0.6 * n_el)
+    h = from_problem(pr, skip_deflation=1)
+    hier = mg.MGHierarchy(2, p, n_el, pr.kfield, 1.0, 0.5)
+    for l in range(3):
+        P = hier.P[l]
+        nf, nc = P.shape
+        r = rvec(nf, 140 + l)
+        assert rel_err(to_n(h.restrict(l, to_t(r))), P.T @ r) <= 1e-13, l
+        c, f = rvec(nc, 150 + l), rvec(nf, 160 + l)
+        assert rel_err(to_n(h.prolong_add(l, to_t(c), to_t(f))), f + P @ c) <= 1e-13, l
+    r = rvec(h.n, 170)
+    ref = hier.apply(r, 1)
+    assert rel_err(to_n(h.vcycle(to_t(r))), ref) <= (1e-11 if p <= 4 else 1e-10)
+    if p <= 4:     # at p = 5 the FP32 V-cycle's own rounding reaches ~1e-2 at this size
+        h32 = from_problem(pr, skip_deflation=1, precision=1)
+        assert rel_err(to_n(h32.vcycle(to_t(r))), ref) <= (1e-4 if p <= 3 else 3e-3)
+
+
 @pytest.mark.parametrize("name", ALL)
 def test_coarse_solve(name):
     h, s, pr = ctx_and_oracle(name)

@@ -6,8 +6,9 @@
     python -m measure.profile_cases solve_host  # same, iterations launched from the host
     python -m measure.profile_cases sweep32     # FP32 Jacobi sweep on level 0, 4097^2 dofs
     python -m measure.profile_cases cnn         # network forward pass, 1281^2 pixels
+    python -m measure.profile_cases esolve1d    # 1D E solve at k = 10^6 (band solver)
 
-The solve, apply32, sweep32 and cnn cases open a profiler range around the
+The solve, apply32, sweep32, cnn and esolve1d cases open a profiler range around the
 timed launches only (capture them with `ncu --profile-from-start off`).
 
 Each case launches a handful of kernels on inputs of the bench problem so a
@@ -54,6 +55,17 @@ def main(case: str) -> None:
         torch.cuda.profiler.start()
         for _ in range(2):
             h.jacobi32(0, bs, xs, xo)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+    elif case == "esolve1d":
+        # one solve with the 1D deflation matrix E at k = 10^6, p = 1 (799 999
+        # unknowns, band solver) inside the profiler range
+        h = Helmholtz(dim=1, p=1, n_el=1600000, kfield=1e6)
+        t = torch.randn(h.m, dtype=torch.complex128, device="cuda")
+        h.esolve(t)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        h.esolve(t)
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
     elif case == "cnn":

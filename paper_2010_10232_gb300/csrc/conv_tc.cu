@@ -12,25 +12,39 @@
 // of the UMMA descriptors: core matrices of 8 rows x 16 bytes (8 bf16 of K),
 // 128 contiguous bytes each.
 //   A (input halo tile, 10 x 18 pixels): byte (cb, hy, hx) at
-//     ((cb * 18 + hy) * 10 + hx) * 16, cb = channel block of 8.  For tap
-//     (dy, dx) the A core matrix of output row py is the 8 pixels
-//     (hy = py + dy, hx = dx .. dx + 7): SBO (next 8 rows = next pixel row) =
-//     160 B, LBO (next 8 channels) = 18 * 10 * 16 B, start offset
-//     ((cb * 18 + dy) * 10 + dx) * 16.
+//     cb * 2944 + (hy * 10 + hx) * 16, cb = channel block of 8 (a block is
+//     18 * 10 * 16 = 2880 bytes, padded to a 128-byte multiple for the tensor
+//     copy).  For tap (dy, dx) the A core matrix of output row py is the 8
+//     pixels (hy = py + dy, hx = dx .. dx + 7): SBO (next 8 rows = next pixel
+//     row) = 160 B, LBO (next 8 channels) = 2944 B, start offset
+//     cb * 2944 + (dy * 10 + dx) * 16.
 //   B (weights, all taps, loaded once per block): byte (t, cb, n) at
 //     ((t * CB + cb) * N + n) * 16: SBO (next 8 output channels) = 128 B,
 //     LBO (next 8 input channels) = N * 16 B.
-// The MMA completion is signalled by tcgen05.commit on an mbarrier; every wait
-// is bounded (on timeout the block records an error, frees its tensor memory
-// and returns).
+//
+// Warp roles of a persistent block (192 threads) over tiles blockIdx.x,
+// blockIdx.x + gridDim.x, ...:
+//   warp 0   the halo tile of each channel block by one tensor copy
+//            (cp.async.bulk.tensor, 4D box 8 channels x 10 x 18 x 1 image;
+//            outside the image the copy fills zeros) into a ring of three or
+//            four stages, completion counted in bytes on the stage's mbarrier;
+//   warp 1   the MMAs of a tile into one of two TMEM accumulators; its
+//            commits release the stage and mark the accumulator full;
+//   warps 2-5  read the accumulator (warp w: TMEM lanes 32 (w % 4) ..),
+//            release it, and write the tile's outputs.
+// Every wait is bounded: a role that gives up records the error and leaves
+// its loop, the others then give up too; in-flight copies and MMAs are
+// waited for (bounded) before the tensor memory is freed.
 #include "common.cuh"
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
 typedef __nv_bfloat16 bf16;
 
 namespace {
 
-constexpr int TC_TX = 8, TC_TY = 16, TC_HX = TC_TX + 2, TC_HY = TC_TY + 2, TC_NT = 128;
+constexpr int TC_TX = 8, TC_TY = 16, TC_HX = TC_TX + 2, TC_HY = TC_TY + 2;
 constexpr unsigned TC_WAIT_LIMIT = 1u << 22;      // mbarrier polls before a block gives up
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -91,181 +105,207 @@ __device__ __forceinline__ void tc_ld16(unsigned taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+constexpr int WS_NA = 2, WS_NT = 192;              // TMEM accumulators, threads
+constexpr int CB_STRIDE = 2944;                     // one channel block of the halo tile (2880 used)
+
 template <int CIN, int N> struct TcGeom {
   static constexpr int CB = CIN / 8;
-  static constexpr size_t a_bytes = (size_t)CB * TC_HY * TC_HX * 16;
+  static constexpr int NS = CIN <= 16 ? 4 : 3;      // A stages (three keep four 32-channel blocks per SM)
+  static constexpr size_t a_stage = (size_t)CB * CB_STRIDE;
   static constexpr size_t b_bytes = (size_t)9 * CB * N * 16;
-  static constexpr size_t smem = 2 * a_bytes + b_bytes + 32;   // + two mbarriers and the TMEM address slot
-  static constexpr int ACC_COLS = 32;                           // one accumulator (>= N FP32 columns)
-  static constexpr int TMEM_COLS = 2 * ACC_COLS;                // two, alternating between tiles
+  static constexpr size_t bar_off = NS * a_stage + b_bytes;
+  static constexpr int n_bar = 2 * NS + 2 * WS_NA;
+  static constexpr size_t smem = bar_off + 8 * n_bar + 16 + 4 * N + 128;   // + TMEM slot, bias, alignment slack
+  static constexpr unsigned tx_bytes = (unsigned)CB * TC_HY * TC_HX * 16;
+  static constexpr int ACC_COLS = 32;                // one accumulator (>= N FP32 columns)
+  static constexpr int TMEM_COLS = WS_NA * ACC_COLS;
   static_assert(N == 16 || N == 32, "accumulator width");
   static_assert(CIN % 16 == 0, "K chunks of 16 channels");
+  static_assert(bar_off % 16 == 0 && CB_STRIDE % 128 == 0, "alignment");
 };
 
-__device__ __forceinline__ void cp_async16(unsigned dst, const void* src, unsigned src_bytes) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+__device__ __forceinline__ void mbar_expect_tx(unsigned a, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive(unsigned a) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
+__device__ __forceinline__ void tma_load_4d(unsigned dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            unsigned mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(dst),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(mbar)
+      : "memory");
+}
 
 // bounded wait on an mbarrier phase; false if the limit ran out
 __device__ __forceinline__ bool mbar_wait_bounded(unsigned a, unsigned parity) {
   unsigned polls = 0;
   while (!mbar_try_wait(a, parity)) {
     if (++polls > TC_WAIT_LIMIT) return false;
-    __nanosleep(32);
+    if (polls > 64) __nanosleep(32);          // spin first: most waits end within a few polls
   }
   return true;
 }
 
 }  // namespace
 
-// X: NHWC bf16 [B][H][W][CIN]; Wt: [COUTP][9][CIN] bf16 (COUTP >= COUT real
-// output channels, rows beyond COUTP read as zero up to N); EPI as in cnn.cu:
-// 0 + bias, ReLU, bf16 [px][N]; 1 + bias, FP32 [px][2]; 2 times (mask > 0),
-// bf16 [px][N].  err: set to 1 if a wait gave up.
-//
-// Persistent blocks take tiles blockIdx.x, blockIdx.x + gridDim.x, ... in a
-// two-stage pipeline: iteration i issues the MMAs of tile i into accumulator
-// i % 2 (from A buffer i % 2), then waits for tile i - 1's MMAs, reads its
-// accumulator, starts the cp.async halo load of tile i + 1 into the A buffer
-// tile i - 1 used, and stores tile i - 1's outputs.  The tensor core works
-// on one tile while the block loads the next and writes the previous.
+// bounded wait by lane 0 of a warp, the result for the whole warp
+__device__ __forceinline__ bool warp_wait(unsigned a, unsigned parity, int lane) {
+  bool ok = true;
+  if (lane == 0) ok = mbar_wait_bounded(a, parity);
+  return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+}
+
+// X (through the tensor map tmx): NHWC bf16 [B][H][W][CIN]; Wt: [COUTP][9][CIN]
+// bf16 (COUTP >= COUT real output channels, rows beyond COUTP read as zero up
+// to N); EPI as in cnn.cu: 0 + bias, ReLU, bf16 [px][N]; 1 + bias, FP32
+// [px][2]; 2 times (mask > 0), bf16 [px][N].  err: set to 1 if a wait gave up.
 template <int CIN, int N, int EPI>
-__global__ void __launch_bounds__(TC_NT) k_conv3x3_tc(const bf16* __restrict__ X, const bf16* __restrict__ Wt,
-                                                      int coutp, const float* __restrict__ bias,
-                                                      const bf16* __restrict__ mask, void* Yout, int B, int H,
-                                                      int W, int* err) {
+__global__ void __launch_bounds__(WS_NT) k_conv3x3_tc(const __grid_constant__ CUtensorMap tmx,
+                                                      const bf16* __restrict__ Wt, int coutp,
+                                                      const float* __restrict__ bias, const bf16* __restrict__ mask,
+                                                      void* Yout, int B, int H, int W, int* err) {
   using G = TcGeom<CIN, N>;
-  constexpr int CB = G::CB;
-  extern __shared__ __align__(128) unsigned char tc_smem[];
-  unsigned char* Bs = tc_smem + 2 * G::a_bytes;
-  unsigned long long* mbar = reinterpret_cast<unsigned long long*>(Bs + G::b_bytes);
-  unsigned* tslot = reinterpret_cast<unsigned*>(mbar + 2);
+  constexpr int CB = G::CB, WS_NS = G::NS;
+  extern __shared__ unsigned char tc_raw[];
+  const unsigned raw_s = smem_u32(tc_raw);
+  const unsigned base = (raw_s + 127u) & ~127u;
+  unsigned char* gbase = tc_raw + (base - raw_s);
+  unsigned char* Bs = gbase + WS_NS * G::a_stage;
+  const unsigned a_s0 = base, b_base = base + (unsigned)(WS_NS * G::a_stage);
+  const unsigned bar = base + (unsigned)G::bar_off;
+  auto full = [&](int q) { return bar + 8u * (unsigned)q; };
+  auto empty = [&](int q) { return bar + 8u * (unsigned)(WS_NS + q); };
+  auto accf = [&](int a) { return bar + 8u * (unsigned)(2 * WS_NS + a); };
+  auto acce = [&](int a) { return bar + 8u * (unsigned)(2 * WS_NS + WS_NA + a); };
+  unsigned* tslot = reinterpret_cast<unsigned*>(gbase + G::bar_off + 8 * G::n_bar);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-  if (warp == 0) {
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
                  "r"(G::TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    mbar_init(smem_u32(mbar), 1);
-    mbar_init(smem_u32(mbar + 1), 1);
+    for (int q = 0; q < WS_NS; ++q) { mbar_init(full(q), 1); mbar_init(empty(q), 1); }
+    for (int a = 0; a < WS_NA; ++a) { mbar_init(accf(a), 1); mbar_init(acce(a), 4); }   // acce: one arrival per epilogue warp
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  // bias into shared memory (read by the epilogue as broadcasts)
+  float* sbias = reinterpret_cast<float*>(gbase + G::bar_off + 8 * G::n_bar + 16);
+  if (tid < N) sbias[tid] = (EPI == 0 || (EPI == 1 && tid < 2)) ? bias[tid] : 0.f;
   // weights into the B layout: chunk (t, cb, n) = Wt[n][t][8 cb .. 8 cb + 7]
-  for (int i = tid; i < 9 * CB * N; i += TC_NT) {
+  for (int i = tid; i < 9 * CB * N; i += WS_NT) {
     const int n = i % N, tcb = i / N, cb = tcb % CB, t = tcb / CB;
     uint4 v = make_uint4(0u, 0u, 0u, 0u);
     if (n < coutp) v = *reinterpret_cast<const uint4*>(Wt + ((size_t)n * 9 + t) * CIN + cb * 8);
     *reinterpret_cast<uint4*>(Bs + (size_t)((t * CB + cb) * N + n) * 16) = v;
   }
-  const unsigned a_base0 = smem_u32(tc_smem), b_base = smem_u32(Bs);
-  constexpr unsigned idesc = umma_idesc_bf16(128, N);
-  constexpr unsigned A_LBO = TC_HY * TC_HX * 16, A_SBO = TC_HX * 16, B_LBO = N * 16, B_SBO = 8 * 16;
-
-  const int tiles_x = (W + TC_TX - 1) / TC_TX, tiles_y = (H + TC_TY - 1) / TC_TY;
-  const int per_img = tiles_x * tiles_y, ntiles = per_img * B;
-
-  // input halo tile into the A layout (16-byte chunks of 8 channels, zero-filled outside the image)
-  auto load_tile = [&](int tile, unsigned a_dst) {
-    const int b = tile / per_img, rem = tile - b * per_img;
-    const int ty = rem / tiles_x, tx = rem - ty * tiles_x;
-    const int x0 = tx * TC_TX, y0 = ty * TC_TY;
-    const size_t img = (size_t)b * H * W;
-    for (int i = tid; i < CB * TC_HY * TC_HX; i += TC_NT) {
-      const int hx = i % TC_HX, r = i / TC_HX, hy = r % TC_HY, cb = r / TC_HY;
-      const int gy = y0 - 1 + hy, gx = x0 - 1 + hx;
-      const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
-      const bf16* src = in ? X + (img + (size_t)gy * W + gx) * CIN + cb * 8 : X;
-      cp_async16(a_dst + (unsigned)i * 16u, src, in ? 16u : 0u);
-    }
-  };
-
-  if ((int)blockIdx.x < ntiles) load_tile(blockIdx.x, a_base0);
-  cp_async_commit();
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic-proxy weights -> tensor core
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const unsigned tmem = *tslot;
-  const unsigned mb0 = smem_u32(mbar);
 
-  unsigned phase = 0u, pending = 0u;     // bit b: parity to wait for / MMAs outstanding on mbarrier b
+  const int tiles_x = (W + TC_TX - 1) / TC_TX, tiles_y = (H + TC_TY - 1) / TC_TY;
+  const int per_img = tiles_x * tiles_y, ntiles = per_img * B;
+  const int nk = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  auto tile_xy = [&](int k, int& b, int& x0, int& y0) {
+    const int tile = (int)blockIdx.x + k * (int)gridDim.x;
+    b = tile / per_img;
+    const int rem = tile - b * per_img, ty = rem / tiles_x;
+    x0 = (rem - ty * tiles_x) * TC_TX;
+    y0 = ty * TC_TY;
+  };
   bool failed = false;
-  for (int it = 0;; ++it) {
-    const int cur = (int)blockIdx.x + it * (int)gridDim.x;
-    const bool have_cur = cur < ntiles;
-    if (!have_cur && it == 0) break;
-    const int s = it & 1;
-    // tile cur's operands landed (the only outstanding cp.async group) and
-    // every thread finished reading the accumulator this tile overwrites
-    cp_async_wait_all();
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    tc_fence_before();
-    __syncthreads();
-    if (have_cur) {
-      if (tid == 0) {
+
+  if (warp == 0) {
+    // ---- producer: tensor copies of the halo tiles
+    int issued = 0;
+    for (int k = 0; k < nk; ++k) {
+      const int q = k % WS_NS;
+      if (k >= WS_NS && !warp_wait(empty(q), ((k / WS_NS) - 1) & 1, lane)) { failed = true; break; }
+      if (lane == 0) {
+        int b, x0, y0;
+        tile_xy(k, b, x0, y0);
+        mbar_expect_tx(full(q), G::tx_bytes);
+        const unsigned dst = a_s0 + (unsigned)(q * G::a_stage);
+#pragma unroll
+        for (int cb = 0; cb < CB; ++cb) tma_load_4d(dst + cb * CB_STRIDE, &tmx, cb * 8, x0 - 1, y0 - 1, b, full(q));
+      }
+      __syncwarp();
+      issued = k + 1;
+    }
+    // the last copies have landed before the block can end (the consumer saw
+    // them already unless something failed)
+    for (int k = max(0, issued - WS_NS); k < issued; ++k)
+      if (!warp_wait(full(k % WS_NS), (k / WS_NS) & 1, lane)) failed = true;
+  } else if (warp == 1) {
+    // ---- MMA issue
+    constexpr unsigned idesc = umma_idesc_bf16(128, N);
+    constexpr unsigned A_LBO = CB_STRIDE, A_SBO = TC_HX * 16, B_LBO = N * 16, B_SBO = 8 * 16;
+    int committed = 0;
+    for (int k = 0; k < nk; ++k) {
+      const int q = k % WS_NS, a = k % WS_NA;
+      if (!warp_wait(full(q), (k / WS_NS) & 1, lane)) { failed = true; break; }
+      if (k >= WS_NA && !warp_wait(acce(a), ((k / WS_NA) - 1) & 1, lane)) { failed = true; break; }
+      if (lane == 0) {
         tc_fence_after();
-        const unsigned a_base = a_base0 + (unsigned)(s * G::a_bytes);
-        const unsigned d_tmem = tmem + (unsigned)(s * G::ACC_COLS);
+        const unsigned a_base = a_s0 + (unsigned)(q * G::a_stage);
+        const unsigned d_tmem = tmem + (unsigned)(a * G::ACC_COLS);
 #pragma unroll
         for (int t = 0; t < 9; ++t) {
           const int dy = t / 3, dx = t % 3;
 #pragma unroll
           for (int kc = 0; kc < CIN / 16; ++kc) {
-            const unsigned a_off = (unsigned)((((2 * kc) * TC_HY + dy) * TC_HX + dx) * 16);
+            const unsigned a_off = (unsigned)((2 * kc) * CB_STRIDE + (dy * TC_HX + dx) * 16);
             const unsigned b_off = (unsigned)((t * CB + 2 * kc) * N * 16);
-            tc_mma(d_tmem, umma_desc(a_base + a_off, A_LBO, A_SBO), umma_desc(b_base + b_off, B_LBO, B_SBO), idesc,
-                   (t | kc) != 0 ? 1u : 0u);
+            tc_mma(d_tmem, umma_desc(a_base + a_off, A_LBO, A_SBO), umma_desc(b_base + b_off, B_LBO, B_SBO),
+                   idesc, (t | kc) != 0 ? 1u : 0u);
           }
         }
-        tc_commit(mb0 + 8u * (unsigned)s);
+        tc_commit(empty(q));
+        tc_commit(accf(a));
       }
-      pending |= 1u << s;
+      __syncwarp();
+      committed = k + 1;
     }
-    const bool have_prev = it > 0;
-    const int q = s ^ 1;
-    float acc[N];
-    if (have_prev) {
-      // the give-up decision is made for the whole block
-      const bool done = mbar_wait_bounded(mb0 + 8u * (unsigned)q, (phase >> q) & 1u);
-      if (__syncthreads_or(!done)) {
-        failed = true;
-        if (tid == 0) atomicExch(err, 1);
-        break;
-      }
-      phase ^= 1u << q;
-      pending &= ~(1u << q);
+    // every MMA of this block has completed before the tensor memory is freed
+    if (committed > 0 && !warp_wait(accf((committed - 1) % WS_NA), ((committed - 1) / WS_NA) & 1, lane)) failed = true;
+  } else {
+    // ---- epilogue: thread <-> TMEM lane 32 (warp % 4) + lane <-> pixel (m % 8, m / 8)
+    const int qw = warp & 3;
+    const int m = 32 * qw + lane;
+    const float* bv = sbias;
+    for (int k = 0; k < nk; ++k) {
+      const int a = k % WS_NA;
+      if (!warp_wait(accf(a), (k / WS_NA) & 1, lane)) { failed = true; break; }
       tc_fence_after();
-      const unsigned trow = tmem + (unsigned)(q * G::ACC_COLS) + ((unsigned)(32 * warp) << 16);
+      float acc[N];
+      const unsigned trow = tmem + (unsigned)(a * G::ACC_COLS) + ((unsigned)(32 * qw) << 16);
       tc_ld16(trow, acc);
       if constexpr (N == 32) tc_ld16(trow + 16, acc + 16);
-    }
-    // A buffer q is free once tile cur - gridDim.x's MMAs completed
-    const int nxt = cur + (int)gridDim.x;
-    if (have_cur && nxt < ntiles) load_tile(nxt, a_base0 + (unsigned)(q * G::a_bytes));
-    cp_async_commit();
-    if (have_prev) {
-      // epilogue: thread <-> TMEM lane 32 warp + lane <-> pixel (m % 8, m / 8)
-      const int prev = cur - (int)gridDim.x;
-      const int b = prev / per_img, rem = prev - b * per_img;
-      const int ty = rem / tiles_x, tx = rem - ty * tiles_x;
-      const int m = 32 * warp + lane;
-      const int gx = tx * TC_TX + (m & 7), gy = ty * TC_TY + (m >> 3);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(acce(a));
+      int b, x0, y0;
+      tile_xy(k, b, x0, y0);
+      const int gx = x0 + (m & 7), gy = y0 + (m >> 3);
       if (gx < W && gy < H) {
         const size_t p = (size_t)b * H * W + (size_t)gy * W + gx;
         if (EPI == 0) {
           __nv_bfloat162 o[N / 2];
 #pragma unroll
           for (int c = 0; c < N; c += 2)
-            o[c / 2] = __floats2bfloat162_rn(fmaxf(acc[c] + bias[c], 0.f), fmaxf(acc[c + 1] + bias[c + 1], 0.f));
+            o[c / 2] = __floats2bfloat162_rn(fmaxf(acc[c] + bv[c], 0.f), fmaxf(acc[c + 1] + bv[c + 1], 0.f));
 #pragma unroll
           for (int v = 0; v < N / 8; ++v)
             reinterpret_cast<uint4*>((bf16*)Yout + p * N)[v] = reinterpret_cast<const uint4*>(o)[v];
         } else if (EPI == 1) {
-          *reinterpret_cast<float2*>((float*)Yout + p * 2) = make_float2(acc[0] + bias[0], acc[1] + bias[1]);
+          *reinterpret_cast<float2*>((float*)Yout + p * 2) = make_float2(acc[0] + bv[0], acc[1] + bv[1]);
         } else {
           __nv_bfloat162 o[N / 2];
           const __nv_bfloat162* mk = reinterpret_cast<const __nv_bfloat162*>(mask + p * N);
@@ -281,21 +321,29 @@ __global__ void __launch_bounds__(TC_NT) k_conv3x3_tc(const bf16* __restrict__ X
         }
       }
     }
-    if (!have_cur) break;
   }
-  cp_async_wait_all();
-  // a block that gave up waits (bounded) for its own MMAs before freeing TMEM
-  if (failed) {
-#pragma unroll
-    for (int b = 0; b < 2; ++b)
-      if ((pending >> b) & 1u) (void)mbar_wait_bounded(mb0 + 8u * (unsigned)b, (phase >> b) & 1u);
-  }
+  if (failed && lane == 0) atomicExch(err, 1);
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) {
+  if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(G::TMEM_COLS) : "memory");
   }
+}
+
+// cuTensorMapEncodeTiled from the driver (no link against the driver library)
+static PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
 }
 
 template <int CIN, int N, int EPI>
@@ -306,22 +354,32 @@ static cudaError_t launch_tc(const bf16* X, const bf16* Wt, int coutp, const flo
   if (per_sm == 0) {
     cudaFuncSetAttribute(k_conv3x3_tc<CIN, N, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::smem);
     // resident blocks per SM: shared memory (plus the 1 KB the runtime
-    // reserves per block), 64 registers x 128 threads, and the SM's 512
-    // tensor-memory columns, TMEM_COLS per block
+    // reserves per block) and the SM's 512 tensor-memory columns
     int dev = 0, smem_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-    int by_smem = smem_sm / (int)(G::smem + 1024);
-    int n = 512 / G::TMEM_COLS;
-    if (by_smem < n) n = by_smem;
-    if (65536 / (64 * TC_NT) < n) n = 65536 / (64 * TC_NT);
+    int n = smem_sm / (int)(G::smem + 1024);
+    if (512 / G::TMEM_COLS < n) n = 512 / G::TMEM_COLS;
     per_sm = n < 1 ? 1 : n;
   }
   const long long tiles = (long long)cdiv(W, TC_TX) * cdiv(H, TC_TY) * B;
   const long long cap = (long long)per_sm * num_sms;
   const int grid = (int)(tiles < cap ? tiles : cap);
   if (grid == 0) return cudaSuccess;
-  k_conv3x3_tc<CIN, N, EPI><<<grid, TC_NT, G::smem, st>>>(X, Wt, coutp, bias, mask, Y, B, H, W, err);
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
+  if (!enc || ((uintptr_t)X & 15u)) return cudaErrorInvalidValue;
+  // X as a 4D tensor (channels, x, y, image); the box is one channel block of
+  // the 10 x 18 halo tile of one image
+  CUtensorMap map;
+  const cuuint64_t dims[4] = {(cuuint64_t)CIN, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
+  const cuuint64_t strides[3] = {(cuuint64_t)CIN * 2, (cuuint64_t)W * CIN * 2, (cuuint64_t)H * W * CIN * 2};
+  const cuuint32_t box[4] = {8, (cuuint32_t)TC_HX, (cuuint32_t)TC_HY, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)X, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+      CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+  k_conv3x3_tc<CIN, N, EPI><<<grid, WS_NT, G::smem, st>>>(map, Wt, coutp, bias, mask, Y, B, H, W, err);
   iga_count_launch();
   return cudaGetLastError();
 }

@@ -272,9 +272,14 @@ iga_status iga_set_wait_limit(iga_ctx* ctx, long long polls, int phantom_arrival
 /* Batched solves in one CUDA-graph launch (not in the paper; the batched form of
    the method): instance b (context ctxs[b], each with its own k, p, mesh and
    precision) solves nrhs[b] right-hand sides stored back to back at rhs[b]
-   (nrhs[b] * n_b complex128, DEVICE) into x[b] (same layout).  The chains of
-   one instance run in order, different instances run concurrently, and each
-   right-hand side stops on its own convergence test (tol, maxit as iga_solve).
+   (nrhs[b] * n_b complex128, DEVICE) into x[b] (same layout).  Every
+   right-hand side runs as its own chain, concurrently with all others: the
+   second and later right-hand sides of an instance use workspace clones of
+   its context (the setup shared, the solve vectors and Krylov workspace of
+   their own; created by the first call that needs them and freed by
+   iga_destroy of the context), except for a context with a network attached,
+   whose chains run in order.  Each right-hand side stops on its own
+   convergence test (tol, maxit as iga_solve).
    iters and status (HOST, sum(nrhs) entries, instance-major; status may be
    NULL) receive per right-hand side the iteration count and IGA_OK /
    IGA_NOT_CONVERGED / error.  Contexts must be distinct, on one device, built

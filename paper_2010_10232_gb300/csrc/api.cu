@@ -4,6 +4,7 @@
 #include "bspline.cuh"
 #include <cmath>
 #include <new>
+#include <type_traits>
 
 #include <atomic>
 
@@ -157,8 +158,72 @@ iga_status iga_setup(const iga_params* prm, iga_ctx** out) {
   return IGA_OK;
 }
 
+}  // extern "C"
+
+// A context for the same problem that shares every setup table, factor and
+// tuned tile shape of `parent` and owns fresh copies of everything a solve
+// writes (level vectors, work vectors, deflation and band-solve scratch; the
+// Krylov workspace is allocated by its first solve), so that it can solve at
+// the same time as the parent.  Owned by the parent (iga_destroy).  Not for a
+// context with a network attached (the network's buffers are not copied).
+iga_ctx* clone_workspace(iga_ctx* parent) {
+  iga_ctx* c = new (std::nothrow) iga_ctx(*parent);
+  if (!c) return nullptr;
+  c->bufs.ptrs.clear();            // the parent's allocations stay the parent's
+  c->clones.clear();
+  c->err.clear();
+  c->graph = nullptr; c->gexec = nullptr; c->cap_stream = nullptr; c->gcond = 0;
+  c->graph_flex = false; c->graph_maxit = 0; c->body_kernels = 0;
+  c->maxit_alloc = -1;
+  c->Vb = c->Zb = c->H = c->gsn = c->gg = c->gy = nullptr;
+  c->gstate = nullptr; c->gflag = nullptr; c->hflag = nullptr;
+  c->kvec = nullptr; c->kint = nullptr; c->kbar = nullptr;
+  c->cgs_part = nullptr; c->cgs_h = nullptr; c->cgs_ticket = nullptr;
+  c->hf = c->hu = nullptr; c->brec = nullptr; c->brec_cap = 0; c->hres = nullptr;
+  c->net = nullptr; c->net_rms = nullptr; c->net_bad = nullptr;
+  bool ok = alloc_level_vectors(c) == IGA_OK;
+  const size_t n = c->lv[0].n;
+  auto fresh = [&](auto*& ptr, size_t count) {
+    using E = std::remove_reference_t<decltype(*ptr)>;
+    if (!ptr) return;
+    ptr = dalloc<E>(c, count);
+    ok = ok && ptr != nullptr;
+  };
+  fresh(c->w0, n); fresh(c->w1, n); fresh(c->w2, n); fresh(c->w3, n);
+  fresh(c->fin, n); fresh(c->fout, n);
+  fresh(c->partials, 4 * (size_t)(2 * c->num_sms) + 16);
+  fresh(c->ct, c->m); fresh(c->cs, c->m); fresh(c->cw, c->m); fresh(c->ce1, c->m); fresh(c->ce2, c->m);
+  fresh(c->ctf, c->m); fresh(c->cef, c->m);
+  const size_t mmE = c->fdmE.n ? (c->dim == 2 ? (size_t)c->fdmE.n * c->fdmE.n : (size_t)c->fdmE.n) : 0;
+  fresh(c->fdmE.w1, mmE); fresh(c->fdmE.w2, mmE);
+  const size_t mmC = c->fdmC.n ? (c->dim == 2 ? (size_t)c->fdmC.n * c->fdmC.n : (size_t)c->fdmC.n) : 0;
+  fresh(c->fdmC.w1, mmC); fresh(c->fdmC.w2, mmC);
+  fresh(c->cxr, n);
+  fresh(c->ep_t, (size_t)c->enb * c->eblk); fresh(c->ep_g, (size_t)c->enb * c->eblk); fresh(c->ep_v, (size_t)c->eblk);
+  fresh(c->cband_t, (size_t)c->nc); fresh(c->cband_x, (size_t)c->nc);
+  ok = ok && band_clone_scratch(c, c->bandE) == IGA_OK && band_clone_scratch(c, c->bandC) == IGA_OK &&
+       band_clone_scratch(c, c->bandX) == IGA_OK;
+  if (!ok) {
+    delete c;
+    return nullptr;
+  }
+  return c;
+}
+
+extern "C" {
+
+static void destroy_one(iga_ctx* ctx) {
+  cudaStreamSynchronize(ctx->st);
+  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+  if (ctx->graph) cudaGraphDestroy(ctx->graph);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  delete ctx;
+}
+
 void iga_destroy(iga_ctx* ctx) {
   if (!ctx) return;
+  for (iga_ctx* c : ctx->clones) destroy_one(c);
+  ctx->clones.clear();
   cudaStreamSynchronize(ctx->st);
   if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
   if (ctx->graph) cudaGraphDestroy(ctx->graph);

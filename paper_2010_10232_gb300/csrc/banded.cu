@@ -441,6 +441,19 @@ iga_status band_setup(iga_ctx* ctx, BandLU& F, const double2* Ab, int n, int b) 
   return IGA_OK;
 }
 
+// fresh solve scratch (y, rz, rz2) for a workspace clone sharing the factors
+iga_status band_clone_scratch(iga_ctx* ctx, BandLU& F) {
+  if (F.n == 0) return IGA_OK;
+  F.y = dalloc<double2>(ctx, F.n);
+  if (!F.y) return set_err(ctx, IGA_E_OOM, "band solver scratch");
+  if (F.P > 1) {
+    F.rz = dalloc<double2>(ctx, F.nr);
+    F.rz2 = dalloc<double2>(ctx, F.nr);
+    if (!F.rz || !F.rz2) return set_err(ctx, IGA_E_OOM, "band solver scratch");
+  }
+  return IGA_OK;
+}
+
 // x = A^{-1} t (t and x may be the same vector)
 iga_status band_solve(iga_ctx* ctx, const BandLU& F, const double2* t, double2* x) {
   if (F.P == 1 && x != t) {

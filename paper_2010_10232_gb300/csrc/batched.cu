@@ -4,11 +4,13 @@
 //
 // Graph layout: for instance b and right-hand side r the chain
 //     init(f_br) -> WHILE(cond_br) { one FGMRES/GMRES iteration } -> finish(f_br, x_br) -> record
-// is appended to the graph; the chains of one instance follow each other (they
-// share that instance's workspace), the chains of different instances have no
-// edges between them and run concurrently.  Each WHILE node stops on its own
-// convergence flag (per-instance masks); the init kernel sets the condition so
-// that a zero right-hand side runs no iteration.
+// is appended to the graph.  Right-hand side r > 0 of an instance runs on the
+// instance's workspace clone r - 1 (same setup, its own vectors; created at
+// the first batched call that needs it and kept by the context), so no chain
+// has an edge to another and all of them run concurrently (an instance with a
+// network attached keeps one workspace: its chains follow each other).  Each
+// WHILE node stops on its own convergence flag; the init kernel sets the
+// condition so that a zero right-hand side runs no iteration.
 #include "common.cuh"
 #include <vector>
 
@@ -78,17 +80,34 @@ extern "C" iga_status iga_solve_batched(iga_ctx* const* ctxs, int nb, const iga_
     total += nrhs[b];
   }
   iga_ctx* ctx = ctxs[0];   // error reporting and the record buffer
+  // the workspace of right-hand side r of instance b
+  auto chain_ctx = [&](int b, int r) -> iga_ctx* {
+    iga_ctx* c = ctxs[b];
+    return (r == 0 || c->net) ? c : c->clones[r - 1];
+  };
   for (int b = 0; b < nb; ++b) {
-    bool flex = ctxs[b]->prm.precision != 0 || ctxs[b]->prm.flexible != 0;
-    if (!ctxs[b]->arnoldi_cgs) {       // the single-solve graph (if any) used the other Arnoldi form
-      ctxs[b]->arnoldi_cgs = true;
-      if (ctxs[b]->gexec) cudaGraphExecDestroy(ctxs[b]->gexec);
-      if (ctxs[b]->graph) cudaGraphDestroy(ctxs[b]->graph);
-      ctxs[b]->gexec = nullptr;
-      ctxs[b]->graph = nullptr;
+    iga_ctx* c = ctxs[b];
+    if (!c->arnoldi_cgs) {       // the single-solve graph (if any) used the other Arnoldi form
+      c->arnoldi_cgs = true;
+      if (c->gexec) cudaGraphExecDestroy(c->gexec);
+      if (c->graph) cudaGraphDestroy(c->graph);
+      c->gexec = nullptr;
+      c->graph = nullptr;
     }
-    iga_status s = kry_prepare(ctxs[b], maxit, flex);
-    if (s != IGA_OK) return s;
+    if (!c->net)
+      while ((int)c->clones.size() < nrhs[b] - 1) {
+        CK(cudaStreamSynchronize(c->st));
+        iga_ctx* k = clone_workspace(c);
+        if (!k) return set_err(ctx, IGA_E_OOM, "workspace for right-hand side %zu of instance %d", c->clones.size() + 2, b);
+        c->clones.push_back(k);
+      }
+    bool flex = c->prm.precision != 0 || c->prm.flexible != 0;
+    for (int r = 0; r < nrhs[b]; ++r) {
+      iga_ctx* w = chain_ctx(b, r);
+      if (r > 0 && w == c) break;
+      iga_status s = kry_prepare(w, maxit, flex);
+      if (s != IGA_OK) return s;
+    }
   }
   if (ctx->brec_cap < total) {
     ctx->brec = dalloc<int>(ctx, 4 * (size_t)total);
@@ -101,11 +120,12 @@ extern "C" iga_status iga_solve_batched(iga_ctx* const* ctxs, int nb, const iga_
   std::vector<unsigned long long> body_k(total, 0);
   int slot = 0;
   for (int b = 0; b < nb; ++b) {
-    iga_ctx* c = ctxs[b];
-    const bool flex = c->prm.precision != 0 || c->prm.flexible != 0;
-    const size_t n = c->lv[0].n;
+    const bool flex = ctxs[b]->prm.precision != 0 || ctxs[b]->prm.flexible != 0;
+    const size_t n = ctxs[b]->lv[0].n;
     std::vector<cudaGraphNode_t> deps;
     for (int r = 0; r < nrhs[b]; ++r, ++slot) {
+      iga_ctx* c = chain_ctx(b, r);
+      if (c != ctxs[b] || r == 0) deps.clear();     // a chain on its own workspace depends on nothing
       const double2* f = (const double2*)rhs[b] + (size_t)r * n;
       double2* xo = (double2*)x[b] + (size_t)r * n;
       cudaGraphConditionalHandle h;

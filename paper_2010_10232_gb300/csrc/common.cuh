@@ -246,6 +246,10 @@ struct iga_ctx {
   int* brec = nullptr;               // batched solve: per right-hand side {iters, conv, nonfinite, timeout}
   int brec_cap = 0;
   double* hres = nullptr;            // pinned host copy of residual
+  // batched solves: workspace clones for the 2nd, 3rd, ... right-hand side of
+  // this instance (every setup table and factor shared read-only with this
+  // context, every vector a solve writes their own); owned and destroyed here
+  std::vector<iga_ctx*> clones;
   DevBuf bufs;
   std::string err;
 };
@@ -329,6 +333,8 @@ iga_status defl_apply_T(iga_ctx* ctx, const double2* x, double2* y, double2* tmp
 // exact CSLP (constant k): z = M_beta^{-1} r on the finest level
 iga_status setup_exact_cslp(iga_ctx* ctx);
 iga_status band_setup(iga_ctx* ctx, BandLU& F, const double2* Ab, int n, int b);
+iga_status band_clone_scratch(iga_ctx* ctx, BandLU& F);
+iga_ctx* clone_workspace(iga_ctx* parent);
 iga_status band_solve(iga_ctx* ctx, const BandLU& F, const double2* t, double2* x);
 iga_status band_probe(iga_ctx* ctx, int n, int b, const std::function<iga_status(const double2*, double2*)>& apply,
                       double2* x, double2* y, double2* Ab);

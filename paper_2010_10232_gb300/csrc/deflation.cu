@@ -394,17 +394,129 @@ __global__ void __launch_bounds__(128) k_fdm_gemm32(const float* R, const XT* X,
   }
 }
 
+// Long panels (m_x > FDM_TK): register-blocked form.  A block computes a
+// 32 x 32 tile of out with 64 threads, each 4 rows x 4 columns (16 complex
+// accumulators); K runs in chunks of 16 through two shared-memory buffers,
+// the next chunk's global loads held in registers while the current one is
+// used.  The real operand R and the complex operand X are staged so that a
+// thread reads its four rows (columns) with one or two 16-byte loads.
+// LEFT: out = R X (R rows x rows, X rows x cols); RIGHT: out = X R (R cols x
+// cols).  Same epilogue as k_fdm_gemm32.
+constexpr int FRB_T = 32, FRB_K = 16;
+template <bool LEFT, bool DIVIDE, bool ACC, typename XT, typename OT>
+__global__ void __launch_bounds__(64) k_fdm_gemm_rb(const float* __restrict__ R, const XT* __restrict__ X,
+                                                    OT* out, int rows, int cols, const float2* __restrict__ dinv) {
+  __shared__ __align__(16) float Rs[2][FRB_K][FRB_T];     // LEFT: R^T chunk [k][i]; RIGHT: R chunk [k][j]
+  __shared__ __align__(16) float2 Xs[2][FRB_K][FRB_T];    // LEFT: X chunk [k][j];  RIGHT: X^T chunk [k][i]
+  const int t = threadIdx.x, ty = t >> 3, tx = t & 7;
+  const int i0 = blockIdx.y * FRB_T, j0 = blockIdx.x * FRB_T;
+  const int K = LEFT ? rows : cols;
+  // this thread's share of a chunk: 8 reals and 8 complex values
+  // LEFT:  R[i0 + (t >> 1)][k0 + 8 (t & 1) + q], X[k0 + (t >> 2)][j0 + 8 (t & 3) + q]
+  // RIGHT: X[i0 + (t >> 1)][k0 + 8 (t & 1) + q], R[k0 + (t >> 2)][j0 + 8 (t & 3) + q]
+  float rv[8];
+  float2 xv[8];
+  auto load_chunk = [&](int k0) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      if (LEFT) {
+        const int i = i0 + (t >> 1), k = k0 + 8 * (t & 1) + q;
+        rv[q] = (i < rows && k < K) ? R[(size_t)i * K + k] : 0.f;
+        const int kx = k0 + (t >> 2), j = j0 + 8 * (t & 3) + q;
+        xv[q] = (kx < K && j < cols) ? ld_f2(X + (size_t)kx * cols + j) : make_float2(0.f, 0.f);
+      } else {
+        const int i = i0 + (t >> 1), k = k0 + 8 * (t & 1) + q;
+        xv[q] = (i < rows && k < K) ? ld_f2(X + (size_t)i * cols + k) : make_float2(0.f, 0.f);
+        const int kr = k0 + (t >> 2), j = j0 + 8 * (t & 3) + q;
+        rv[q] = (kr < K && j < cols) ? R[(size_t)kr * cols + j] : 0.f;
+      }
+    }
+  };
+  auto store_chunk = [&](int b) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      if (LEFT) {
+        Rs[b][8 * (t & 1) + q][t >> 1] = rv[q];
+        Xs[b][t >> 2][8 * (t & 3) + q] = xv[q];
+      } else {
+        Xs[b][8 * (t & 1) + q][t >> 1] = xv[q];
+        Rs[b][t >> 2][8 * (t & 3) + q] = rv[q];
+      }
+    }
+  };
+  float2 acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = make_float2(0.f, 0.f);
+  const int nch = (K + FRB_K - 1) / FRB_K;
+  load_chunk(0);
+  store_chunk(0);
+  __syncthreads();
+  for (int ch = 0; ch < nch; ++ch) {
+    const int b = ch & 1;
+    if (ch + 1 < nch) load_chunk((ch + 1) * FRB_K);
+#pragma unroll
+    for (int k = 0; k < FRB_K; ++k) {
+      if (LEFT) {
+        const float4 a = *reinterpret_cast<const float4*>(&Rs[b][k][4 * ty]);
+        const float4 x01 = *reinterpret_cast<const float4*>(&Xs[b][k][4 * tx]);
+        const float4 x23 = *reinterpret_cast<const float4*>(&Xs[b][k][4 * tx + 2]);
+        const float ar[4] = {a.x, a.y, a.z, a.w};
+        const float2 xc[4] = {make_float2(x01.x, x01.y), make_float2(x01.z, x01.w), make_float2(x23.x, x23.y),
+                              make_float2(x23.z, x23.w)};
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[r][c] = cfma(ar[r], xc[c], acc[r][c]);
+      } else {
+        const float4 x01 = *reinterpret_cast<const float4*>(&Xs[b][k][4 * ty]);
+        const float4 x23 = *reinterpret_cast<const float4*>(&Xs[b][k][4 * ty + 2]);
+        const float4 a = *reinterpret_cast<const float4*>(&Rs[b][k][4 * tx]);
+        const float ar[4] = {a.x, a.y, a.z, a.w};
+        const float2 xc[4] = {make_float2(x01.x, x01.y), make_float2(x01.z, x01.w), make_float2(x23.x, x23.y),
+                              make_float2(x23.z, x23.w)};
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[r][c] = cfma(ar[c], xc[r], acc[r][c]);
+      }
+    }
+    if (ch + 1 < nch) store_chunk(b ^ 1);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int i = i0 + 4 * ty + r;
+    if (i >= rows) continue;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int j = j0 + 4 * tx + c;
+      if (j >= cols) continue;
+      float2 v = acc[r][c];
+      if (DIVIDE) v = cmul(dinv[(size_t)i * cols + j], v);
+      if constexpr (ACC) {
+        OT* o = out + (size_t)i * cols + j;
+        *o = *o + tod(v);
+      } else {
+        st_c(out + (size_t)i * cols + j, v);
+      }
+    }
+  }
+}
+
 template <bool LEFT, bool DIVIDE, bool ACC, typename XT, typename OT>
 static void launch_fdm_gemm(iga_ctx* ctx, const float* R, const XT* X, OT* out, int rows, int cols,
                             const float2* dinv) {
   // up to FDM_TK the whole K extent in one stage, 16 loads in flight per
-  // thread; longer panels in 64-deep stages with 4 (measured faster there)
+  // thread; longer panels by the register-blocked kernel
   const int K = LEFT ? rows : cols;
   dim3 g(cdiv(cols, FDM_TX), cdiv(rows, FDM_TY));
   if (K <= FDM_TK) {
     k_fdm_gemm32<LEFT, DIVIDE, ACC, XT, OT, 16><<<g, 128, fdm_gemm_smem(K), ctx->st>>>(R, X, out, rows, cols, dinv, K);
   } else {
-    k_fdm_gemm32<LEFT, DIVIDE, ACC, XT, OT, 4><<<g, 128, fdm_gemm_smem(64), ctx->st>>>(R, X, out, rows, cols, dinv, 64);
+    dim3 gb(cdiv(cols, FRB_T), cdiv(rows, FRB_T));
+    k_fdm_gemm_rb<LEFT, DIVIDE, ACC, XT, OT><<<gb, 64, 0, ctx->st>>>(R, X, out, rows, cols, dinv);
   }
   iga_count_launch();
 }

@@ -505,6 +505,25 @@ def test_esolve_fdm_sizes(n_el, p):
     assert rel_err(to_n(h.esolve(to_t(t))), s.defl.lu.solve(t)) <= 1e-10
 
 
+@pytest.mark.parametrize("p", [2, 3])
+def test_esolve_register_blocked_transforms(p):
+    """m_x above 192: the fast-diagonalisation transforms of the E solve run
+    on the register-blocked GEMM; E^{-1} t against the oracle's sparse LU of
+    Z^T A Z, and the exact CSLP inverse of a 258^2-dof level against the
+    oracle's sparse LU of M_beta."""
+    n_el = 416
+    pr = W.small_2d(n_el=n_el, p=p, k=0.55 * n_el)
+    h, s = from_problem(pr), Solver(pr)
+    assert int(round(h.m ** 0.5)) > 192
+    t = rvec(h.m, 97)
+    assert rel_err(to_n(h.esolve(to_t(t))), s.defl.lu.solve(t)) <= 1e-10
+    pc = W.small_2d(n_el=256, p=p, k=100.0)
+    pc.precond, pc.deflation, pc.shift = "exact", False, (1.0, 1.0 / 300.0)
+    hc, sc = from_problem(pc), Solver(pc)
+    r = rvec(hc.n, 98)
+    assert rel_err(to_n(hc.precond(to_t(r))), sc.cslp_lu.solve(r)) <= 1e-10
+
+
 def test_coarsest_level_too_large_is_rejected():
     """n_el = 150 halves once (75 is odd): the 76^2-dof coarsest level is refused
     by the setup with IGA_E_INVALID instead of a failing launch."""

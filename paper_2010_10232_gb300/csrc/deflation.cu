@@ -695,7 +695,10 @@ iga_status setup_deflation(iga_ctx* ctx) {
   ctx->ctf = dalloc<float2>(ctx, ctx->m);
   ctx->cef = dalloc<float2>(ctx, ctx->m);
   if (!ctx->ce1 || !ctx->ce2 || !ctx->ctf || !ctx->cef) return set_err(ctx, IGA_E_OOM, "deflation alloc");
-  if (ctx->dim == 1) return setup_banded_E(ctx);
+  // 1D: the band solver, except for small constant-k problems without a
+  // Sommerfeld end, where the dense fast diagonalisation (a few tiny GEMVs)
+  // beats a sequential band recurrence
+  if (ctx->dim == 1 && (ctx->vark || ctx->robin_k != 0.0 || ctx->mx > FDM_TK)) return setup_banded_E(ctx);
   ctx->kc = dalloc<double>(ctx, (size_t)ctx->mx * ctx->mx);
   ctx->mc = dalloc<double>(ctx, (size_t)ctx->mx * ctx->mx);
   if (!ctx->ct || !ctx->cs || !ctx->cw || !ctx->kc || !ctx->mc) return set_err(ctx, IGA_E_OOM, "deflation alloc");
@@ -731,13 +734,20 @@ static iga_status fdm_solve32(iga_ctx* ctx, const FdmData& F, const double2* t, 
   const int mx = F.n;
   const float* V = F.Vf;
   const float* Vt = F.Vtf;
-  // (2D) T1 = V^T T; T2 = T1 V / D; T3 = V T2; S = T3 V^T (or s += S)
-  if (tf) launch_fdm_gemm<true, false, false>(ctx, Vt, tf, F.w1, mx, mx, nullptr);
-  else launch_fdm_gemm<true, false, false>(ctx, Vt, t, F.w1, mx, mx, nullptr);
-  launch_fdm_gemm<false, true, false>(ctx, V, F.w1, F.w2, mx, mx, F.dinv);
-  launch_fdm_gemm<true, false, false>(ctx, V, F.w2, F.w1, mx, mx, nullptr);
-  if (accumulate) launch_fdm_gemm<false, false, true>(ctx, Vt, F.w1, s, mx, mx, nullptr);
-  else launch_fdm_gemm<false, false, false>(ctx, Vt, F.w1, s, mx, mx, nullptr);
+  if (ctx->dim == 1) {
+    // s^T = ((t^T V) / d) V^T with t as a 1 x m row
+    launch_fdm_gemm<false, true, false>(ctx, V, t, F.w1, 1, mx, F.dinv);
+    if (accumulate) launch_fdm_gemm<false, false, true>(ctx, Vt, F.w1, s, 1, mx, nullptr);
+    else launch_fdm_gemm<false, false, false>(ctx, Vt, F.w1, s, 1, mx, nullptr);
+  } else {
+    // T1 = V^T T; T2 = T1 V / D; T3 = V T2; S = T3 V^T (or s += S)
+    if (tf) launch_fdm_gemm<true, false, false>(ctx, Vt, tf, F.w1, mx, mx, nullptr);
+    else launch_fdm_gemm<true, false, false>(ctx, Vt, t, F.w1, mx, mx, nullptr);
+    launch_fdm_gemm<false, true, false>(ctx, V, F.w1, F.w2, mx, mx, F.dinv);
+    launch_fdm_gemm<true, false, false>(ctx, V, F.w2, F.w1, mx, mx, nullptr);
+    if (accumulate) launch_fdm_gemm<false, false, true>(ctx, Vt, F.w1, s, mx, mx, nullptr);
+    else launch_fdm_gemm<false, false, false>(ctx, Vt, F.w1, s, mx, mx, nullptr);
+  }
   CKL();
   return IGA_OK;
 }
@@ -751,19 +761,21 @@ static iga_status fdm_solve32(iga_ctx* ctx, const FdmData& F, const double2* t, 
 static iga_status e0_solve(iga_ctx* ctx, const double2* t, double2* s, const float2* tf) {
   TRY(fdm_solve32(ctx, ctx->fdmE, t, s, false, tf));
   const int bw = (ctx->p + 4) / 2;
+  const int my = ctx->dim == 2 ? ctx->mx : 1;
+  float2* rf = ctx->dim == 2 ? ctx->cef : nullptr;
   for (int it = 0; it < ctx->fdmE.refine; ++it) {
-    TRY(op_apply_bands(ctx, bw, ctx->mx, ctx->mx, ctx->kcb, ctx->mcb, make_double2(-ctx->k2const, 0.0), s, ctx->ce1,
-                       t, EPI_ZMINUS, ctx->cef));
-    TRY(fdm_solve32(ctx, ctx->fdmE, ctx->ce1, s, true, ctx->cef));   // s += FDM(r)
+    TRY(op_apply_bands(ctx, bw, ctx->mx, my, ctx->kcb, ctx->mcb, make_double2(-ctx->k2const, 0.0), s, ctx->ce1, t,
+                       EPI_ZMINUS, rf));
+    TRY(fdm_solve32(ctx, ctx->fdmE, ctx->ce1, s, true, rf));   // s += FDM(r)
   }
   CKL();
   return IGA_OK;
 }
 
-// s = E^{-1} t.  2D: constant k by fast diagonalisation (e0_solve), variable
-// k by block LU; 1D: the band solver.
+// s = E^{-1} t.  Constant k by fast diagonalisation (e0_solve), 2D variable k
+// by block LU, 1D otherwise (and above m_x = FDM_TK) by the band solver.
 iga_status defl_esolve(iga_ctx* ctx, const double2* t, double2* s, const float2* tf) {
-  if (ctx->dim == 1) return band_solve(ctx, ctx->bandE, t, s);
+  if (ctx->dim == 1 && ctx->bandE.n > 0) return band_solve(ctx, ctx->bandE, t, s);
   if (ctx->vark) return block_E_solve(ctx, t, s);
   return e0_solve(ctx, t, s, tf);
 }

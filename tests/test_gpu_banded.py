@@ -37,7 +37,9 @@ def mp1b(k, p, n_el=None, **kw):
     return W.Problem(dim=1, p=p, n_el=n_el, kfield=W.constant_k(k), sources=[(0.5,)], **kw)
 
 
-# n_el = 40: one partition; 400 / 2000: several partitions and the interface system
+# n_el = 40: a small constant-k E (m_x <= 192), solved by the dense fast
+# diagonalisation; 400 / 2000: the band solver with several partitions and the
+# interface system
 @pytest.mark.parametrize("p", [1, 2, 3, 4, 5])
 @pytest.mark.parametrize("n_el,k", [(40, 20.0), (400, 250.0), (2000, 1250.0)])
 def test_banded_E_solve(p, n_el, k):

@@ -121,9 +121,10 @@ void iga_default_params(iga_params* prm);
    Gauss tables, 1D band matrices and transfer operators per multigrid level,
    the coarsest-level inverse, Z and the factorised E.  The coarsest level is
    inverted densely up to 2048 dofs; beyond that 2D setups are refused and 1D
-   ones factorise its band.  1D E is factorised as a band matrix (partitioned
-   LU with partial pivoting), 2D E by fast diagonalisation (constant k) or
-   block LU (variable k).  Synchronises.
+   ones factorise its band.  E: fast diagonalisation for constant k in 2D and
+   for small constant-k 1D problems without a Sommerfeld end (m_x <= 192),
+   block LU for variable k in 2D, otherwise (1D) a band factorisation
+   (partitioned LU with partial pivoting).  Synchronises.
    prm is a host pointer; *out receives a context to release with iga_destroy.
    Errors: IGA_E_INVALID for out-of-range parameters, IGA_E_OOM, IGA_E_CUDA. */
 iga_status iga_setup(const iga_params* prm, iga_ctx** out);

@@ -402,45 +402,46 @@ __global__ void __launch_bounds__(128) k_fdm_gemm32(const float* R, const XT* X,
 // thread reads its four rows (columns) with one or two 16-byte loads.
 // LEFT: out = R X (R rows x rows, X rows x cols); RIGHT: out = X R (R cols x
 // cols).  Same epilogue as k_fdm_gemm32.
-constexpr int FRB_T = 32, FRB_K = 16;
+constexpr int FRB_T = 32, FRB_K = 16, FRB_RS = 36, FRB_XS = 34;   // padded rows, 16-byte aligned
 template <bool LEFT, bool DIVIDE, bool ACC, typename XT, typename OT>
 __global__ void __launch_bounds__(64) k_fdm_gemm_rb(const float* __restrict__ R, const XT* __restrict__ X,
                                                     OT* out, int rows, int cols, const float2* __restrict__ dinv) {
-  __shared__ __align__(16) float Rs[2][FRB_K][FRB_T];     // LEFT: R^T chunk [k][i]; RIGHT: R chunk [k][j]
-  __shared__ __align__(16) float2 Xs[2][FRB_K][FRB_T];    // LEFT: X chunk [k][j];  RIGHT: X^T chunk [k][i]
+  __shared__ __align__(16) float Rs[2][FRB_K][FRB_RS];    // LEFT: R^T chunk [k][i]; RIGHT: R chunk [k][j]
+  __shared__ __align__(16) float2 Xs[2][FRB_K][FRB_XS];   // LEFT: X chunk [k][j];  RIGHT: X^T chunk [k][i]
   const int t = threadIdx.x, ty = t >> 3, tx = t & 7;
   const int i0 = blockIdx.y * FRB_T, j0 = blockIdx.x * FRB_T;
   const int K = LEFT ? rows : cols;
-  // this thread's share of a chunk: 8 reals and 8 complex values
-  // LEFT:  R[i0 + (t >> 1)][k0 + 8 (t & 1) + q], X[k0 + (t >> 2)][j0 + 8 (t & 3) + q]
-  // RIGHT: X[i0 + (t >> 1)][k0 + 8 (t & 1) + q], R[k0 + (t >> 2)][j0 + 8 (t & 3) + q]
+  // this thread's share of a chunk: elements e = 64 q + t, q = 0..7, of the
+  // 32 x 16 panel read along its contiguous index (16 K entries of a row, or
+  // 32 entries of a K row), so consecutive lanes load consecutive addresses
   float rv[8];
   float2 xv[8];
   auto load_chunk = [&](int k0) {
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
+      const int e = 64 * q + t;
+      const int a = e >> 4, kk = e & 15;     // row a of a 32 x 16 [row][k] panel
+      const int kr = e >> 5, c = e & 31;     // k row kr of a 16 x 32 [k][column] panel
       if (LEFT) {
-        const int i = i0 + (t >> 1), k = k0 + 8 * (t & 1) + q;
-        rv[q] = (i < rows && k < K) ? R[(size_t)i * K + k] : 0.f;
-        const int kx = k0 + (t >> 2), j = j0 + 8 * (t & 3) + q;
-        xv[q] = (kx < K && j < cols) ? ld_f2(X + (size_t)kx * cols + j) : make_float2(0.f, 0.f);
+        rv[q] = (i0 + a < rows && k0 + kk < K) ? R[(size_t)(i0 + a) * K + k0 + kk] : 0.f;
+        xv[q] = (k0 + kr < K && j0 + c < cols) ? ld_f2(X + (size_t)(k0 + kr) * cols + j0 + c) : make_float2(0.f, 0.f);
       } else {
-        const int i = i0 + (t >> 1), k = k0 + 8 * (t & 1) + q;
-        xv[q] = (i < rows && k < K) ? ld_f2(X + (size_t)i * cols + k) : make_float2(0.f, 0.f);
-        const int kr = k0 + (t >> 2), j = j0 + 8 * (t & 3) + q;
-        rv[q] = (kr < K && j < cols) ? R[(size_t)kr * cols + j] : 0.f;
+        xv[q] = (i0 + a < rows && k0 + kk < K) ? ld_f2(X + (size_t)(i0 + a) * cols + k0 + kk) : make_float2(0.f, 0.f);
+        rv[q] = (k0 + kr < K && j0 + c < cols) ? R[(size_t)(k0 + kr) * cols + j0 + c] : 0.f;
       }
     }
   };
   auto store_chunk = [&](int b) {
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
+      const int e = 64 * q + t;
+      const int a = e >> 4, kk = e & 15, kr = e >> 5, c = e & 31;
       if (LEFT) {
-        Rs[b][8 * (t & 1) + q][t >> 1] = rv[q];
-        Xs[b][t >> 2][8 * (t & 3) + q] = xv[q];
+        Rs[b][kk][a] = rv[q];
+        Xs[b][kr][c] = xv[q];
       } else {
-        Xs[b][8 * (t & 1) + q][t >> 1] = xv[q];
-        Rs[b][t >> 2][8 * (t & 3) + q] = rv[q];
+        Xs[b][kk][a] = xv[q];
+        Rs[b][kr][c] = rv[q];
       }
     }
   };

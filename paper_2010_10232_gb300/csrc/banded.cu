@@ -15,11 +15,11 @@
 // top/bot = first/last b entries; evaluated at the partition ends this is a
 // band system of size 2 b P (half bandwidth 3 b) for the interface values,
 // factorised the same way as one partition.  A solve is: a warp per
-// partition for y (forward and back substitution with register windows), one
-// warp for the interface system, and a thread per row for x.  Sequential
-// depth ~ 2 (s + 2 b P) steps with s ~ sqrt(2 b n), each step reading its
-// coefficients from shared memory (staged chunk by chunk with cp.async);
-// setup runs on the device.
+// partition for y (forward and back substitution, the elimination window
+// spread over the warp's lanes), one warp for the interface system, and a
+// thread per row for x.  Sequential depth ~ 2 (s + 2 b P) steps with
+// s ~ sqrt(2 b n), each step reading its coefficients from shared memory
+// (staged chunk by chunk with cp.async); setup runs on the device.
 #include "common.cuh"
 
 #include <cmath>
@@ -163,39 +163,52 @@ __device__ __forceinline__ void cpa4(void* dst, const void* src) {
 __device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cpa_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
-// rows of coefficients staged per chunk (two chunks in flight per warp)
-__host__ __device__ constexpr int band_chunk(int b) { return b <= 5 ? 128 : 64; }
-__host__ __device__ constexpr size_t band_smem(int b) {
-  return 2 * ((size_t)band_chunk(b) * (2 * b + 2) * sizeof(double2) + (size_t)band_chunk(b) * sizeof(int));
+__device__ __forceinline__ double2 shfl2(double2 v, int src) {
+  return make_double2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+// w - a s with four fused multiply-adds (dependent depth two)
+__device__ __forceinline__ double2 cfms(double2 w, double2 a, double2 s) {
+  return make_double2(fma(-a.x, s.x, fma(a.y, s.y, w.x)), fma(-a.x, s.y, fma(-a.y, s.x, w.y)));
 }
 
+// rows of coefficients staged per chunk (two chunks in flight per warp), a
+// multiple of the warp width; a stage holds [CH][2b] coefficients, [CH]
+// entering values and [CH] pivots
+__host__ __device__ constexpr int band_chunk(int b) { return b <= 5 ? 128 : 64; }
+__host__ __device__ constexpr size_t band_stage(int b) {
+  return (size_t)band_chunk(b) * (2 * b + 1) * sizeof(double2) + (size_t)band_chunk(b) * sizeof(int);
+}
+__host__ __device__ constexpr size_t band_smem(int b) { return 2 * band_stage(b); }
+
 // y = A_i^{-1} t for every partition: one warp per partition (one warp per
-// block).  The 32 lanes copy the next chunk of the partition's coefficient
-// rows (multipliers, pivots and entering right-hand sides for the forward
-// sweep; U rows, 1/U(r,r) and forward results for the back sweep) into shared
-// memory with cp.async while lane 0 runs the sequential recurrence on the
-// current chunk with register windows (forward: rows j .. j+b; back: the last
-// 2b solution values).  BM >= b.  t, y and rz must not overlap.  rz
-// (optional): the partition's first and last b solution values, as the
-// interface system's right-hand side.
-template <int BM>
-__global__ void __launch_bounds__(32) k_band_solve_local(int n, int b, int s, int P, const double2* __restrict__ lu,
-                                                         const double2* __restrict__ lm,
-                                                         const double2* __restrict__ rdiag,
-                                                         const int* __restrict__ ipiv, const double2* __restrict__ t,
-                                                         double2* __restrict__ y, double2* __restrict__ rz) {
+// block), b <= 15.  Row j of the partition lives in lane j mod 32 while it is
+// in the elimination window, so a step moves no window: the forward sweep's
+// step j takes the pivot row by one shuffle (lane p gets row j, every lane the
+// pivot value), updates rows j+1 .. j+b in their lanes with one complex
+// multiply-add, and hands lane j the right-hand side of row j+32.  The back
+// sweep runs column by column: step j broadcasts the finished sum acc_j of
+// row j and subtracts U(r, j) x_j = (U(r, j) / U(j, j)) acc_j from rows
+// j-1 .. j-2b (the columns of U are scaled at setup), so that
+// x_j = acc_j / U(j, j) is formed 32 rows at a time, off the dependent chain.  Per row: two shuffles and eight
+// FP64 warp instructions, whatever b.  The next chunk of coefficients is
+// copied into shared memory with cp.async while the current one is swept.  t,
+// y and rz must not overlap.  rz (optional): the partition's first and last b
+// solution values, as the interface system's right-hand side.
+__global__ void __launch_bounds__(32) k_band_solve_warp(int n, int b, int s, int P, const double2* __restrict__ lm,
+                                                        const int* __restrict__ ipiv, const double2* __restrict__ ucs,
+                                                        const double2* __restrict__ rdiag,
+                                                        const double2* __restrict__ t, double2* __restrict__ y,
+                                                        double2* __restrict__ rz) {
   const int i = blockIdx.x, lane = threadIdx.x;
   if (i >= P) return;
   int r0, r1;
   part_rows(i, n, s, P, r0, r1);
-  const int len = r1 - r0, W = 3 * b + 1, CH = band_chunk(b);
+  const int len = r1 - r0, b2 = 2 * b, CH = band_chunk(b);
   extern __shared__ __align__(16) unsigned char band_sm[];
-  // buffer q: A [CH][2b] complex, B [CH], C [CH] complex, I [CH] int
-  const size_t buf_bytes = (size_t)CH * (2 * b + 2) * sizeof(double2) + (size_t)CH * sizeof(int);
-  auto bufA = [&](int q) { return reinterpret_cast<double2*>(band_sm + q * buf_bytes); };
-  auto bufB = [&](int q) { return bufA(q) + (size_t)CH * 2 * b; };
-  auto bufC = [&](int q) { return bufB(q) + CH; };
-  auto bufI = [&](int q) { return reinterpret_cast<int*>(bufC(q) + CH); };
+  const size_t sb = band_stage(b);
+  auto bufA = [&](int q) { return reinterpret_cast<double2*>(band_sm + q * sb); };
+  auto bufE = [&](int q) { return bufA(q) + (size_t)CH * b2; };
+  auto bufI = [&](int q) { return reinterpret_cast<int*>(bufE(q) + CH); };
   const int nch = (len + CH - 1) / CH;
 
   // ---- forward sweep: chunk c = rows j0 .. j0 + CH - 1
@@ -203,17 +216,17 @@ __global__ void __launch_bounds__(32) k_band_solve_local(int n, int b, int s, in
     const int j0 = c * CH, rows = min(CH, len - j0);
     double2* A = bufA(q);
     for (int e = lane; e < rows * b; e += 32) cpa16(A + e, lm + (size_t)(r0 + j0) * b + e);
-    double2* Bv = bufB(q);
+    double2* Ev = bufE(q);
     for (int e = lane; e < rows; e += 32) {
-      const int idx = j0 + e + b + 1;
-      if (idx < len) cpa16(Bv + e, t + r0 + idx);
+      const int idx = j0 + e + 32;
+      if (idx < len) cpa16(Ev + e, t + r0 + idx);
+      else Ev[e] = bz();
     }
     int* I = bufI(q);
     for (int e = lane; e < rows; e += 32) cpa4(I + e, ipiv + r0 + j0 + e);
   };
-  double2 w[BM + 1];
-#pragma unroll
-  for (int q = 0; q <= BM; ++q) w[q] = (lane == 0 && q <= b && q < len) ? t[r0 + q] : bz();
+  double2 w = lane < len ? t[r0 + lane] : bz();
+  double2 fin = bz();                              // the pivot value of this lane's last finished row
   load_fwd(0, 0);
   cpa_commit();
   for (int c = 0; c < nch; ++c) {
@@ -221,66 +234,49 @@ __global__ void __launch_bounds__(32) k_band_solve_local(int n, int b, int s, in
     cpa_commit();
     cpa_wait1();
     __syncwarp();
-    if (lane == 0) {
-      const int j0 = c * CH, rows = min(CH, len - j0);
-      const double2* A = bufA(c & 1);
-      const double2* Bv = bufB(c & 1);
-      const int* I = bufI(c & 1);
-      for (int jj = 0; jj < rows; ++jj) {
-        const int j = j0 + jj, g = r0 + j;
-        const int pj = I[jj] - g;
-        const double2 w0 = w[0];
-        double2 sel = w0;
-#pragma unroll
-        for (int q = 1; q <= BM; ++q) {           // interchange rows j and ipiv[j] (selects, no indexing)
-          const bool hit = q == pj;
-          const double2 wq = w[q];
-          sel = hit ? wq : sel;
-          w[q] = hit ? w0 : wq;
-        }
-        w[0] = sel;
-        y[g] = sel;
-#pragma unroll
-        for (int q = 1; q <= BM; ++q)
-          if (q <= b) w[q] = w[q] - cmul(A[jj * b + q - 1], sel);
-#pragma unroll
-        for (int q = 0; q < BM; ++q) w[q] = w[q + 1];
-        w[BM] = bz();
-        const double2 tn = (j + 1 + b < len) ? Bv[jj] : bz();
-#pragma unroll
-        for (int q = 0; q <= BM; ++q) w[q] = q == b ? tn : w[q];
+    const int j0 = c * CH, rows = min(CH, len - j0);
+    const double2* A = bufA(c & 1);
+    const double2* Ev = bufE(c & 1);
+    const int* I = bufI(c & 1);
+#pragma unroll 4
+    for (int jj = 0; jj < rows; ++jj) {
+      const int j = j0 + jj, me = j & 31;
+      const int pl = (I[jj] - r0) & 31;            // lane of the pivot row (j <= pivot <= j + b)
+      const bool piv = lane == pl;
+      const double2 tv = shfl2(w, piv ? me : pl);
+      const double2 sel = piv ? w : tv;
+      if (piv) w = tv;                             // the pivot row's lane now holds row j
+      const int d = (lane - me) & 31;              // this lane holds row j + d
+      if (d >= 1 && d <= b) w = cfms(w, A[jj * b + d - 1], sel);
+      if (lane == me) { fin = sel; w = Ev[jj]; }
+      if (me == 31 || j == len - 1) {              // rows (j & ~31) .. j are final: one coalesced store
+        const int row = (j & ~31) + lane;
+        if (row <= j) y[r0 + row] = fin;
       }
     }
     __syncwarp();                                  // the buffer is refilled two chunks later
   }
-  // forward results are read back by every lane's copies
-  if (lane == 0) __threadfence();
+  __threadfence();                                 // forward results are read back by cp.async
   __syncwarp();
 
-  // ---- back sweep: chunk c = rows jlo .. jhi, taken from the end
-  auto back_range = [&](int c, int& jlo, int& rows) {
-    const int jhi = len - c * CH - 1;
-    jlo = max(0, jhi - CH + 1);
-    rows = jhi - jlo + 1;
-  };
+  // ---- back sweep over m = len - 1 - j; chunk c = m0 .. m0 + CH - 1; row
+  // j = len - 1 - m lives in lane m mod 32
   auto load_back = [&](int c, int q) {
-    int jlo, rows;
-    back_range(c, jlo, rows);
+    const int m0 = c * CH, rows = min(CH, len - m0);
     double2* A = bufA(q);
-    for (int e = lane; e < rows * 2 * b; e += 32) {
-      const int row = e / (2 * b), qq = e - row * 2 * b;
-      cpa16(A + e, lu + (size_t)(r0 + jlo + row) * W + b + 1 + qq);
+    for (int e = lane; e < rows * b2; e += 32) {
+      const int mm = e / b2, qq = e - mm * b2;
+      cpa16(A + e, ucs + (size_t)(r0 + len - 1 - m0 - mm) * b2 + qq);
     }
-    double2* Bv = bufB(q);
-    double2* Cv = bufC(q);
+    double2* Ev = bufE(q);
     for (int e = lane; e < rows; e += 32) {
-      cpa16(Bv + e, rdiag + r0 + jlo + e);
-      cpa16(Cv + e, y + r0 + jlo + e);
+      const int jn = len - 1 - m0 - e - 32;
+      if (jn >= 0) cpa16(Ev + e, y + r0 + jn);
+      else Ev[e] = bz();
     }
   };
-  double2 x[2 * BM];
-#pragma unroll
-  for (int q = 0; q < 2 * BM; ++q) x[q] = bz();
+  double2 acc = lane < len ? y[r0 + len - 1 - lane] : bz();
+  double2 dv = bz();
   load_back(0, 0);
   cpa_commit();
   for (int c = 0; c < nch; ++c) {
@@ -288,33 +284,31 @@ __global__ void __launch_bounds__(32) k_band_solve_local(int n, int b, int s, in
     cpa_commit();
     cpa_wait1();
     __syncwarp();
-    if (lane == 0) {
-      int jlo, rows;
-      back_range(c, jlo, rows);
-      const double2* A = bufA(c & 1);
-      const double2* Bv = bufB(c & 1);
-      const double2* Cv = bufC(c & 1);
-      for (int jj = rows - 1; jj >= 0; --jj) {
-        double2 a0 = Cv[jj], a1 = bz();            // two partial sums shorten the dependent chain
-#pragma unroll
-        for (int q = 0; q < 2 * BM; q += 2) {
-          if (q < 2 * b) a0 = a0 - cmul(A[jj * 2 * b + q], x[q]);
-          if (q + 1 < 2 * b) a1 = a1 - cmul(A[jj * 2 * b + q + 1], x[q + 1]);
-        }
-        const double2 xj = cmul(a0 + a1, Bv[jj]);
-#pragma unroll
-        for (int q = 2 * BM - 1; q > 0; --q) x[q] = x[q - 1];
-        x[0] = xj;
-        y[r0 + jlo + jj] = xj;
+    const int m0 = c * CH, rows = min(CH, len - m0);
+    const double2* A = bufA(c & 1);
+    const double2* Ev = bufE(c & 1);
+#pragma unroll 4
+    for (int mm = 0; mm < rows; ++mm) {
+      const int m = m0 + mm, me = m & 31;
+      if (me == 0) {                               // 1 / U(j, j) of this lane's row in the coming group
+        const int jr = len - 1 - m - lane;
+        dv = jr >= 0 ? rdiag[r0 + jr] : bz();
+      }
+      const double2 a = shfl2(acc, me);            // acc_j, final
+      const int d = (lane - me) & 31;              // this lane holds row j - d
+      if (d >= 1 && d <= b2) acc = cfms(acc, A[mm * b2 + d - 1], a);
+      if (lane == me) { fin = a; acc = Ev[mm]; }
+      if (me == 31 || m == len - 1) {              // rows of m = (m & ~31) .. m are final
+        const int mr = (m & ~31) + lane;
+        if (mr <= m) y[r0 + len - 1 - mr] = cmul(fin, dv);
       }
     }
     __syncwarp();
   }
-  if (rz && lane == 0)
-    for (int a = 0; a < b; ++a) {
-      rz[2 * b * i + a] = y[r0 + a];
-      rz[2 * b * i + b + a] = y[r1 - b + a];
-    }
+  if (rz) {
+    __syncwarp();
+    for (int a = lane; a < b2; a += 32) rz[b2 * i + a] = a < b ? y[r0 + a] : y[r1 - b2 + a];
+  }
 }
 
 // x_r = y_r - V_r top(x_{i+1}) - W_r bot(x_{i-1}) (thread per row)
@@ -346,35 +340,30 @@ __global__ void k_probe_scatter(const double2* y, int n, int b, int c, double2* 
   if (j >= 0 && j < n) Ab[(size_t)i * stride + j - i + b] = y[i];
 }
 
-// forward and back substitution of every partition (b <= 5: the matrices;
-// b <= 15: the interface system, half bandwidth 3b)
-template <int BM>
-void launch_local(int n, int b, int s, int P, const double2* lu, const double2* lm, const double2* rdiag,
-                  const int* ipiv, const double2* t, double2* y, double2* rz, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_band_solve_local<BM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)band_smem(BM));
-    attr = true;
+// U(j-1-q, j) / U(j, j), q < 2b, inside each partition (thread per row)
+__global__ void k_band_ucols(int n, int b, int s, int P, const double2* __restrict__ lu,
+                             const double2* __restrict__ rdiag, double2* __restrict__ ucs) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n) return;
+  const int i = min(g / s, P - 1), r0 = i * s, W = 3 * b + 1;
+  const double2 dj = rdiag[g];
+  for (int q = 0; q < 2 * b; ++q) {
+    const int r = g - 1 - q;
+    ucs[(size_t)g * 2 * b + q] = r >= r0 ? cmul(lu[(size_t)r * W + q + 1 + b], dj) : bz();
   }
-  k_band_solve_local<BM><<<P, 32, band_smem(b), st>>>(n, b, s, P, lu, lm, rdiag, ipiv, t, y, rz);
-  iga_count_launch();
 }
 
-// forward and back substitution of every partition with the narrowest window
-// that holds b (b <= 5: the matrices; 3, 6, 9, 12, 15: interface systems)
-void solve_parts(int n, int b, int s, int P, const double2* lu, const double2* lm, const double2* rdiag,
-                 const int* ipiv, const double2* t, double2* y, double2* rz, cudaStream_t st) {
-  switch (b) {
-    case 1: launch_local<1>(n, b, s, P, lu, lm, rdiag, ipiv, t, y, rz, st); break;
-    case 2: launch_local<2>(n, b, s, P, lu, lm, rdiag, ipiv, t, y, rz, st); break;
-    case 3: launch_local<3>(n, b, s, P, lu, lm, rdiag, ipiv, t, y, rz, st); break;
-    case 4: launch_local<4>(n, b, s, P, lu, lm, rdiag, ipiv, t, y, rz, st); break;
-    case 5: launch_local<5>(n, b, s, P, lu, lm, rdiag, ipiv, t, y, rz, st); break;
-    case 6: launch_local<6>(n, b, s, P, lu, lm, rdiag, ipiv, t, y, rz, st); break;
-    case 9: launch_local<9>(n, b, s, P, lu, lm, rdiag, ipiv, t, y, rz, st); break;
-    case 12: launch_local<12>(n, b, s, P, lu, lm, rdiag, ipiv, t, y, rz, st); break;
-    default: launch_local<15>(n, b, s, P, lu, lm, rdiag, ipiv, t, y, rz, st); break;
+// forward and back substitution of every partition (b <= 5: the matrices;
+// b <= 15: interface systems, half bandwidth 3b)
+void solve_parts(int n, int b, int s, int P, const double2* lm, const int* ipiv, const double2* ucs,
+                 const double2* rdiag, const double2* t, double2* y, double2* rz, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_band_solve_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)band_smem(15));
+    attr = true;
   }
+  k_band_solve_warp<<<P, 32, band_smem(b), st>>>(n, b, s, P, lm, ipiv, ucs, rdiag, t, y, rz);
+  iga_count_launch();
 }
 
 }  // namespace
@@ -409,6 +398,9 @@ iga_status band_setup(iga_ctx* ctx, BandLU& F, const double2* Ab, int n, int b) 
   if (!F.lu || !F.y || !F.lm || !F.rdiag || !F.ipiv || !info) return set_err(ctx, IGA_E_OOM, "band solver");
   CK(cudaMemsetAsync(info, 0, 2 * sizeof(int), ctx->st));
   k_band_factor<<<cdiv(P, 32), 32, 0, ctx->st>>>(Ab, n, b, s, P, F.lu, F.lm, F.rdiag, F.ipiv, info); iga_count_launch();
+  F.ucs = dalloc<double2>(ctx, (size_t)n * 2 * b);
+  if (!F.ucs) return set_err(ctx, IGA_E_OOM, "band solver");
+  k_band_ucols<<<cdiv(n, 256), 256, 0, ctx->st>>>(n, b, s, P, F.lu, F.rdiag, F.ucs); iga_count_launch();
   CKL();
   if (P > 1) {
     F.V = dalloc<double2>(ctx, (size_t)n * b);
@@ -422,14 +414,17 @@ iga_status band_setup(iga_ctx* ctx, BandLU& F, const double2* Ab, int n, int b) 
     F.rlm = dalloc<double2>(ctx, (size_t)F.nr * F.br);
     F.rrdiag = dalloc<double2>(ctx, F.nr);
     F.ripiv = dalloc<int>(ctx, F.nr);
+    F.rucs = dalloc<double2>(ctx, (size_t)F.nr * 2 * F.br);
     F.rz = dalloc<double2>(ctx, F.nr);
     F.rz2 = dalloc<double2>(ctx, F.nr);
-    if (!F.V || !F.Wl || !scratch || !R || !F.rlu || !F.rlm || !F.rrdiag || !F.ripiv || !F.rz || !F.rz2)
+    if (!F.V || !F.Wl || !scratch || !R || !F.rlu || !F.rlm || !F.rrdiag || !F.ripiv || !F.rucs || !F.rz || !F.rz2)
       return set_err(ctx, IGA_E_OOM, "band solver spikes");
     k_band_spikes<<<cdiv(P * 2 * b, 64), 64, 0, ctx->st>>>(Ab, n, b, s, P, F.lu, F.lm, F.rdiag, F.ipiv, scratch, F.V,
                                                           F.Wl); iga_count_launch();
     k_band_reduced<<<cdiv(P, 64), 64, 0, ctx->st>>>(n, b, s, P, F.V, F.Wl, R); iga_count_launch();
     k_band_factor<<<1, 32, 0, ctx->st>>>(R, F.nr, F.br, F.nr, 1, F.rlu, F.rlm, F.rrdiag, F.ripiv, info + 1);
+    iga_count_launch();
+    k_band_ucols<<<cdiv(F.nr, 256), 256, 0, ctx->st>>>(F.nr, F.br, F.nr, 1, F.rlu, F.rrdiag, F.rucs);
     iga_count_launch();
     CKL();
   }
@@ -457,11 +452,11 @@ iga_status band_clone_scratch(iga_ctx* ctx, BandLU& F) {
 // x = A^{-1} t (t and x may be the same vector)
 iga_status band_solve(iga_ctx* ctx, const BandLU& F, const double2* t, double2* x) {
   if (F.P == 1 && x != t) {
-    solve_parts(F.n, F.b, F.s, 1, F.lu, F.lm, F.rdiag, F.ipiv, t, x, nullptr, ctx->st);
+    solve_parts(F.n, F.b, F.s, 1, F.lm, F.ipiv, F.ucs, F.rdiag, t, x, nullptr, ctx->st);
   } else {
-    solve_parts(F.n, F.b, F.s, F.P, F.lu, F.lm, F.rdiag, F.ipiv, t, F.y, F.P > 1 ? F.rz : nullptr, ctx->st);
+    solve_parts(F.n, F.b, F.s, F.P, F.lm, F.ipiv, F.ucs, F.rdiag, t, F.y, F.P > 1 ? F.rz : nullptr, ctx->st);
     if (F.P > 1) {
-      solve_parts(F.nr, F.br, F.nr, 1, F.rlu, F.rlm, F.rrdiag, F.ripiv, F.rz, F.rz2, nullptr, ctx->st);
+      solve_parts(F.nr, F.br, F.nr, 1, F.rlm, F.ripiv, F.rucs, F.rrdiag, F.rz, F.rz2, nullptr, ctx->st);
       k_band_update<<<cdiv(F.n, 256), 256, 0, ctx->st>>>(F.n, F.b, F.s, F.P, F.V, F.Wl, F.rz2, F.y, x);
       iga_count_launch();
     } else {

@@ -95,11 +95,13 @@ struct BandLU {
   double2* lm = nullptr;             // [n][b] multipliers of elimination step j (rows j+1 .. j+b)
   double2* rdiag = nullptr;          // [n] 1 / U(r, r)
   int* ipiv = nullptr;               // [n] pivot row of step j
+  double2* ucs = nullptr;            // [n][2b] column j of U above the diagonal scaled by 1 / U(j, j):
+                                     //   U(j-1-q, j) / U(j, j), zero above the partition's first row
   double2* V = nullptr;              // [n][b] right spikes A_i^{-1} [0; B_i]
   double2* Wl = nullptr;             // [n][b] left spikes A_i^{-1} [C_i; 0]
   double2* y = nullptr;              // [n] partition solutions
   int nr = 0, br = 0;                // interface system: 2 b P unknowns, half bandwidth 3b
-  double2 *rlu = nullptr, *rlm = nullptr, *rrdiag = nullptr, *rz = nullptr, *rz2 = nullptr;
+  double2 *rlu = nullptr, *rlm = nullptr, *rrdiag = nullptr, *rucs = nullptr, *rz = nullptr, *rz2 = nullptr;
   int* ripiv = nullptr;
 };
 

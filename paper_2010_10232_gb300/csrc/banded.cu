@@ -340,6 +340,146 @@ __global__ void k_probe_scatter(const double2* y, int n, int b, int c, double2* 
   if (j >= 0 && j < n) Ab[(size_t)i * stride + j - i + b] = y[i];
 }
 
+__device__ __forceinline__ double flip_sign(double v, bool neg) {
+  return __hiloint2double(__double2hiint(v) ^ (neg ? (int)0x80000000 : 0), __double2loint(v));
+}
+
+// The same two sweeps with a row's real and imaginary parts in two lanes
+// (lane 2 slot + c holds component c of the row in slot j mod 16): a complex
+// multiply-add is then two FP64 warp instructions instead of four.  The back
+// sweep's window of 2b + 1 rows must fit in 16 slots: b <= 7.  Arguments as
+// k_band_solve_warp.
+__global__ void __launch_bounds__(32) k_band_solve_pair(int n, int b, int s, int P, const double2* __restrict__ lm,
+                                                        const int* __restrict__ ipiv, const double2* __restrict__ ucs,
+                                                        const double2* __restrict__ rdiag,
+                                                        const double2* __restrict__ t, double2* __restrict__ y,
+                                                        double2* __restrict__ rz) {
+  const int i = blockIdx.x, lane = threadIdx.x, slot = lane >> 1, c = lane & 1;
+  if (i >= P) return;
+  int r0, r1;
+  part_rows(i, n, s, P, r0, r1);
+  const int len = r1 - r0, b2 = 2 * b, CH = band_chunk(b);
+  const double* td = reinterpret_cast<const double*>(t);
+  double* yd = reinterpret_cast<double*>(y);
+  extern __shared__ __align__(16) unsigned char band_sm[];
+  const size_t sb = band_stage(b);
+  auto bufA = [&](int q) { return reinterpret_cast<double2*>(band_sm + q * sb); };
+  auto bufE = [&](int q) { return bufA(q) + (size_t)CH * b2; };
+  auto bufI = [&](int q) { return reinterpret_cast<int*>(bufE(q) + CH); };
+  const int nch = (len + CH - 1) / CH;
+
+  // ---- forward sweep; the lane of a finished row takes row j + 16
+  auto load_fwd = [&](int ch, int q) {
+    const int j0 = ch * CH, rows = min(CH, len - j0);
+    double2* A = bufA(q);
+    for (int e = lane; e < rows * b; e += 32) cpa16(A + e, lm + (size_t)(r0 + j0) * b + e);
+    double2* Ev = bufE(q);
+    for (int e = lane; e < rows; e += 32) {
+      const int idx = j0 + e + 16;
+      if (idx < len) cpa16(Ev + e, t + r0 + idx);
+      else Ev[e] = bz();
+    }
+    int* I = bufI(q);
+    for (int e = lane; e < rows; e += 32) cpa4(I + e, ipiv + r0 + j0 + e);
+  };
+  double w = slot < len ? td[2 * (size_t)(r0 + slot) + c] : 0.0;
+  double fin = 0.0;
+  load_fwd(0, 0);
+  cpa_commit();
+  for (int ch = 0; ch < nch; ++ch) {
+    if (ch + 1 < nch) load_fwd(ch + 1, (ch + 1) & 1);
+    cpa_commit();
+    cpa_wait1();
+    __syncwarp();
+    const int j0 = ch * CH, rows = min(CH, len - j0);
+    const double2* A = bufA(ch & 1);
+    const double* Ev = reinterpret_cast<const double*>(bufE(ch & 1));
+    const int* I = bufI(ch & 1);
+#pragma unroll 4
+    for (int jj = 0; jj < rows; ++jj) {
+      const int j = j0 + jj, me = j & 15;
+      const int pl = (I[jj] - r0) & 15;            // slot of the pivot row
+      const double sc = __shfl_sync(0xffffffffu, w, 2 * pl + c);       // pivot value, this lane's part
+      const double so = __shfl_sync(0xffffffffu, w, 2 * pl + 1 - c);   // and the other part
+      const double rj = __shfl_sync(0xffffffffu, w, 2 * me + c);       // row j, for the pivot row's lanes
+      if (slot == pl) w = rj;
+      const int d = (slot - me) & 15;              // this lane holds row j + d
+      if (d >= 1 && d <= b) {
+        const double2 a = A[jj * b + d - 1];
+        w = fma(-a.x, sc, fma(flip_sign(a.y, c), so, w));
+      }
+      if (slot == me) { fin = sc; w = Ev[2 * jj + c]; }
+      if (me == 15 || j == len - 1) {
+        const int row = (j & ~15) + slot;
+        if (row <= j) yd[2 * (size_t)(r0 + row) + c] = fin;
+      }
+    }
+    __syncwarp();
+  }
+  __threadfence();
+  __syncwarp();
+
+  // ---- back sweep over m = len - 1 - j; row j in slot m mod 16
+  auto load_back = [&](int ch, int q) {
+    const int m0 = ch * CH, rows = min(CH, len - m0);
+    double2* A = bufA(q);
+    for (int e = lane; e < rows * b2; e += 32) {
+      const int mm = e / b2, qq = e - mm * b2;
+      cpa16(A + e, ucs + (size_t)(r0 + len - 1 - m0 - mm) * b2 + qq);
+    }
+    double2* Ev = bufE(q);
+    for (int e = lane; e < rows; e += 32) {
+      const int jn = len - 1 - m0 - e - 16;
+      if (jn >= 0) cpa16(Ev + e, y + r0 + jn);
+      else Ev[e] = bz();
+    }
+  };
+  double acc = slot < len ? yd[2 * (size_t)(r0 + len - 1 - slot) + c] : 0.0;
+  double fx = 0.0, fy = 0.0;
+  double2 dv = bz();
+  load_back(0, 0);
+  cpa_commit();
+  for (int ch = 0; ch < nch; ++ch) {
+    if (ch + 1 < nch) load_back(ch + 1, (ch + 1) & 1);
+    cpa_commit();
+    cpa_wait1();
+    __syncwarp();
+    const int m0 = ch * CH, rows = min(CH, len - m0);
+    const double2* A = bufA(ch & 1);
+    const double* Ev = reinterpret_cast<const double*>(bufE(ch & 1));
+#pragma unroll 4
+    for (int mm = 0; mm < rows; ++mm) {
+      const int m = m0 + mm, me = m & 15;
+      if (me == 0) {
+        const int jr = len - 1 - m - slot;
+        dv = jr >= 0 ? rdiag[r0 + jr] : bz();
+      }
+      const double ac = __shfl_sync(0xffffffffu, acc, 2 * me + c);     // acc_j, this lane's part
+      const double ao = __shfl_sync(0xffffffffu, acc, 2 * me + 1 - c);
+      const int d = (slot - me) & 15;              // this lane holds row j - d
+      if (d >= 1 && d <= b2) {
+        const double2 u = A[mm * b2 + d - 1];
+        acc = fma(-u.x, ac, fma(flip_sign(u.y, c), ao, acc));
+      }
+      if (slot == me) {
+        fx = c ? ao : ac;
+        fy = c ? ac : ao;
+        acc = Ev[2 * mm + c];
+      }
+      if (me == 15 || m == len - 1) {              // x = acc_j / U(j, j), part c
+        const int mr = (m & ~15) + slot;
+        if (mr <= m)
+          yd[2 * (size_t)(r0 + len - 1 - mr) + c] = fma(fx, c ? dv.y : dv.x, flip_sign(fy, !c) * (c ? dv.x : dv.y));
+      }
+    }
+    __syncwarp();
+  }
+  if (rz) {
+    __syncwarp();
+    for (int a = lane; a < b2; a += 32) rz[b2 * i + a] = a < b ? y[r0 + a] : y[r1 - b2 + a];
+  }
+}
+
 // U(j-1-q, j) / U(j, j), q < 2b, inside each partition (thread per row)
 __global__ void k_band_ucols(int n, int b, int s, int P, const double2* __restrict__ lu,
                              const double2* __restrict__ rdiag, double2* __restrict__ ucs) {
@@ -354,15 +494,18 @@ __global__ void k_band_ucols(int n, int b, int s, int P, const double2* __restri
 }
 
 // forward and back substitution of every partition (b <= 5: the matrices;
-// b <= 15: interface systems, half bandwidth 3b)
+// b <= 15: interface systems, half bandwidth 3b); two lanes per row where the
+// window fits (b <= 7)
 void solve_parts(int n, int b, int s, int P, const double2* lm, const int* ipiv, const double2* ucs,
                  const double2* rdiag, const double2* t, double2* y, double2* rz, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_band_solve_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)band_smem(15));
+    cudaFuncSetAttribute(k_band_solve_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)band_smem(15));
     attr = true;
   }
-  k_band_solve_warp<<<P, 32, band_smem(b), st>>>(n, b, s, P, lm, ipiv, ucs, rdiag, t, y, rz);
+  if (b <= 7) k_band_solve_pair<<<P, 32, band_smem(b), st>>>(n, b, s, P, lm, ipiv, ucs, rdiag, t, y, rz);
+  else k_band_solve_warp<<<P, 32, band_smem(b), st>>>(n, b, s, P, lm, ipiv, ucs, rdiag, t, y, rz);
   iga_count_launch();
 }
 

@@ -7,8 +7,9 @@
     python -m measure.profile_cases sweep32     # FP32 Jacobi sweep on level 0, 4097^2 dofs
     python -m measure.profile_cases cnn         # network forward pass, 1281^2 pixels
     python -m measure.profile_cases esolve1d    # 1D E solve at k = 10^6 (band solver)
+    python -m measure.profile_cases solve1d     # 1D deflated GMRES at k = 10^6, p = 5, 12 iterations
 
-The solve, apply32, sweep32, cnn and esolve1d cases open a profiler range around the
+The solve, apply32, sweep32, cnn, esolve1d and solve1d cases open a profiler range around the
 timed launches only (capture them with `ncu --profile-from-start off`).
 
 Each case launches a handful of kernels on inputs of the bench problem so a
@@ -66,6 +67,18 @@ def main(case: str) -> None:
         torch.cuda.synchronize()
         torch.cuda.profiler.start()
         h.esolve(t)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+    elif case == "solve1d":
+        # MP 1-B at k = 10^6, p = 5 (1.6 10^6 dofs), deflation alone (D): one
+        # solve of 12 iterations inside the profiler range
+        h = Helmholtz(dim=1, p=5, n_el=1600000, kfield=1e6, n_vcycles=0)
+        f = h.point_source(0.5)
+        x = h.vec()
+        h.solve(f, x=x, tol=0.0, maxit=12)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        h.solve(f, x=x, tol=0.0, maxit=12)
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
     elif case == "cnn":

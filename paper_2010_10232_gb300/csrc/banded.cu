@@ -180,20 +180,91 @@ __host__ __device__ constexpr size_t band_stage(int b) {
 }
 __host__ __device__ constexpr size_t band_smem(int b) { return 2 * band_stage(b); }
 
+__device__ __forceinline__ double flip_sign(double v, bool neg) {
+  return __hiloint2double(__double2hiint(v) ^ (neg ? (int)0x80000000 : 0), __double2loint(v));
+}
+
+// Forward sweep of one partition (rows r0 .. r0 + len - 1), y = L^{-1} Pi t,
+// with the real and imaginary parts of the row in slot j mod 16 in lanes
+// 2 slot and 2 slot + 1: a step is three shuffles (the pivot row's two parts
+// to every lane, row j's part to the pivot row's lanes) and one complex
+// multiply-add of two FP64 warp instructions in the b rows below; the lanes of
+// a finished row take row j + 16.  b <= 15.  Ends with the results visible to
+// the back sweep's cp.async copies.
+__device__ __forceinline__ void band_fwd_pair(int b, int r0, int len, const double2* __restrict__ lm,
+                                              const int* __restrict__ ipiv, const double2* __restrict__ t,
+                                              double2* __restrict__ y, unsigned char* band_sm, int lane) {
+  const int slot = lane >> 1, c = lane & 1, b2 = 2 * b, CH = band_chunk(b);
+  const double* td = reinterpret_cast<const double*>(t);
+  double* yd = reinterpret_cast<double*>(y);
+  const size_t sb = band_stage(b);
+  auto bufA = [&](int q) { return reinterpret_cast<double2*>(band_sm + q * sb); };
+  auto bufE = [&](int q) { return bufA(q) + (size_t)CH * b2; };
+  auto bufI = [&](int q) { return reinterpret_cast<int*>(bufE(q) + CH); };
+  const int nch = (len + CH - 1) / CH;
+  auto load_fwd = [&](int ch, int q) {
+    const int j0 = ch * CH, rows = min(CH, len - j0);
+    double2* A = bufA(q);
+    for (int e = lane; e < rows * b; e += 32) cpa16(A + e, lm + (size_t)(r0 + j0) * b + e);
+    double2* Ev = bufE(q);
+    for (int e = lane; e < rows; e += 32) {
+      const int idx = j0 + e + 16;
+      if (idx < len) cpa16(Ev + e, t + r0 + idx);
+      else Ev[e] = bz();
+    }
+    int* I = bufI(q);
+    for (int e = lane; e < rows; e += 32) cpa4(I + e, ipiv + r0 + j0 + e);
+  };
+  double w = slot < len ? td[2 * (size_t)(r0 + slot) + c] : 0.0;
+  double fin = 0.0;
+  load_fwd(0, 0);
+  cpa_commit();
+  for (int ch = 0; ch < nch; ++ch) {
+    if (ch + 1 < nch) load_fwd(ch + 1, (ch + 1) & 1);
+    cpa_commit();
+    cpa_wait1();
+    __syncwarp();
+    const int j0 = ch * CH, rows = min(CH, len - j0);
+    const double2* A = bufA(ch & 1);
+    const double* Ev = reinterpret_cast<const double*>(bufE(ch & 1));
+    const int* I = bufI(ch & 1);
+#pragma unroll 4
+    for (int jj = 0; jj < rows; ++jj) {
+      const int j = j0 + jj, me = j & 15;
+      const int pl = (I[jj] - r0) & 15;            // slot of the pivot row
+      const double sc = __shfl_sync(0xffffffffu, w, 2 * pl + c);       // pivot value, this lane's part
+      const double so = __shfl_sync(0xffffffffu, w, 2 * pl + 1 - c);   // and the other part
+      const double rj = __shfl_sync(0xffffffffu, w, 2 * me + c);       // row j, for the pivot row's lanes
+      if (slot == pl) w = rj;
+      const int d = (slot - me) & 15;              // this lane holds row j + d
+      if (d >= 1 && d <= b) {
+        const double2 a = A[jj * b + d - 1];
+        w = fma(-a.x, sc, fma(flip_sign(a.y, c), so, w));
+      }
+      if (slot == me) { fin = sc; w = Ev[2 * jj + c]; }
+      if (me == 15 || j == len - 1) {
+        const int row = (j & ~15) + slot;
+        if (row <= j) yd[2 * (size_t)(r0 + row) + c] = fin;
+      }
+    }
+    __syncwarp();
+  }
+  __threadfence();
+  __syncwarp();
+}
+
 // y = A_i^{-1} t for every partition: one warp per partition (one warp per
-// block), b <= 15.  Row j of the partition lives in lane j mod 32 while it is
-// in the elimination window, so a step moves no window: the forward sweep's
-// step j takes the pivot row by one shuffle (lane p gets row j, every lane the
-// pivot value), updates rows j+1 .. j+b in their lanes with one complex
-// multiply-add, and hands lane j the right-hand side of row j+32.  The back
-// sweep runs column by column: step j broadcasts the finished sum acc_j of
-// row j and subtracts U(r, j) x_j = (U(r, j) / U(j, j)) acc_j from rows
-// j-1 .. j-2b (the columns of U are scaled at setup), so that
-// x_j = acc_j / U(j, j) is formed 32 rows at a time, off the dependent chain.  Per row: two shuffles and eight
-// FP64 warp instructions, whatever b.  The next chunk of coefficients is
-// copied into shared memory with cp.async while the current one is swept.  t,
-// y and rz must not overlap.  rz (optional): the partition's first and last b
-// solution values, as the interface system's right-hand side.
+// block), b <= 15.  The forward sweep is band_fwd_pair.  The back sweep runs
+// column by column with row j in lane j mod 32 for as long as it is in the
+// window (so no step shifts the window): step j broadcasts the finished sum
+// acc_j of row j (one shuffle) and subtracts U(r, j) x_j = (U(r, j) / U(j, j))
+// acc_j from rows j-1 .. j-2b in their lanes (one complex multiply-add, four
+// FP64 warp instructions, whatever b; the columns of U are scaled at setup),
+// so that x_j = acc_j / U(j, j) is formed 32 rows at a time, off the
+// dependent chain.  The next chunk of coefficients is copied into shared
+// memory with cp.async while the current one is swept.  t, y and rz must not
+// overlap.  rz (optional): the partition's first and last b solution values,
+// as the interface system's right-hand side.
 __global__ void __launch_bounds__(32) k_band_solve_warp(int n, int b, int s, int P, const double2* __restrict__ lm,
                                                         const int* __restrict__ ipiv, const double2* __restrict__ ucs,
                                                         const double2* __restrict__ rdiag,
@@ -208,56 +279,9 @@ __global__ void __launch_bounds__(32) k_band_solve_warp(int n, int b, int s, int
   const size_t sb = band_stage(b);
   auto bufA = [&](int q) { return reinterpret_cast<double2*>(band_sm + q * sb); };
   auto bufE = [&](int q) { return bufA(q) + (size_t)CH * b2; };
-  auto bufI = [&](int q) { return reinterpret_cast<int*>(bufE(q) + CH); };
   const int nch = (len + CH - 1) / CH;
 
-  // ---- forward sweep: chunk c = rows j0 .. j0 + CH - 1
-  auto load_fwd = [&](int c, int q) {
-    const int j0 = c * CH, rows = min(CH, len - j0);
-    double2* A = bufA(q);
-    for (int e = lane; e < rows * b; e += 32) cpa16(A + e, lm + (size_t)(r0 + j0) * b + e);
-    double2* Ev = bufE(q);
-    for (int e = lane; e < rows; e += 32) {
-      const int idx = j0 + e + 32;
-      if (idx < len) cpa16(Ev + e, t + r0 + idx);
-      else Ev[e] = bz();
-    }
-    int* I = bufI(q);
-    for (int e = lane; e < rows; e += 32) cpa4(I + e, ipiv + r0 + j0 + e);
-  };
-  double2 w = lane < len ? t[r0 + lane] : bz();
-  double2 fin = bz();                              // the pivot value of this lane's last finished row
-  load_fwd(0, 0);
-  cpa_commit();
-  for (int c = 0; c < nch; ++c) {
-    if (c + 1 < nch) load_fwd(c + 1, (c + 1) & 1);
-    cpa_commit();
-    cpa_wait1();
-    __syncwarp();
-    const int j0 = c * CH, rows = min(CH, len - j0);
-    const double2* A = bufA(c & 1);
-    const double2* Ev = bufE(c & 1);
-    const int* I = bufI(c & 1);
-#pragma unroll 4
-    for (int jj = 0; jj < rows; ++jj) {
-      const int j = j0 + jj, me = j & 31;
-      const int pl = (I[jj] - r0) & 31;            // lane of the pivot row (j <= pivot <= j + b)
-      const bool piv = lane == pl;
-      const double2 tv = shfl2(w, piv ? me : pl);
-      const double2 sel = piv ? w : tv;
-      if (piv) w = tv;                             // the pivot row's lane now holds row j
-      const int d = (lane - me) & 31;              // this lane holds row j + d
-      if (d >= 1 && d <= b) w = cfms(w, A[jj * b + d - 1], sel);
-      if (lane == me) { fin = sel; w = Ev[jj]; }
-      if (me == 31 || j == len - 1) {              // rows (j & ~31) .. j are final: one coalesced store
-        const int row = (j & ~31) + lane;
-        if (row <= j) y[r0 + row] = fin;
-      }
-    }
-    __syncwarp();                                  // the buffer is refilled two chunks later
-  }
-  __threadfence();                                 // forward results are read back by cp.async
-  __syncwarp();
+  band_fwd_pair(b, r0, len, lm, ipiv, t, y, band_sm, lane);
 
   // ---- back sweep over m = len - 1 - j; chunk c = m0 .. m0 + CH - 1; row
   // j = len - 1 - m lives in lane m mod 32
@@ -276,7 +300,7 @@ __global__ void __launch_bounds__(32) k_band_solve_warp(int n, int b, int s, int
     }
   };
   double2 acc = lane < len ? y[r0 + len - 1 - lane] : bz();
-  double2 dv = bz();
+  double2 fin = bz(), dv = bz();
   load_back(0, 0);
   cpa_commit();
   for (int c = 0; c < nch; ++c) {
@@ -340,12 +364,9 @@ __global__ void k_probe_scatter(const double2* y, int n, int b, int c, double2* 
   if (j >= 0 && j < n) Ab[(size_t)i * stride + j - i + b] = y[i];
 }
 
-__device__ __forceinline__ double flip_sign(double v, bool neg) {
-  return __hiloint2double(__double2hiint(v) ^ (neg ? (int)0x80000000 : 0), __double2loint(v));
-}
 
-// The same two sweeps with a row's real and imaginary parts in two lanes
-// (lane 2 slot + c holds component c of the row in slot j mod 16): a complex
+// The same solve with the back sweep also on two lanes per row (lane
+// 2 slot + c holds part c of the row in slot m mod 16): a complex
 // multiply-add is then two FP64 warp instructions instead of four.  The back
 // sweep's window of 2b + 1 rows must fit in 16 slots: b <= 7.  Arguments as
 // k_band_solve_warp.
@@ -359,65 +380,14 @@ __global__ void __launch_bounds__(32) k_band_solve_pair(int n, int b, int s, int
   int r0, r1;
   part_rows(i, n, s, P, r0, r1);
   const int len = r1 - r0, b2 = 2 * b, CH = band_chunk(b);
-  const double* td = reinterpret_cast<const double*>(t);
   double* yd = reinterpret_cast<double*>(y);
   extern __shared__ __align__(16) unsigned char band_sm[];
   const size_t sb = band_stage(b);
   auto bufA = [&](int q) { return reinterpret_cast<double2*>(band_sm + q * sb); };
   auto bufE = [&](int q) { return bufA(q) + (size_t)CH * b2; };
-  auto bufI = [&](int q) { return reinterpret_cast<int*>(bufE(q) + CH); };
   const int nch = (len + CH - 1) / CH;
 
-  // ---- forward sweep; the lane of a finished row takes row j + 16
-  auto load_fwd = [&](int ch, int q) {
-    const int j0 = ch * CH, rows = min(CH, len - j0);
-    double2* A = bufA(q);
-    for (int e = lane; e < rows * b; e += 32) cpa16(A + e, lm + (size_t)(r0 + j0) * b + e);
-    double2* Ev = bufE(q);
-    for (int e = lane; e < rows; e += 32) {
-      const int idx = j0 + e + 16;
-      if (idx < len) cpa16(Ev + e, t + r0 + idx);
-      else Ev[e] = bz();
-    }
-    int* I = bufI(q);
-    for (int e = lane; e < rows; e += 32) cpa4(I + e, ipiv + r0 + j0 + e);
-  };
-  double w = slot < len ? td[2 * (size_t)(r0 + slot) + c] : 0.0;
-  double fin = 0.0;
-  load_fwd(0, 0);
-  cpa_commit();
-  for (int ch = 0; ch < nch; ++ch) {
-    if (ch + 1 < nch) load_fwd(ch + 1, (ch + 1) & 1);
-    cpa_commit();
-    cpa_wait1();
-    __syncwarp();
-    const int j0 = ch * CH, rows = min(CH, len - j0);
-    const double2* A = bufA(ch & 1);
-    const double* Ev = reinterpret_cast<const double*>(bufE(ch & 1));
-    const int* I = bufI(ch & 1);
-#pragma unroll 4
-    for (int jj = 0; jj < rows; ++jj) {
-      const int j = j0 + jj, me = j & 15;
-      const int pl = (I[jj] - r0) & 15;            // slot of the pivot row
-      const double sc = __shfl_sync(0xffffffffu, w, 2 * pl + c);       // pivot value, this lane's part
-      const double so = __shfl_sync(0xffffffffu, w, 2 * pl + 1 - c);   // and the other part
-      const double rj = __shfl_sync(0xffffffffu, w, 2 * me + c);       // row j, for the pivot row's lanes
-      if (slot == pl) w = rj;
-      const int d = (slot - me) & 15;              // this lane holds row j + d
-      if (d >= 1 && d <= b) {
-        const double2 a = A[jj * b + d - 1];
-        w = fma(-a.x, sc, fma(flip_sign(a.y, c), so, w));
-      }
-      if (slot == me) { fin = sc; w = Ev[2 * jj + c]; }
-      if (me == 15 || j == len - 1) {
-        const int row = (j & ~15) + slot;
-        if (row <= j) yd[2 * (size_t)(r0 + row) + c] = fin;
-      }
-    }
-    __syncwarp();
-  }
-  __threadfence();
-  __syncwarp();
+  band_fwd_pair(b, r0, len, lm, ipiv, t, y, band_sm, lane);
 
   // ---- back sweep over m = len - 1 - j; row j in slot m mod 16
   auto load_back = [&](int ch, int q) {
